@@ -1,0 +1,165 @@
+/*
+ * rd.h -- C ABI of the GB300 R-distance library (librd.so).
+ *
+ * The library computes the R-distance of Jing & Meister, "A fast algorithm for
+ * All-Pairs-Shortest-Paths suitable for neural networks":
+ *
+ *   Y = (I - gamma A)^-1                         (Sec. 2, eq. Y-defined)
+ *   Y = (I - X)^-1, X_ij = gamma^W_ij on edges   (Sec. 3.2, weighted extension)
+ *   D_ij = ceil(log_gamma Y_ij)                  (Sec. 2 eq. R-defined; Sec. 4.1 eq.
+ *                                                 rounded-distance-function)
+ *
+ * on one GPU, with every step of the path in the library's own CUDA kernels (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Orientation (Sec. 2, adjacency definition and its footnote): A[i*n + j] != 0 iff there
+ *    is a directed edge from node j to node i.  Column j of A lists the successors of j and
+ *    the out-degree of j is a column sum.  D[i*n + j] is the distance FROM j TO i.
+ *    All matrices are dense, row-major, with leading dimension n.
+ *  - Pointers may be host memory (pageable or pinned) or device memory of the handle's
+ *    device; the library inspects each pointer.  Device pointers are used in place and the
+ *    call is asynchronous on the handle's stream.  Host inputs are copied in; when an output
+ *    is host memory the call waits for the stream before returning so the data is valid.
+ *    The caller owns every buffer it passes; the library never keeps a caller pointer after
+ *    a call returns (rd_create copies A and W).
+ *  - The handle owns its device workspace (the packed LU factors, the triangular inverses
+ *    and scratch, about 2.5 * 8 * N^2 bytes with N = n rounded up to a multiple of 128).
+ *  - Errors found on the host are returned at once and nothing is enqueued.  Errors found on
+ *    the device (a non-positive pivot, a non-finite Y) are recorded in a device status word
+ *    and returned by the next call that synchronises (rd_sync, or any call with a host
+ *    output).
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *
+ * Decode details (readings of the paper, identical in the CPU oracle):
+ *  - D_ij = ceil(log(Y_ij)/log(gamma) - tau), tau = 1e-9 unless changed by rd_set_tau.  When
+ *    Y_ij is an exact power of gamma (one path and no longer walks) R_ij is an integer and the
+ *    snap keeps FP64 rounding from moving the ceil.
+ *  - D_ii = 0.  Y_ij <= 0 (unreachable, or below the smallest double: Sec. 5.1, eq.
+ *    gamma-precision) gives RD_UNREACHABLE.  A value too large for int32 is clamped to
+ *    RD_UNREACHABLE - 1.  Off-diagonal Y_ij >= 1 (near the critical gain, Example 4.1) keeps
+ *    the literal ceil, which may be 0 or negative.
+ */
+#ifndef RD_H_
+#define RD_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RD_UNREACHABLE INT32_MAX
+
+typedef struct rd_ctx* rd_handle;
+
+typedef enum {
+  RD_OK = 0,
+  RD_ERR_ARG = 1,         /* null pointer, n < 1, k out of range, goal index out of range   */
+  RD_ERR_GAMMA = 2,       /* gamma not in (0,1), or the largest column sum of X is >= 1      */
+  RD_ERR_OOM = 3,         /* a device allocation failed                                     */
+  RD_ERR_CUDA = 4,        /* a CUDA runtime call failed (text in rd_last_error)             */
+  RD_ERR_NUMERIC = 5,     /* the device saw a non-positive pivot or a non-finite Y          */
+  RD_ERR_STATE = 6,       /* call out of order                                              */
+  RD_ERR_TIMEOUT = 7,     /* a bounded device-side wait expired                             */
+  RD_ERR_UNSUPPORTED = 8  /* mode not available on this device                              */
+} rd_status;
+
+/* Precision of the dense inverse. */
+enum {
+  RD_PREC_FP64 = 0,       /* plain FP64 GEMMs throughout                                    */
+  RD_PREC_SPLIT_BF16 = 1  /* big GEMMs as exact BF16 slice products on the tensor cores,    */
+                          /* FP64 kept for diagonal blocks, slicing, recombination, decode  */
+};
+
+typedef struct {
+  int32_t n;              /* graph size                                                      */
+  int32_t n_padded;       /* N: n rounded up to the tile size                                */
+  int32_t precision;      /* RD_PREC_*                                                       */
+  int32_t slices;         /* slice count used by the split path (0 for FP64)                 */
+  double gamma;
+  double max_column_sum;  /* largest column sum of X (gamma * Delta when unweighted)         */
+  double tau;
+  double ms_factor;       /* device time of the last LU factorisation                        */
+  double ms_inverse;      /* device time of the last triangular inverses + product + decode  */
+  double ms_goal;         /* device time of the last goal solve                              */
+  double ms_greedy;       /* device time of the last greedy next-hop pass                    */
+  int64_t bytes_device;   /* device bytes owned by the handle                                */
+  int64_t launches;       /* kernel launches issued by this handle since it was created      */
+  int64_t prof_launches;  /* profiled dense-contraction launches (see rd_set_profiling)      */
+  double prof_ms;         /* their summed device time (CUDA events on the handle's stream)   */
+  double prof_flops;      /* their summed algorithmic flop count                             */
+} rd_stats;
+
+/* Create a handle for the unweighted graph A (n x n bytes) and gain gamma: validates gamma
+ * (0 < gamma < 1 and gamma * Delta < 1, Delta the largest out-degree: strict column diagonal
+ * dominance of M, which makes the no-pivot LU stable -- the condition of Theorem 4), allocates
+ * the workspace on the current device and forms M = I - gamma A (Sec. 2).  Synchronises once
+ * (to read Delta).  On success *out receives the handle; on failure *out is NULL. */
+rd_status rd_create(const uint8_t* A, int32_t n, double gamma, rd_handle* out);
+
+/* As rd_create for the weighted extension (Sec. 3.2): X_ij = gamma^W_ij where A_ij != 0,
+ * W float32 n x n, positive and finite on edges (entries off the edges are ignored).
+ * Requires the largest column sum of X to be < 1. */
+rd_status rd_create_weighted(const uint8_t* A, const float* W, int32_t n, double gamma,
+                             rd_handle* out);
+
+/* Load a new graph of the same n into an existing handle (re-validates gamma, rebuilds M,
+ * drops cached factors).  W may be NULL for an unweighted graph.  Synchronises once. */
+rd_status rd_load(rd_handle h, const uint8_t* A, const float* W, double gamma);
+
+/* Use the given cudaStream_t (passed as void*) for all later work of this handle. */
+rd_status rd_set_stream(rd_handle h, void* stream);
+
+/* Select RD_PREC_FP64 or RD_PREC_SPLIT_BF16; slices = 0 lets the library choose.
+ * Drops cached factors when the mode changes. */
+rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices);
+
+/* Change the decode snap tau (>= 0, < 0.5). */
+rd_status rd_set_tau(rd_handle h, double tau);
+
+/* All-pairs R-distance: D (n*n int32, row-major, D[i*n+j] = distance j -> i).  If Y is not
+ * NULL it also receives Y (n*n float64).  Factors M on first use and keeps the factors for
+ * rd_goal_solve. */
+rd_status rd_apsp(rd_handle h, int32_t* D, double* Y);
+
+/* Goal rows (the local mode of Sec. 4.2): for each goal g = goals[c], 0 <= c < k, writes row
+ * g of Y, Y_out[c*n + j] = Y_{g j} (the signal from j at the goal), by solving M^T y = e_g on
+ * the resident LU factors (factoring first if needed).  1 <= k <= 64; goals in [0, n). */
+rd_status rd_goal_solve(rd_handle h, const int32_t* goals, int32_t k, double* Y_out);
+
+/* Greedy next hop (Sec. 4.2, eq. descent, as ascent on Y per Theorem 4's proof): for goal
+ * g = goals[c] and node i, next[c*n + i] = g if i == g or g is a successor of i; otherwise
+ * the successor j of i (edge i -> j) with the largest Yrows[c*n + j], smallest j among equal
+ * values; -1 if i has no successor.  Yrows is the output of rd_goal_solve for the same goals
+ * (k x n). */
+rd_status rd_greedy_next(rd_handle h, const int32_t* goals, int32_t k, const double* Yrows,
+                         int32_t* next);
+
+/* Turn the per-kernel profile on (1) or off (0); either way its counters restart at zero.
+ * With the profile on, every launch of the dense-contraction (GEMM) kernels is bracketed by a
+ * pair of CUDA events on the handle's stream and its algorithmic flop count is accumulated;
+ * rd_get_stats reports the totals (prof_launches, prof_ms, prof_flops). */
+rd_status rd_set_profiling(rd_handle h, int32_t on);
+
+/* Wait for the handle's stream and return the device status (RD_OK or RD_ERR_NUMERIC). */
+rd_status rd_sync(rd_handle h);
+
+/* Copy the handle's statistics (synchronises). */
+rd_status rd_get_stats(rd_handle h, rd_stats* s);
+
+/* Text of the last error on this handle (or of the last failed rd_create when h is NULL).
+ * Valid until the next call on the handle. */
+const char* rd_last_error(rd_handle h);
+
+/* Name of a status code. */
+const char* rd_status_string(rd_status s);
+
+/* Free the handle and its device memory (synchronises its stream).  NULL is ignored. */
+void rd_destroy(rd_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RD_H_ */

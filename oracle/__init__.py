@@ -63,6 +63,7 @@ def _load():
             "rdo_inverse_from_lu": (None, [P, I64, P]),
             "rdo_goal_rows": (None, [P, I64, P, I64, P]),
             "rdo_decode": (I64, [P, I64, D, D, P]),
+            "rdo_decode_vector": (None, [P, I64, I64, D, D, P]),
             "rdo_rdistance": (I64, [P, P, I64, D, D, P, P]),
             "rdo_series_vector": (I64, [P, P, I64, D, I64, ctypes.c_int, I64, P]),
             "rdo_bfs": (ctypes.c_int, [P, I64, P, I64, P, P]),
@@ -141,6 +142,14 @@ def decode(Y: np.ndarray, gamma: float, tau: float = TAU) -> np.ndarray:
     bad = _load().rdo_decode(_ptr(Y), n, float(gamma), float(tau), _ptr(D))
     if bad:
         raise ArithmeticError(f"{bad} non-finite entries of Y")
+    return D
+
+
+def decode_vector(y, diag: int, gamma: float, tau: float = TAU) -> np.ndarray:
+    """Decode one row (or column) ``diag`` of Y."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    D = np.empty(y.size, dtype=np.int32)
+    _load().rdo_decode_vector(_ptr(y), y.size, int(diag), float(gamma), float(tau), _ptr(D))
     return D
 
 

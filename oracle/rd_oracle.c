@@ -167,6 +167,15 @@ int64_t rdo_decode(const double* Y, int64_t n, double gamma, double tau, int32_t
   return bad;
 }
 
+/* Decode one vector y of length n that is row (or column) `diag` of Y: same rule as
+ * rdo_decode, with entry `diag` forced to 0. */
+void rdo_decode_vector(const double* y, int64_t n, int64_t diag, double gamma, double tau,
+                       int32_t* D) {
+  double lg = log(gamma);
+  for (int64_t j = 0; j < n; ++j)
+    D[j] = (j == diag) ? 0 : (isfinite(y[j]) ? decode_one(y[j], lg, tau) : RDO_UNREACHABLE);
+}
+
 /* Whole method: build M, LU, inverse, decode.  Y_out may be NULL.
  * Returns 0, -1 on allocation failure, -2 on non-finite Y, or k+1 for a bad pivot k. */
 int64_t rdo_rdistance(const uint8_t* A, const float* W, int64_t n, double gamma, double tau,

@@ -1,0 +1,126 @@
+// k_build.cu -- operator build (M = I - gamma A, or I - gamma^W), the gain check, and the
+// successor lists used by the greedy next hop.
+//
+// Sec. 2 (eq. Y-defined) and Sec. 3.2 (X = gamma^W elementwise).  The gain check computes,
+// for every column j, the out-degree Delta_j = sum_i [A_ij != 0] (Theorem 2's definition of
+// Delta) and, for weighted graphs, the column sum of X; the host accepts the gain when the
+// largest column sum of X is below one (strict column diagonal dominance of M).
+//
+// All three kernels are HBM-bound streams over the n x n byte matrix (and the N x N FP64 M):
+// one thread per column walks down the rows, so a warp reads 32 consecutive bytes of a row
+// per step and writes consecutive doubles of M.
+#include "rd_internal.cuh"
+
+namespace {
+
+__global__ void build_m_kernel(const uint8_t* __restrict__ A, const float* __restrict__ W,
+                               int n, int N, double gamma, double log_gamma, double* __restrict__ M,
+                               int32_t* __restrict__ deg, unsigned long long* __restrict__ red) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;  // column of M
+  if (j >= N) return;
+  int cnt = 0;
+  double colsum = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double x = 0.0;
+    if (i < n && j < n && A[(long long)i * n + j]) {
+      ++cnt;
+      x = W ? pow(gamma, (double)W[(long long)i * n + j]) : gamma;
+      colsum += x;
+    }
+    M[(long long)i * N + j] = (i == j ? 1.0 : 0.0) - x;
+  }
+  if (j < n) {
+    deg[j] = cnt;
+    atomicMax(&red[0], (unsigned long long)cnt);
+    atomicAdd(&red[2], (unsigned long long)cnt);
+    // non-negative doubles order like their bit patterns
+    atomicMax(&red[1], (unsigned long long)__double_as_longlong(colsum));
+  }
+}
+
+// exclusive prefix sum of deg[0..n) into ptr[0..n] (single block; n is at most a few 10^5)
+__global__ void scan_kernel(const int32_t* __restrict__ deg, int n, int32_t* __restrict__ ptr) {
+  __shared__ long long part[1024];
+  const int t = threadIdx.x;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int b = t * per, e = min(n, b + per);
+  long long s = 0;
+  for (int i = b; i < e; ++i) s += deg[i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    long long run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      long long v = part[i];
+      part[i] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  long long run = part[t];
+  for (int i = b; i < e; ++i) {
+    ptr[i] = (int32_t)run;
+    run += deg[i];
+  }
+  if (e == n && b < e) ptr[n] = (int32_t)run;
+  if (n == 0 && t == 0) ptr[0] = 0;
+}
+
+// successors of node v: {j : A[j][v] != 0} (edge v -> j), ascending j
+__global__ void succ_fill_kernel(const uint8_t* __restrict__ A, int n, const int32_t* __restrict__ ptr,
+                                 int32_t* __restrict__ idx) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  int w = ptr[v];
+  for (int j = 0; j < n; ++j)
+    if (A[(long long)j * n + v]) idx[w++] = j;
+}
+
+__global__ void copy_rows_kernel(const double* __restrict__ R, long long ldr, int rows, int cols,
+                                 double* __restrict__ out, long long ldo) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * cols) return;
+  const int r = (int)(t / cols), c = (int)(t % cols);
+  out[(long long)r * ldo + c] = R[(long long)r * ldr + c];
+}
+
+}  // namespace
+
+cudaError_t rd_build_m(rd_ctx* h, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(h->dRed, 0, 3 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int threads = 128;
+  const int blocks = (h->N + threads - 1) / threads;
+  if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
+  build_m_kernel<<<blocks, threads, 0, s>>>(h->dA, h->weighted ? h->dW : nullptr, h->n, h->N,
+                                             h->gamma, log(h->gamma), h->dLU, h->dDeg, h->dRed);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return rd_prof_end(h, s, false, 0.0);
+}
+
+cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s) {
+  // ptr lives after the degrees: dDeg[0..n) degrees, dDeg[n+1 .. 2n+1] prefix
+  int32_t* ptr = h->dDeg + (h->n + 1);
+  cudaError_t e = rd_prof_begin(h, s, false);
+  if (e != cudaSuccess) return e;
+  scan_kernel<<<1, 1024, 0, s>>>(h->dDeg, h->n, ptr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, false, 0.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
+  succ_fill_kernel<<<(h->n + 127) / 128, 128, 0, s>>>(h->dA, h->n, ptr, h->dSucc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return rd_prof_end(h, s, false, 0.0);
+}
+
+cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows, int cols,
+                             double* out, long long ldo, cudaStream_t s) {
+  const long long total = (long long)rows * cols;
+  if (total == 0) return cudaSuccess;
+  const int threads = 256;
+  cudaError_t e = rd_prof_begin(h, s, false);
+  if (e != cudaSuccess) return e;
+  copy_rows_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(R, ldr, rows, cols,
+                                                                                 out, ldo);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return rd_prof_end(h, s, false, 0.0);
+}

@@ -1,0 +1,162 @@
+// k_gemm_f64.cu -- the FP64 GEMM of the plain path.
+//
+// Every dense contraction of the plain path goes through this kernel: the trailing updates and
+// the two panel products of the blocked LU, the off-diagonal products of the blocked
+// triangular inverses, the final product Y = U^-1 L^-1 (with the R-distance decode fused into
+// its epilogue), and the blocked goal solves.
+//
+// FP64 throughput on this part is two orders of magnitude below its BF16 tensor rate, so the
+// kernel is bound by the FP64 pipe whatever the tiling: a 64x64 CTA tile with a 4x4 register
+// micro-tile per thread and a 16-deep K step in shared memory keeps the pipe fed while the
+// memory traffic stays three orders of magnitude below the HBM rate.
+//
+// Operands may be read through a "triangular view" of the packed storage: the strict lower
+// part with an implied unit diagonal (L, L^-1) or the upper part including the diagonal
+// (U, U^-1).  The view also bounds the K loop: a CTA skips the K range where its row (or
+// column) strip of the triangular operand is zero, so triangular products cost what they
+// should (n^3/3 for a triangle times a full matrix).
+//
+// In-place use: C may alias A's row strip or B's column strip of the same CTA (the panel
+// products of the LU and the goal solves do this).  Every CTA reads all of its K range before
+// its epilogue writes, and reads no other CTA's output, so this is safe when beta == 0.
+#include "rd_internal.cuh"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__device__ __forceinline__ double tri_load(const double* p, long long ld, int r, int c, int tri) {
+  // r, c are indices inside the operand view; the view's diagonal is r == c
+  if (tri == RD_TRI_LOWER_UNIT) {
+    if (r < c) return 0.0;
+    if (r == c) return 1.0;
+  } else if (tri == RD_TRI_UPPER) {
+    if (r > c) return 0.0;
+  }
+  return p[(long long)r * ld + c];
+}
+
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(const rd_gemm_f64_args* __restrict__ probs_dev,
+                                                      rd_gemm_f64_args p0, rd_gemm_f64_args p1) {
+  const rd_gemm_f64_args& p = (blockIdx.z == 0) ? p0 : p1;
+  (void)probs_dev;
+  const int tiles_n = p.N / BN;
+  const int tiles = (p.M / BM) * tiles_n;
+  const int tile = blockIdx.x;
+  if (tile >= tiles) return;
+  const int r0 = (tile / tiles_n) * BM;
+  const int c0 = (tile % tiles_n) * BN;
+
+  int kbeg = 0, kend = p.K;
+  if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, r0 + BM);
+  if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, r0);
+  if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, c0);
+  if (p.b_tri == RD_TRI_UPPER) kend = min(kend, c0 + BN);
+
+  __shared__ double As[2][BK][BM];
+  __shared__ double Bs[2][BK][BN];
+
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  // global -> smem assignment: A tile 64 rows x 16 k, B tile 16 k x 64 cols, 4 elements each
+  const int a_r = tid / 4, a_k = (tid % 4) * 4;
+  const int b_k = tid / 16, b_c = (tid % 16) * 4;
+
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  double ra[4], rb[4];
+  auto load_regs = [&](int k0) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ra[e] = tri_load(p.A, p.lda, r0 + a_r, k0 + a_k + e, p.a_tri);
+      rb[e] = tri_load(p.B, p.ldb, k0 + b_k, c0 + b_c + e, p.b_tri);
+    }
+  };
+  auto store_regs = [&](int buf) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      As[buf][a_k + e][a_r] = ra[e];
+      Bs[buf][b_k][b_c + e] = rb[e];
+    }
+  };
+
+  if (kbeg < kend) {
+    load_regs(kbeg);
+    store_regs(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+      const bool more = (k0 + BK) < kend;
+      if (more) load_regs(k0 + BK);
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      if (more) {
+        store_regs(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+  // every global read of this CTA's K range has been issued and consumed before any thread
+  // reaches this barrier, so an epilogue that overwrites A's or B's strip is safe
+  __syncthreads();
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx + 16 * j;
+      double v = p.alpha * acc[i][j];
+      if (p.beta != 0.0) v = fma(p.beta, p.C[(long long)r * p.ldc + c], v);
+      if (p.store_c && r < p.c_rows && c < p.c_cols) p.C[(long long)r * p.ldc + c] = v;
+      if (p.D && r < p.d_rows && c < p.d_cols) {
+        int32_t d;
+        if (!isfinite(v)) {
+          rd_set_status(p.status, RD_DEV_NONFINITE, r);
+          d = RD_UNREACHABLE;
+        } else {
+          d = (r == c) ? 0 : rd_decode_entry(v, p.log_gamma, p.tau);
+        }
+        p.D[(long long)r * p.ldd + c] = d;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cudaStream_t s,
+                        double flops) {
+  if (nprob < 1 || nprob > 2) return cudaErrorInvalidValue;
+  int maxtiles = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const rd_gemm_f64_args& p = probs[i];
+    if (p.M % BM || p.N % BN || p.K % BK || p.M < 0 || p.N < 0 || p.K < 0)
+      return cudaErrorInvalidValue;
+    int t = (p.M / BM) * (p.N / BN);
+    if (t > maxtiles) maxtiles = t;
+  }
+  if (maxtiles == 0) return cudaSuccess;
+  dim3 grid(maxtiles, 1, nprob);
+  cudaError_t e = rd_prof_begin(h, s, true);
+  if (e != cudaSuccess) return e;
+  gemm_f64_kernel<<<grid, NT, 0, s>>>(nullptr, probs[0], nprob > 1 ? probs[1] : probs[0]);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return rd_prof_end(h, s, true, flops);
+}

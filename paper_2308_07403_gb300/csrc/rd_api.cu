@@ -1,0 +1,493 @@
+// rd_api.cu -- the C ABI declared in include/rd.h: handles, argument checks, host/device
+// pointer handling, and the order of the kernels of the path.
+//
+// Path of rd_apsp (all on the handle's stream, no host synchronisation unless an output is
+// host memory):
+//   rd_load:  copy A (and W) -> build M = I - X, degrees and column sums -> gain check (one
+//             synchronisation to read the largest column sum)
+//   factor:   blocked no-pivot LU of M (FP64, or split BF16 products on the tensor cores)
+//   inverse:  blocked triangular inverses L^-1, U^-1
+//   product:  Y = U^-1 L^-1 with D = ceil(log_gamma Y - tau) fused into the epilogue
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "rd_internal.cuh"
+
+namespace {
+
+thread_local std::string g_create_err;
+
+rd_status fail(rd_ctx* h, rd_status st, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_create_err = msg;
+  return st;
+}
+
+rd_status fail_cuda(rd_ctx* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? RD_ERR_OOM : RD_ERR_CUDA, m);
+}
+
+#define RD_CK(h, call)                                   \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return fail_cuda((h), _e, #call); \
+  } while (0)
+
+// true when p is device (or managed) memory usable by the handle's device
+bool is_device_ptr(const void* p, int device) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
+bool is_foreign_device_ptr(const void* p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device != device;
+}
+
+template <class T>
+cudaError_t dalloc(rd_ctx* h, T** p, size_t count) {
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess) h->bytes += (int64_t)bytes;
+  return e;
+}
+
+void free_all(rd_ctx* h) {
+  rd_split_release(h);
+  if (h->prof_ev) {
+    for (int i = 0; i < 2 * rd_ctx::kProfPairs; ++i)
+      if (h->prof_ev[i]) cudaEventDestroy(h->prof_ev[i]);
+    delete[] h->prof_ev;
+    h->prof_ev = nullptr;
+  }
+  void* ptrs[] = {h->dA, h->dW, h->dLU, h->dT, h->dS, h->dR, h->dStatus, h->dRed, h->dDeg,
+                  h->dSucc, h->dGoals, h->dNext, h->dYrows, h->dDout, h->dYout};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+}
+
+rd_status check_device_status(rd_ctx* h) {
+  int st[2] = {0, 0};
+  RD_CK(h, cudaMemcpyAsync(st, h->dStatus, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  RD_CK(h, cudaStreamSynchronize(h->stream));
+  if (st[0] == RD_DEV_OK) return RD_OK;
+  char buf[160];
+  if (st[0] == RD_DEV_PIVOT) {
+    snprintf(buf, sizeof buf, "non-positive pivot at row %d (gain too large for a no-pivot LU)", st[1]);
+    return fail(h, RD_ERR_NUMERIC, buf);
+  }
+  if (st[0] == RD_DEV_NONFINITE) {
+    snprintf(buf, sizeof buf, "non-finite entry of Y in row %d", st[1]);
+    return fail(h, RD_ERR_NUMERIC, buf);
+  }
+  if (st[0] == RD_DEV_TIMEOUT) return fail(h, RD_ERR_TIMEOUT, "a bounded device wait expired");
+  snprintf(buf, sizeof buf, "device status %d (detail %d)", st[0], st[1]);
+  return fail(h, RD_ERR_ARG, buf);
+}
+
+rd_status load_impl(rd_ctx* h, const uint8_t* A, const float* W, double gamma) {
+  if (!A) return fail(h, RD_ERR_ARG, "A is NULL");
+  if (!(gamma > 0.0 && gamma < 1.0) || !std::isfinite(gamma))
+    return fail(h, RD_ERR_GAMMA, "gamma must lie in (0, 1)");
+  if (is_foreign_device_ptr(A, h->device) || (W && is_foreign_device_ptr(W, h->device)))
+    return fail(h, RD_ERR_ARG, "input lives on another device");
+  const size_t nn = (size_t)h->n * (size_t)h->n;
+  RD_CK(h, cudaSetDevice(h->device));
+  RD_CK(h, cudaMemcpyAsync(h->dA, A, nn, cudaMemcpyDefault, h->stream));
+  h->weighted = W != nullptr;
+  if (W) {
+    if (!h->dW) RD_CK(h, dalloc(h, &h->dW, nn));
+    RD_CK(h, cudaMemcpyAsync(h->dW, W, nn * sizeof(float), cudaMemcpyDefault, h->stream));
+  }
+  h->gamma = gamma;
+  h->factored = h->inverted = 0;
+  h->succ_ready = 0;
+  RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 2 * sizeof(int), h->stream));
+  RD_CK(h, rd_build_m(h, h->stream));
+  unsigned long long red[3];
+  RD_CK(h, cudaMemcpyAsync(red, h->dRed, sizeof(red), cudaMemcpyDeviceToHost, h->stream));
+  RD_CK(h, cudaStreamSynchronize(h->stream));
+  if ((int64_t)red[2] > h->succ_cap) {
+    if (h->dSucc) {
+      cudaFree(h->dSucc);
+      h->bytes -= h->succ_cap * (int64_t)sizeof(int32_t);
+      h->dSucc = nullptr;
+      h->succ_cap = 0;
+    }
+    if (red[2] <= 2147483647ull) {
+      RD_CK(h, dalloc(h, &h->dSucc, (size_t)red[2]));
+      h->succ_cap = (int64_t)red[2];
+    }
+  }
+  const double delta = (double)red[0];
+  double colsum;
+  memcpy(&colsum, &red[1], sizeof(double));
+  if (!h->weighted) colsum = gamma * delta;
+  h->max_colsum = colsum;
+  if (!(colsum < 1.0) || !std::isfinite(colsum)) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "largest column sum of X is %.17g >= 1 (gamma * Delta with Delta = %.0f): M is not "
+             "strictly column diagonally dominant",
+             colsum, delta);
+    return fail(h, RD_ERR_GAMMA, buf);
+  }
+  return RD_OK;
+}
+
+rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma, rd_handle* out) {
+  if (!out) return fail(nullptr, RD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!A) return fail(nullptr, RD_ERR_ARG, "A is NULL");
+  if (n < 1) return fail(nullptr, RD_ERR_ARG, "n must be >= 1");
+  if (n > 65536) return fail(nullptr, RD_ERR_ARG, "n must be <= 65536");
+  if (!(gamma > 0.0 && gamma < 1.0) || !std::isfinite(gamma))
+    return fail(nullptr, RD_ERR_GAMMA, "gamma must lie in (0, 1)");
+  rd_ctx* h = new rd_ctx();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail_cuda(nullptr, e, "cudaGetDevice");
+  }
+  h->device = dev;
+  h->n = n;
+  h->N = (n + RD_PAD - 1) / RD_PAD * RD_PAD;
+  const size_t N = (size_t)h->N;
+  const size_t nn = (size_t)n * (size_t)n;
+  rd_status st = RD_OK;
+#define RD_ALLOC(ptr, cnt)                                  \
+  if (st == RD_OK) {                                        \
+    cudaError_t _e = dalloc(h, &(ptr), (cnt));              \
+    if (_e != cudaSuccess) st = fail_cuda(h, _e, "cudaMalloc " #ptr); \
+  }
+  RD_ALLOC(h->dA, nn);
+  RD_ALLOC(h->dLU, N * N);
+  RD_ALLOC(h->dT, N * N);
+  RD_ALLOC(h->dS, N * N / 2);
+  RD_ALLOC(h->dR, (size_t)RD_MAX_GOALS * N);
+  RD_ALLOC(h->dStatus, 2);
+  RD_ALLOC(h->dRed, 3);
+  RD_ALLOC(h->dDeg, 2 * (size_t)n + 2);
+  RD_ALLOC(h->dGoals, RD_MAX_GOALS);
+#undef RD_ALLOC
+  for (auto& ev : h->ev)
+    if (st == RD_OK) {
+      cudaError_t e2 = cudaEventCreate(&ev);
+      if (e2 != cudaSuccess) st = fail_cuda(h, e2, "cudaEventCreate");
+    }
+  if (st == RD_OK) st = load_impl(h, A, W, gamma);
+  if (st != RD_OK) {
+    g_create_err = h->err;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return RD_OK;
+}
+
+rd_status ensure_factored(rd_ctx* h) {
+  if (h->factored) return RD_OK;
+  RD_CK(h, cudaEventRecord(h->ev[0], h->stream));
+  if (h->precision == RD_PREC_SPLIT_BF16) {
+    rd_status st = rd_split_prepare(h);
+    if (st != RD_OK) return st;
+    RD_CK(h, rd_lu_split(h, h->stream));
+  } else {
+    RD_CK(h, rd_lu_f64(h, h->stream));
+  }
+  RD_CK(h, cudaEventRecord(h->ev[1], h->stream));
+  h->ev_used[0] = 1;
+  h->factored = 1;
+  h->inverted = 0;
+  return RD_OK;
+}
+
+rd_status ensure_goals(rd_ctx* h, const int32_t* goals, int32_t k) {
+  if (!goals) return fail(h, RD_ERR_ARG, "goals is NULL");
+  if (k < 1 || k > RD_MAX_GOALS) return fail(h, RD_ERR_ARG, "k must lie in [1, 64]");
+  if (!is_device_ptr(goals, h->device)) {
+    for (int c = 0; c < k; ++c)
+      if (goals[c] < 0 || goals[c] >= h->n) return fail(h, RD_ERR_ARG, "goal index out of range");
+  }
+  RD_CK(h, cudaMemcpyAsync(h->dGoals, goals, k * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+  return RD_OK;
+}
+
+double event_ms(rd_ctx* h, int slot) {
+  float ms = 0.f;
+  if (!h->ev_used[slot]) return 0.0;
+  if (cudaEventElapsedTime(&ms, h->ev[2 * slot], h->ev[2 * slot + 1]) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return ms;
+}
+
+}  // namespace
+
+cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, bool contraction) {
+  h->launches++;
+  if (!h->prof_on || !contraction) return cudaSuccess;
+  if (h->prof_used == rd_ctx::kProfPairs) {
+    cudaError_t e = rd_prof_collect(h);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaEventRecord(h->prof_ev[2 * h->prof_used], s);
+}
+
+cudaError_t rd_prof_end(rd_ctx* h, cudaStream_t s, bool contraction, double flops) {
+  if (!h->prof_on || !contraction) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
+  if (e != cudaSuccess) return e;
+  h->prof_used++;
+  h->prof_pending_flops += flops;
+  return cudaSuccess;
+}
+
+cudaError_t rd_prof_collect(rd_ctx* h) {
+  if (!h->prof_ev || h->prof_used == 0) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(h->prof_ev[2 * h->prof_used - 1]);
+  if (e != cudaSuccess) return e;
+  double sum = 0.0;
+  for (int i = 0; i < h->prof_used; ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]);
+    if (e != cudaSuccess) return e;
+    sum += ms;
+  }
+  h->prof_ms += sum;
+  h->prof_flops += h->prof_pending_flops;
+  h->prof_launches += h->prof_used;
+  h->prof_pending_flops = 0.0;
+  h->prof_used = 0;
+  return cudaSuccess;
+}
+
+extern "C" {
+
+rd_status rd_set_profiling(rd_handle h, int32_t on) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  RD_CK(h, cudaSetDevice(h->device));
+  if (on && !h->prof_ev) {
+    h->prof_ev = new cudaEvent_t[2 * rd_ctx::kProfPairs]();
+    for (int i = 0; i < 2 * rd_ctx::kProfPairs; ++i) RD_CK(h, cudaEventCreate(&h->prof_ev[i]));
+  }
+  RD_CK(h, cudaStreamSynchronize(h->stream));
+  h->prof_on = on ? 1 : 0;
+  h->prof_used = 0;
+  h->prof_ms = h->prof_flops = h->prof_pending_flops = 0.0;
+  h->prof_launches = 0;
+  return RD_OK;
+}
+
+rd_status rd_create(const uint8_t* A, int32_t n, double gamma, rd_handle* out) {
+  return create_impl(A, nullptr, n, gamma, out);
+}
+
+rd_status rd_create_weighted(const uint8_t* A, const float* W, int32_t n, double gamma, rd_handle* out) {
+  if (!W) {
+    if (out) *out = nullptr;
+    return fail(nullptr, RD_ERR_ARG, "W is NULL");
+  }
+  return create_impl(A, W, n, gamma, out);
+}
+
+rd_status rd_load(rd_handle h, const uint8_t* A, const float* W, double gamma) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  return load_impl(h, A, W, gamma);
+}
+
+rd_status rd_set_stream(rd_handle h, void* stream) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  h->stream = (cudaStream_t)stream;
+  return RD_OK;
+}
+
+rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  if (mode != RD_PREC_FP64 && mode != RD_PREC_SPLIT_BF16) return fail(h, RD_ERR_ARG, "unknown precision mode");
+  if (slices < 0 || slices > 16) return fail(h, RD_ERR_ARG, "slices must lie in [0, 16]");
+  if (mode != h->precision || slices != h->slices_req) {
+    if (h->factored) {
+      // the factors in dLU belong to the old mode: rebuild M from the resident graph
+      RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 2 * sizeof(int), h->stream));
+      RD_CK(h, rd_build_m(h, h->stream));
+    }
+    h->factored = h->inverted = 0;
+  }
+  h->precision = mode;
+  h->slices_req = slices;
+  return RD_OK;
+}
+
+rd_status rd_set_tau(rd_handle h, double tau) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  if (!(tau >= 0.0 && tau < 0.5)) return fail(h, RD_ERR_ARG, "tau must lie in [0, 0.5)");
+  h->tau = tau;
+  return RD_OK;
+}
+
+rd_status rd_apsp(rd_handle h, int32_t* D, double* Y) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  if (!D) return fail(h, RD_ERR_ARG, "D is NULL");
+  if (is_foreign_device_ptr(D, h->device) || (Y && is_foreign_device_ptr(Y, h->device)))
+    return fail(h, RD_ERR_ARG, "output lives on another device");
+  RD_CK(h, cudaSetDevice(h->device));
+  rd_status st = ensure_factored(h);
+  if (st != RD_OK) return st;
+  const size_t nn = (size_t)h->n * (size_t)h->n;
+  const bool d_host = !is_device_ptr(D, h->device);
+  const bool y_host = Y && !is_device_ptr(Y, h->device);
+  if (d_host && !h->dDout) RD_CK(h, dalloc(h, &h->dDout, nn));
+  if (y_host && !h->dYout) RD_CK(h, dalloc(h, &h->dYout, nn));
+  int32_t* dD = d_host ? h->dDout : D;
+  double* dY = Y ? (y_host ? h->dYout : Y) : nullptr;
+  RD_CK(h, cudaEventRecord(h->ev[2], h->stream));
+  if (h->precision == RD_PREC_SPLIT_BF16) {
+    if (!h->inverted) RD_CK(h, rd_trtri_split(h, h->stream));
+    h->inverted = 1;
+    RD_CK(h, rd_trmm_decode_split(h, dD, dY, h->stream));
+  } else {
+    if (!h->inverted) RD_CK(h, rd_trtri_f64(h, h->stream));
+    h->inverted = 1;
+    RD_CK(h, rd_trmm_decode_f64(h, dD, dY, h->stream));
+  }
+  RD_CK(h, cudaEventRecord(h->ev[3], h->stream));
+  h->ev_used[1] = 1;
+  if (d_host) RD_CK(h, cudaMemcpyAsync(D, dD, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  if (y_host) RD_CK(h, cudaMemcpyAsync(Y, dY, nn * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (d_host || y_host) return check_device_status(h);
+  return RD_OK;
+}
+
+rd_status rd_goal_solve(rd_handle h, const int32_t* goals, int32_t k, double* Y_out) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  if (!Y_out) return fail(h, RD_ERR_ARG, "Y_out is NULL");
+  RD_CK(h, cudaSetDevice(h->device));
+  rd_status st = ensure_goals(h, goals, k);
+  if (st != RD_OK) return st;
+  st = ensure_factored(h);
+  if (st != RD_OK) return st;
+  const bool host = !is_device_ptr(Y_out, h->device);
+  if (host && !h->dYrows) RD_CK(h, dalloc(h, &h->dYrows, (size_t)RD_MAX_GOALS * h->n));
+  double* dst = host ? h->dYrows : Y_out;
+  RD_CK(h, cudaEventRecord(h->ev[4], h->stream));
+  RD_CK(h, rd_goal_f64(h, h->dGoals, k, dst, h->stream));
+  RD_CK(h, cudaEventRecord(h->ev[5], h->stream));
+  h->ev_used[2] = 1;
+  if (host) {
+    RD_CK(h, cudaMemcpyAsync(Y_out, dst, (size_t)k * h->n * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+    return check_device_status(h);
+  }
+  return RD_OK;
+}
+
+rd_status rd_greedy_next(rd_handle h, const int32_t* goals, int32_t k, const double* Yrows, int32_t* next) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  if (!Yrows || !next) return fail(h, RD_ERR_ARG, "Yrows and next must not be NULL");
+  RD_CK(h, cudaSetDevice(h->device));
+  rd_status st = ensure_goals(h, goals, k);
+  if (st != RD_OK) return st;
+  if (!h->dSucc) return fail(h, RD_ERR_UNSUPPORTED, "too many edges for int32 successor lists");
+  if (!h->succ_ready) {
+    // successor lists (CSR of the columns of A), sized at load from the edge count
+    RD_CK(h, rd_build_succ(h, h->stream));
+    h->succ_ready = 1;
+  }
+  const size_t kn = (size_t)k * h->n;
+  const bool y_host = !is_device_ptr(Yrows, h->device);
+  const bool n_host = !is_device_ptr(next, h->device);
+  if (y_host) {
+    if (!h->dYrows) RD_CK(h, dalloc(h, &h->dYrows, (size_t)RD_MAX_GOALS * h->n));
+    RD_CK(h, cudaMemcpyAsync(h->dYrows, Yrows, kn * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  }
+  if (n_host && !h->dNext) RD_CK(h, dalloc(h, &h->dNext, (size_t)RD_MAX_GOALS * h->n));
+  int32_t* dn = n_host ? h->dNext : next;
+  RD_CK(h, cudaEventRecord(h->ev[6], h->stream));
+  RD_CK(h, rd_greedy(h, h->dGoals, k, y_host ? h->dYrows : Yrows, dn, h->stream));
+  RD_CK(h, cudaEventRecord(h->ev[7], h->stream));
+  h->ev_used[3] = 1;
+  if (n_host) {
+    RD_CK(h, cudaMemcpyAsync(next, dn, kn * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    return check_device_status(h);
+  }
+  return RD_OK;
+}
+
+rd_status rd_sync(rd_handle h) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  return check_device_status(h);
+}
+
+rd_status rd_get_stats(rd_handle h, rd_stats* s) {
+  if (!h || !s) return fail(h, RD_ERR_ARG, "NULL argument");
+  rd_status st = check_device_status(h);
+  s->n = h->n;
+  s->n_padded = h->N;
+  s->precision = h->precision;
+  s->slices = h->precision == RD_PREC_SPLIT_BF16 ? h->slices : 0;
+  s->gamma = h->gamma;
+  s->max_column_sum = h->max_colsum;
+  s->tau = h->tau;
+  s->ms_factor = event_ms(h, 0);
+  s->ms_inverse = event_ms(h, 1);
+  s->ms_goal = event_ms(h, 2);
+  s->ms_greedy = event_ms(h, 3);
+  s->bytes_device = h->bytes;
+  cudaError_t e = rd_prof_collect(h);
+  if (e != cudaSuccess) return fail_cuda(h, e, "rd_prof_collect");
+  s->launches = h->launches;
+  s->prof_launches = h->prof_launches;
+  s->prof_ms = h->prof_ms;
+  s->prof_flops = h->prof_flops;
+  return st;
+}
+
+const char* rd_last_error(rd_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+const char* rd_status_string(rd_status s) {
+  switch (s) {
+    case RD_OK: return "RD_OK";
+    case RD_ERR_ARG: return "RD_ERR_ARG";
+    case RD_ERR_GAMMA: return "RD_ERR_GAMMA";
+    case RD_ERR_OOM: return "RD_ERR_OOM";
+    case RD_ERR_CUDA: return "RD_ERR_CUDA";
+    case RD_ERR_NUMERIC: return "RD_ERR_NUMERIC";
+    case RD_ERR_STATE: return "RD_ERR_STATE";
+    case RD_ERR_TIMEOUT: return "RD_ERR_TIMEOUT";
+    case RD_ERR_UNSUPPORTED: return "RD_ERR_UNSUPPORTED";
+  }
+  return "RD_ERR_UNKNOWN";
+}
+
+void rd_destroy(rd_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// rd_internal.cuh -- handle layout and kernel launchers shared by the library's .cu files.
+//
+// Data layout in HBM (N = n rounded up to RD_PAD):
+//   dLU  N x N f64  M, then its packed no-pivot LU factors (strict lower = L, upper = U).
+//                   Rows/columns n..N-1 hold an identity block, so every kernel works on
+//                   whole tiles and the padding never changes the n x n result.
+//   dT   N x N f64  the triangular inverses, packed the same way: strict lower = L^-1
+//                   (unit diagonal implied), upper = U^-1.
+//   dS   N*N/2 f64  scratch for the off-diagonal products of the blocked triangular inverse.
+//   dR   64 x N f64 right-hand sides of the goal solves.
+//   dA   n x n u8   the graph (kept for reloads and the successor lists).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "rd.h"
+
+#define RD_PAD 128          // padding granule of N (the largest tile edge used)
+#define RD_BF 64            // block size of the FP64 factorisation
+#define RD_MAX_GOALS 64
+
+// device status codes (first error wins)
+#define RD_DEV_OK 0
+#define RD_DEV_PIVOT 1      // non-positive or non-finite pivot
+#define RD_DEV_NONFINITE 2  // non-finite entry of Y
+#define RD_DEV_TIMEOUT 3    // a bounded wait expired
+
+struct rd_split_plan;       // defined by the split path
+
+struct rd_ctx {
+  int device = 0;
+  int32_t n = 0, N = 0;
+  double gamma = 0.0, tau = 1e-9, max_colsum = 0.0;
+  int weighted = 0;
+  int precision = RD_PREC_FP64;
+  int slices_req = 0, slices = 0;
+  cudaStream_t stream = nullptr;
+
+  uint8_t* dA = nullptr;
+  float* dW = nullptr;
+  double* dLU = nullptr;
+  double* dT = nullptr;
+  double* dS = nullptr;
+  double* dR = nullptr;
+  int* dStatus = nullptr;      // [0] code, [1] detail
+  unsigned long long* dRed = nullptr;  // reductions: [0] max degree, [1] max column sum bits
+  int32_t* dDeg = nullptr;     // n+1: out-degree, then exclusive prefix (successor CSR ptr)
+  int32_t* dSucc = nullptr;    // successor CSR indices
+  int64_t succ_cap = 0;
+  int succ_ready = 0;
+  int32_t* dGoals = nullptr;   // RD_MAX_GOALS
+  int32_t* dNext = nullptr;    // staging for host next-hop output (k x n)
+  double* dYrows = nullptr;    // staging for host goal rows (k x n)
+  int32_t* dDout = nullptr;    // staging for host D output (n x n), lazy
+  double* dYout = nullptr;     // staging for host Y output (n x n), lazy
+
+  int factored = 0;            // dLU holds the factors of the current graph
+  int inverted = 0;            // dT holds the triangular inverses
+
+  rd_split_plan* split = nullptr;
+
+  cudaEvent_t ev[8] = {};
+  int ev_used[4] = {0, 0, 0, 0};
+  double ms_factor = 0, ms_inverse = 0, ms_goal = 0, ms_greedy = 0;
+  int64_t bytes = 0;
+  std::string err;
+
+  // launch accounting: every kernel launch of the library bumps `launches`; with profiling on,
+  // each launch of the dense-contraction kernels is bracketed by a pair of events and its
+  // algorithmic flop count is accumulated.
+  int64_t launches = 0;
+  int prof_on = 0;
+  static constexpr int kProfPairs = 4096;
+  cudaEvent_t* prof_ev = nullptr;  // 2 * kProfPairs
+  int prof_used = 0;
+  double prof_ms = 0.0, prof_flops = 0.0, prof_pending_flops = 0.0;
+  int64_t prof_launches = 0;
+};
+
+// Launch accounting around one kernel launch (see rd_ctx).  `contraction` marks the dense
+// GEMM kernels whose time and algorithmic flops are profiled.
+cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, bool contraction);
+cudaError_t rd_prof_end(rd_ctx* h, cudaStream_t s, bool contraction, double flops);
+cudaError_t rd_prof_collect(rd_ctx* h);  // fold finished event pairs into prof_ms
+
+// ---- FP64 GEMM (k_gemm_f64.cu) ----------------------------------------------------------
+// C = beta*C + alpha * opA(A) * opB(B), all row-major, M, N multiples of 64, K multiple of 16.
+// tri modes describe how a diagonal block of the packed triangular storage is read.
+enum { RD_TRI_FULL = 0, RD_TRI_LOWER_UNIT = 1, RD_TRI_UPPER = 2 };
+
+struct rd_gemm_f64_args {
+  const double* A;
+  long long lda;
+  int a_tri;
+  const double* B;
+  long long ldb;
+  int b_tri;
+  double* C;
+  long long ldc;
+  int M, N, K;
+  double alpha, beta;
+  int store_c;           // write C (rows < c_rows, cols < c_cols)
+  int c_rows, c_cols;
+  // fused R-distance decode of the result (trmm epilogue); D == nullptr disables it
+  int32_t* D;
+  long long ldd;
+  int d_rows, d_cols;
+  double log_gamma, tau;
+  int* status;
+};
+
+// flops: algorithmic flop count of the launch (for the profile), computed by the caller
+cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cudaStream_t s,
+                        double flops);
+
+// ---- kernels in k_build.cu ----------------------------------------------------------------
+cudaError_t rd_build_m(rd_ctx* h, cudaStream_t s);       // M into dLU, degrees, column sums
+cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s);    // successor CSR from dA
+cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows, int cols,
+                             double* out, long long ldo, cudaStream_t s);
+
+// ---- FP64 factorisation and inverse (k_lu_f64.cu) --------------------------------------------
+cudaError_t rd_lu_f64(rd_ctx* h, cudaStream_t s);
+cudaError_t rd_trtri_f64(rd_ctx* h, cudaStream_t s);
+cudaError_t rd_lu_diag(rd_ctx* h, int k0, cudaStream_t s);   // diag LU + its inverses
+cudaError_t rd_trmm_decode_f64(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s);
+
+// ---- goals (k_goal.cu) ---------------------------------------------------------------------
+cudaError_t rd_goal_f64(rd_ctx* h, const int32_t* dgoals, int k, double* out, cudaStream_t s);
+cudaError_t rd_greedy(rd_ctx* h, const int32_t* dgoals, int k, const double* yrows,
+                      int32_t* next, cudaStream_t s);
+
+// ---- split path (k_split.cu) -----------------------------------------------------------------
+rd_status rd_split_prepare(rd_ctx* h);
+void rd_split_release(rd_ctx* h);
+cudaError_t rd_lu_split(rd_ctx* h, cudaStream_t s);
+cudaError_t rd_trtri_split(rd_ctx* h, cudaStream_t s);
+cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s);
+
+// ---- device decode shared by the epilogues -----------------------------------------------------
+__device__ __forceinline__ int32_t rd_decode_entry(double y, double log_gamma, double tau) {
+  if (!(y > 0.0)) return RD_UNREACHABLE;
+  double r = log(y) / log_gamma - tau;
+  double c = ceil(r);
+  if (c >= 2147483646.0) return RD_UNREACHABLE - 1;
+  if (c <= -2147483647.0) return -2147483647;
+  return (int32_t)c;
+}
+
+__device__ __forceinline__ void rd_set_status(int* status, int code, int detail) {
+  if (status && atomicCAS(status, 0, code) == 0) status[1] = detail;
+}

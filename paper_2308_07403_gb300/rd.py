@@ -1,0 +1,258 @@
+"""Python binding of librd.so (include/rd.h): argument marshalling only.
+
+Every function below has the name of the C entry point it calls and forwards plain pointers
+and sizes.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays; CUDA tensors are passed
+as device pointers, everything else as host pointers (the library copies host data itself).
+No step of the R-distance runs in Python: if librd.so is missing the import of the library
+fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librd.so")
+
+RD_OK = 0
+RD_ERR_ARG = 1
+RD_ERR_GAMMA = 2
+RD_ERR_OOM = 3
+RD_ERR_CUDA = 4
+RD_ERR_NUMERIC = 5
+RD_ERR_STATE = 6
+RD_ERR_TIMEOUT = 7
+RD_ERR_UNSUPPORTED = 8
+
+RD_PREC_FP64 = 0
+RD_PREC_SPLIT_BF16 = 1
+RD_UNREACHABLE = 2**31 - 1
+MAX_GOALS = 64
+
+# every symbol declared in include/rd.h, with its ctypes signature
+_P = ctypes.c_void_p
+_SIGS = {
+    "rd_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(_P)]),
+    "rd_create_weighted": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(_P)]),
+    "rd_load": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "rd_set_stream": (ctypes.c_int, [_P, _P]),
+    "rd_set_precision": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "rd_set_tau": (ctypes.c_int, [_P, ctypes.c_double]),
+    "rd_apsp": (ctypes.c_int, [_P, _P, _P]),
+    "rd_goal_solve": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
+    "rd_greedy_next": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "rd_set_profiling": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "rd_sync": (ctypes.c_int, [_P]),
+    "rd_get_stats": (ctypes.c_int, [_P, _P]),
+    "rd_last_error": (ctypes.c_char_p, [_P]),
+    "rd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rd_destroy": (None, [_P]),
+}
+
+
+class rd_stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("n_padded", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("slices", ctypes.c_int32), ("gamma", ctypes.c_double), ("max_column_sum", ctypes.c_double),
+        ("tau", ctypes.c_double), ("ms_factor", ctypes.c_double), ("ms_inverse", ctypes.c_double),
+        ("ms_goal", ctypes.c_double), ("ms_greedy", ctypes.c_double), ("bytes_device", ctypes.c_int64),
+        ("launches", ctypes.c_int64), ("prof_launches", ctypes.c_int64), ("prof_ms", ctypes.c_double),
+        ("prof_flops", ctypes.c_double),
+    ]
+
+
+class RDError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_string(status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load librd.so (built by paper_2308_07403_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"{p} is missing: build it with `python -m paper_2308_07403_gb300.build` "
+                          "(or __graft_entry__.build())")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def status_string(st: int) -> str:
+    return load().rd_status_string(int(st)).decode()
+
+
+def _check(st: int, h=None):
+    if st != RD_OK:
+        msg = load().rd_last_error(h).decode(errors="replace")
+        raise RDError(st, msg)
+
+
+def _ptr(x):
+    """(pointer, keepalive) of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data_as(ctypes.c_void_p), a
+
+
+def _np_out(x):
+    if isinstance(x, np.ndarray) and not x.flags.c_contiguous:
+        raise ValueError("output arrays must be C-contiguous")
+
+
+# ---- entry points (same names as the C ABI) -------------------------------------------------
+
+def rd_create(A, n: int, gamma: float):
+    h = ctypes.c_void_p()
+    pa, keep = _ptr(A)
+    _check(load().rd_create(pa, int(n), float(gamma), ctypes.byref(h)))
+    del keep
+    return h
+
+
+def rd_create_weighted(A, W, n: int, gamma: float):
+    h = ctypes.c_void_p()
+    pa, ka = _ptr(A)
+    pw, kw = _ptr(W)
+    _check(load().rd_create_weighted(pa, pw, int(n), float(gamma), ctypes.byref(h)))
+    del ka, kw
+    return h
+
+
+def rd_load(h, A, W, gamma: float):
+    pa, ka = _ptr(A)
+    pw, kw = _ptr(W)
+    _check(load().rd_load(h, pa, pw, float(gamma)), h)
+
+
+def rd_set_stream(h, stream_ptr: int):
+    _check(load().rd_set_stream(h, ctypes.c_void_p(int(stream_ptr))), h)
+
+
+def rd_set_precision(h, mode: int, slices: int = 0):
+    _check(load().rd_set_precision(h, int(mode), int(slices)), h)
+
+
+def rd_set_tau(h, tau: float):
+    _check(load().rd_set_tau(h, float(tau)), h)
+
+
+def rd_apsp(h, D, Y=None):
+    _np_out(D)
+    _np_out(Y)
+    pd, kd = _ptr(D)
+    py, ky = _ptr(Y)
+    _check(load().rd_apsp(h, pd, py), h)
+
+
+def rd_goal_solve(h, goals, k: int, Y_out):
+    _np_out(Y_out)
+    pg, kg = _ptr(goals)
+    py, ky = _ptr(Y_out)
+    _check(load().rd_goal_solve(h, pg, int(k), py), h)
+
+
+def rd_greedy_next(h, goals, k: int, Yrows, nxt):
+    _np_out(nxt)
+    pg, kg = _ptr(goals)
+    py, ky = _ptr(Yrows)
+    pn, kn = _ptr(nxt)
+    _check(load().rd_greedy_next(h, pg, int(k), py, pn), h)
+
+
+def rd_set_profiling(h, on: bool):
+    _check(load().rd_set_profiling(h, int(bool(on))), h)
+
+
+def rd_sync(h):
+    _check(load().rd_sync(h), h)
+
+
+def rd_get_stats(h) -> dict:
+    s = rd_stats()
+    _check(load().rd_get_stats(h, ctypes.byref(s)), h)
+    return {name: getattr(s, name) for name, _ in rd_stats._fields_}
+
+
+def rd_last_error(h=None) -> str:
+    return load().rd_last_error(h).decode(errors="replace")
+
+
+def rd_destroy(h):
+    if h:
+        load().rd_destroy(h)
+
+
+# ---- convenience wrapper ---------------------------------------------------------------------
+
+class Handle:
+    """Owns one rd_handle; methods forward to the entry points above."""
+
+    def __init__(self, A, gamma: float, W=None, stream=None):
+        n = int(A.shape[0])
+        self.n = n
+        self.h = rd_create(A, n, gamma) if W is None else rd_create_weighted(A, W, n, gamma)
+        if stream is not None:
+            rd_set_stream(self.h, stream)
+
+    def load(self, A, gamma, W=None):
+        rd_load(self.h, A, W, gamma)
+
+    def set_precision(self, mode, slices=0):
+        rd_set_precision(self.h, mode, slices)
+
+    def apsp(self, D, Y=None):
+        rd_apsp(self.h, D, Y)
+        return D
+
+    def goal_solve(self, goals, Y_out):
+        rd_goal_solve(self.h, goals, int(goals.shape[0]), Y_out)
+        return Y_out
+
+    def greedy_next(self, goals, Yrows, nxt):
+        rd_greedy_next(self.h, goals, int(goals.shape[0]), Yrows, nxt)
+        return nxt
+
+    def sync(self):
+        rd_sync(self.h)
+
+    def stats(self):
+        return rd_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            rd_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,97 @@
+"""Full-size parity at n = 8192, in the launch configuration bench.py times.
+
+For each of the six n = 8192 workloads (ER p=0.01, 90x91 grid, WS ring k=10 beta=0.1, gain
+0.5 and 0.9 of 1/Delta):
+  * D from the CUDA path must hash to the D the CPU oracle produced (tests/golden, written by
+    tests/golden/make_golden.py from oracle/ only); on a mismatch the 64-row block hashes
+    locate it and the test reports the count.
+  * Sampled rows and columns of Y must match the oracle's series fixpoint (a different
+    algorithm: partial sums of sum_k gamma^k A^k, Sec. 3.1) within a relative 1e-11, and
+    the decoded sampled rows must equal the GPU's D rows.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_07403_gb300 import graphs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden")
+CASES = [(k, f) for k in graphs.LARGE_KINDS for f in graphs.LARGE_FRACS]
+
+
+@pytest.fixture(scope="module")
+def rd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_07403_gb300 import build
+    from paper_2308_07403_gb300 import rd as _rd
+
+    build.build()
+    _rd.load()
+    return _rd
+
+
+@pytest.fixture(scope="module")
+def bufs():
+    n = 8192
+    return {"D": torch.empty((n, n), dtype=torch.int32, device="cuda"),
+            "Y": torch.empty((n, n), dtype=torch.float64, device="cuda")}
+
+
+def gold(kind, frac):
+    p = os.path.join(GOLDEN, f"large_{kind}_{frac}.json")
+    if not os.path.exists(p):
+        pytest.skip(f"golden file {p} missing")
+    with open(p) as f:
+        return json.load(f)
+
+
+def check_against_golden(Dh, rec):
+    full = hashlib.sha256(np.ascontiguousarray(Dh, dtype="<i4").tobytes()).hexdigest()
+    if full == rec["sha256_D"]:
+        return 0
+    bad_blocks = []
+    B = rec["block_rows"]
+    for b, hx in enumerate(rec["block_sha256_16"]):
+        got = hashlib.sha256(np.ascontiguousarray(Dh[b * B:(b + 1) * B], dtype="<i4").tobytes()).hexdigest()[:16]
+        if got != hx:
+            bad_blocks.append(b)
+    return bad_blocks
+
+
+@pytest.mark.parametrize("kind,frac", CASES)
+def test_full_size_fp64(rd, bufs, kind, frac):
+    rec = gold(kind, frac)
+    A, g = graphs.workload_large(kind, frac)
+    assert repr(g) == rec["gamma"]
+    n = A.shape[0]
+    D, Y = bufs["D"], bufs["Y"]
+    At = torch.from_numpy(A).cuda()
+    with rd.Handle(At, g, stream=torch.cuda.current_stream().cuda_stream) as h:
+        h.apsp(D, Y)
+        h.sync()
+    torch.cuda.synchronize()
+    Dh = D.cpu().numpy()
+    bad = check_against_golden(Dh, rec)
+    assert bad == 0, f"{len(bad)} row blocks of D differ from the oracle's: {bad[:10]}"
+    rng = np.random.default_rng(hash((kind, frac)) % 2**32)
+    for idx in rng.choice(n, size=3, replace=False):
+        row, _ = oracle.series_vector(A, g, int(idx), transpose=True)
+        col, _ = oracle.series_vector(A, g, int(idx), transpose=False)
+        yr = Y[int(idx)].cpu().numpy()
+        yc = Y[:, int(idx)].cpu().numpy()
+        for ref, got in ((row, yr), (col, yc)):
+            assert np.array_equal(ref == 0, got == 0)
+            nz = ref != 0
+            err = np.max(np.abs(got[nz] - ref[nz]) / ref[nz])
+            assert err < 1e-11, err
+        assert np.array_equal(oracle.decode_vector(row, int(idx), g), Dh[int(idx)])
+        assert np.array_equal(oracle.decode_vector(col, int(idx), g), Dh[:, int(idx)])

@@ -348,3 +348,12 @@ def test_planted_sign_is_caught(oracle_lib):
     Y = oracle.inverse(graphs.complete(n), -g)
     off = g / ((1 + g) * (1 - (n - 1) * g))
     assert abs(Y[0, 1] - off) / off > 1e-3
+
+
+def test_decode_vector_matches_matrix_decode(oracle_lib):
+    A = graphs.er(90, 0.05, 4)
+    g = graphs.gamma_frac(A, 0.9)
+    D, Y = oracle.rdistance(A, g, want_y=True)
+    for i in (0, 45, 89):
+        assert np.array_equal(oracle.decode_vector(Y[i], i, g), D[i])
+        assert np.array_equal(oracle.decode_vector(Y[:, i], i, g), D[:, i])
