@@ -148,8 +148,9 @@ rd_status rd_sync(rd_handle h);
 /* Copy the handle's statistics (synchronises). */
 rd_status rd_get_stats(rd_handle h, rd_stats* s);
 
-/* Text of the last error on this handle (or of the last failed rd_create when h is NULL).
- * Valid until the next call on the handle. */
+/* Text of the last error on this handle (or, when h is NULL, of the last failed call made
+ * without a handle: rd_create, rd_create_weighted, rd_apsp_noalloc).  Valid until the next
+ * call on the handle. */
 const char* rd_last_error(rd_handle h);
 
 /* Name of a status code. */
@@ -157,6 +158,29 @@ const char* rd_status_string(rd_status s);
 
 /* Free the handle and its device memory (synchronises its stream).  NULL is ignored. */
 void rd_destroy(rd_handle h);
+
+/* Largest n accepted by rd_apsp_noalloc. */
+#define RD_NOALLOC_MAX_N 512
+
+/* All-pairs R-distance (the same FP64 kernels and result as rd_create + rd_apsp) for callers
+ * that must not allocate device memory: for example a host program whose device memory is
+ * handed out up front by another runtime or framework, or code that runs inside another
+ * system's time-critical loop, where cudaMalloc is not allowed or its implicit device
+ * synchronisation is not acceptable.  The paper has no counterpart; this is a deployment
+ * variant of the library.
+ *
+ * No handle and no allocation: the workspace is a fixed array in device memory that the
+ * library declares at file scope (about 5.3 MB, sized for n <= RD_NOALLOC_MAX_N); every GPU
+ * that loads the library holds it until the process exits.  A (n x n bytes) and D (n x n
+ * int32) must be device memory of the current device, owned by the caller; the work runs on
+ * `stream` (a cudaStream_t, NULL for the default stream) and the call waits for it.
+ * n > RD_NOALLOC_MAX_N returns RD_ERR_ARG without touching the GPU.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture.  All calls share the one
+ * array: each call resets what must start at zero and overwrites the rest, and calls whose
+ * GPU work overlaps (other threads, other streams) race on it and must be serialised by the
+ * caller.  Errors are readable with rd_last_error(NULL). */
+rd_status rd_apsp_noalloc(const uint8_t* A, int32_t n, double gamma, int32_t* D, void* stream);
 
 #ifdef __cplusplus
 }

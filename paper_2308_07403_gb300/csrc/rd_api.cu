@@ -246,6 +246,8 @@ double event_ms(rd_ctx* h, int slot) {
 
 }  // namespace
 
+void rd_record_error(const std::string& msg) { g_create_err = msg; }
+
 cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, bool contraction) {
   h->launches++;
   if (!h->prof_on || !contraction) return cudaSuccess;

@@ -140,6 +140,9 @@ cudaError_t rd_lu_split(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_trtri_split(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s);
 
+// ---- errors of calls without a handle (read back through rd_last_error(NULL)) -----------------
+void rd_record_error(const std::string& msg);
+
 // ---- device decode shared by the epilogues -----------------------------------------------------
 __device__ __forceinline__ int32_t rd_decode_entry(double y, double log_gamma, double tau) {
   if (!(y > 0.0)) return RD_UNREACHABLE;

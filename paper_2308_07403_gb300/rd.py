@@ -30,6 +30,7 @@ RD_PREC_FP64 = 0
 RD_PREC_SPLIT_BF16 = 1
 RD_UNREACHABLE = 2**31 - 1
 MAX_GOALS = 64
+NOALLOC_MAX_N = 512
 
 # every symbol declared in include/rd.h, with its ctypes signature
 _P = ctypes.c_void_p
@@ -49,6 +50,7 @@ _SIGS = {
     "rd_last_error": (ctypes.c_char_p, [_P]),
     "rd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rd_destroy": (None, [_P]),
+    "rd_apsp_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, _P, _P]),
 }
 
 
@@ -202,6 +204,13 @@ def rd_last_error(h=None) -> str:
 def rd_destroy(h):
     if h:
         load().rd_destroy(h)
+
+
+def rd_apsp_noalloc(A, n: int, gamma: float, D, stream_ptr: int = 0):
+    """APSP without any device allocation (device A and D, n <= NOALLOC_MAX_N)."""
+    pa, ka = _ptr(A)
+    pd, kd = _ptr(D)
+    _check(load().rd_apsp_noalloc(pa, int(n), float(gamma), pd, ctypes.c_void_p(int(stream_ptr))))
 
 
 # ---- convenience wrapper ---------------------------------------------------------------------
