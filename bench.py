@@ -35,8 +35,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "n=8192 R-distance APSP time/TFLOPS, split-prec vs FP64 (D exact); p50/p99"
 GOLDEN = os.path.join(ROOT, "tests", "golden")
-NOMINAL_FP64_TFLOPS = 1.25     # GB300 FP64 (nominal)
-NOMINAL_BF16_TFLOPS = 2250.0
 
 
 def parse():
@@ -273,12 +271,13 @@ def main():
     prof_ms, prof_fl = st1["prof_ms"], st1["prof_flops"]
     achieved = prof_fl / (prof_ms * 1e-3) / 1e12 if prof_ms > 0 else None
     if args.precision == "fp64":
-        # FP64 is not in the measured peaks: the recipe's rule scales the measured bf16 peak by
-        # the nominal FP64/BF16 ratio (sustained: the kernel runs inside a long step)
-        peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+        # FP64 SIMT GEMM, bound by the FP64 pipe: peak from unit counts and the sampled clock
+        # (152 SMs x 2 DFMA/clk x 2 flops); a DFMA probe measured 1.19 TFLOP/s at 2.07 GHz
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
         roof = {"kernel": "gemm_f64_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "peak_source": f"{pk_kind} bf16 sustained x nominal FP64/BF16 (1.25/2250)",
+                "peak_source": f"FP64 pipe: 152 SMs x 4 flop/clk x {sm_mhz:.0f} MHz (unit counts)",
                 "launches": st1["prof_launches"], "kernel_ms": prof_ms,
                 "kernel_share_of_step": prof_ms / total_ms if total_ms else None}
     else:
