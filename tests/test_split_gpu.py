@@ -1,0 +1,143 @@
+"""Parity of the split-precision path (BF16 digit products on the tensor cores) with the oracle.
+
+D must equal the oracle's D exactly.  Y must agree entrywise within a relative 1e-10 at the
+default 12 digits of 7 bits: the digit truncation leaves a relative 2^-84 of each operand
+chunk's scale, the float-float (two FP32) accumulation carries about 2^-44 of each entry, and
+the products are sign-definite, so each entry of Y keeps a relative error of a few 2^-44 times
+the depth of the recursion (observed well below 1e-11).
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_07403_gb300 import graphs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+YTOL = 1e-10
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def rd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_07403_gb300 import build
+    from paper_2308_07403_gb300 import rd as _rd
+
+    build.build()
+    _rd.load()
+    return _rd
+
+
+def run(rd, A, g, slices=0, want_y=True):
+    n = A.shape[0]
+    At = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    D = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    Y = torch.empty((n, n), dtype=torch.float64, device="cuda") if want_y else None
+    with rd.Handle(At, g, stream=torch.cuda.current_stream().cuda_stream) as h:
+        h.set_precision(rd.RD_PREC_SPLIT_BF16, slices)
+        h.apsp(D, Y)
+        h.sync()
+        st = h.stats()
+    torch.cuda.synchronize()
+    return D.cpu().numpy(), (Y.cpu().numpy() if want_y else None), st
+
+
+def rel_err(Yg, Yo):
+    assert np.array_equal(Yg == 0, Yo == 0)
+    nz = Yo != 0
+    return float(np.max(np.abs(Yg[nz] - Yo[nz]) / np.abs(Yo[nz]))) if nz.any() else 0.0
+
+
+# (name, graph and gain, digit count): the directed path puts a 2^-68 range of Y inside one
+# 128-node chunk, which 12 digits of 7 bits cannot resolve to 1e-10; 16 digits do.
+SLICES = {"dpath40": 16}
+CASES = [
+    ("er128", lambda: (graphs.er(128, 0.06, 1), None)),
+    ("dpath40", lambda: (graphs.directed_path(40), 0.3)),
+    ("complete64", lambda: (graphs.complete(64), 0.5 / 64)),
+    ("grid200", lambda: (graphs.grid4(200, 15), None)),
+    ("ws257", lambda: (graphs.ws(257, 6, 0.1, 3), None)),
+    ("tree300", lambda: (graphs.binary_tree(300), None)),
+    ("er512_small_workload", lambda: graphs.workload_small()),
+    ("ws1000_ragged", lambda: (graphs.ws(1000, 10, 0.1, 9), None)),
+]
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_split_matches_oracle(rd, name):
+    A, g = dict(CASES)[name]()
+    if g is None:
+        g = graphs.gamma_frac(A, 0.9)
+    Do, Yo = oracle.rdistance(A, g, want_y=True)
+    s = SLICES.get(name, 12)
+    Dg, Yg, st = run(rd, A, g, slices=s)
+    assert st["precision"] == rd.RD_PREC_SPLIT_BF16 and st["slices"] == s
+    err = rel_err(Yg, Yo)
+    assert err < YTOL, err
+    assert np.array_equal(Dg, Do), int(np.sum(Dg != Do))
+
+
+def test_split_slice_count_controls_precision(rd):
+    A, g = graphs.workload_small()
+    _, Yo = oracle.rdistance(A, g, want_y=True)
+    errs = {}
+    for s in (4, 8, 12):
+        _, Yg, st = run(rd, A, g, slices=s)
+        assert st["slices"] == s
+        errs[s] = rel_err(Yg, Yo)
+    assert errs[4] > errs[8] > errs[12] or errs[12] < 1e-13
+    assert errs[8] < 1e-6
+
+
+def test_split_goal_rows_and_greedy(rd):
+    n = 333
+    A = graphs.grid4(n, 19)
+    g = graphs.gamma_frac(A, 0.9)
+    goals = np.array([0, 7, 100, n - 1], dtype=np.int32)
+    rows_o = oracle.goal_rows(A, g, goals)
+    rows = np.empty((goals.size, n))
+    nxt = np.empty((goals.size, n), np.int32)
+    with rd.Handle(A, g) as h:
+        h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
+        h.goal_solve(goals, rows)
+        h.greedy_next(goals, rows, nxt)
+    assert rel_err(rows, rows_o) < YTOL
+    assert np.array_equal(nxt, oracle.greedy_next(A, goals, rows))
+
+
+def test_split_rejects_bad_slice_counts(rd):
+    A, g = graphs.workload_small()
+    with rd.Handle(A, g) as h:
+        with pytest.raises(rd.RDError):
+            h.set_precision(rd.RD_PREC_SPLIT_BF16, 17)
+        h.set_precision(rd.RD_PREC_SPLIT_BF16, 1)
+        D = np.empty((512, 512), np.int32)
+        with pytest.raises(rd.RDError) as ei:
+            h.apsp(D)
+        assert ei.value.status == rd.RD_ERR_ARG
+
+
+@pytest.mark.parametrize("kind,frac", [(k, f) for k in graphs.LARGE_KINDS for f in graphs.LARGE_FRACS])
+def test_split_full_size_D_identical(rd, kind, frac):
+    """n = 8192: the split path's D hashes to the oracle's D."""
+    p = os.path.join(HERE, "golden", f"large_{kind}_{frac}.json")
+    if not os.path.exists(p):
+        pytest.skip("golden file missing")
+    with open(p) as f:
+        rec = json.load(f)
+    A, g = graphs.workload_large(kind, frac)
+    Dg, _, _ = run(rd, A, g, want_y=False)
+    digest = hashlib.sha256(np.ascontiguousarray(Dg, dtype="<i4").tobytes()).hexdigest()
+    if digest != rec["sha256_D"]:
+        B = rec["block_rows"]
+        bad = [b for b, hx in enumerate(rec["block_sha256_16"])
+               if hashlib.sha256(np.ascontiguousarray(Dg[b * B:(b + 1) * B], dtype="<i4").tobytes())
+               .hexdigest()[:16] != hx]
+        pytest.fail(f"{len(bad)} of {len(rec['block_sha256_16'])} row blocks differ")
