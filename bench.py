@@ -5,6 +5,8 @@ the 4-neighbour grid with 91 columns (90 full rows + 2), and the Watts-Strogatz 
 beta=0.1) -- each at gain 0.5/Delta and 0.9/Delta.  One step = the whole hot path on one
 graph, cycling through the six: rd_load (gain check + M), rd_apsp (LU, triangular inverses,
 product with the fused decode into int32 D), rd_goal_solve for 64 goals and rd_greedy_next.
+The headline is the split-precision path (--precision split, the default); the FP64 path is
+timed beside it ("compare") and D of all six graphs is checked against the oracle for both.
 
 value   = effective TFLOP/s, 2 n^3 per step (the dense inverse's flop count) over the device
           time of the step, summed over ranks (replicas) and divided by the slowest rank's time.
@@ -43,7 +45,8 @@ def parse():
     p.add_argument("--steps", type=int, default=6)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    p.add_argument("--precision", default="split", choices=["fp64", "split"])
+    p.add_argument("--compare-steps", type=int, default=2, help="steps of the other precision, 0 = skip")
     p.add_argument("--slices", type=int, default=0)
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--goals", type=int, default=64)
@@ -188,6 +191,62 @@ def cpu_baseline(args, A):
 
 # ---- our arm ---------------------------------------------------------------------------------
 
+def time_path(rd, h, step, first, steps, warmup, stream, local, world, dist, profile=True):
+    """Warm up, then time `steps` calls of step(i) with CUDA events on the handle's stream.
+
+    Returns per-step ms, total ms (max over ranks), the stats delta and the clock record."""
+    import torch
+
+    for i in range(warmup):
+        step(first + i)
+    torch.cuda.synchronize()
+    st0 = rd.rd_get_stats(h)
+    if profile:
+        rd.rd_set_profiling(h, True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for i in range(steps):
+        step(first + warmup + i)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    total = ev[0].elapsed_time(ev[-1])
+    st1 = rd.rd_get_stats(h)
+    if profile:
+        rd.rd_set_profiling(h, False)
+    total = reduce_max(total, dist, world, f"cuda:{local}")
+    return per_step, total, st0, st1, clk
+
+
+def reduce_max(x, dist, world, device):
+    """Largest value over the ranks (every rank gets it); the slowest replica sets the time."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, flop_per_step, steps, total_ms):
+    """Whole-job rate in TFLOP/s: every replica processed `steps` steps; time is the slowest."""
+    return world * flop_per_step * steps / (total_ms * 1e-3) / 1e12
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -224,8 +283,7 @@ def main():
 
     h = rd.rd_create(A_dev[0], n, wl[0][3])
     rd.rd_set_stream(h, stream.cuda_stream)
-    prec = rd.RD_PREC_SPLIT_BF16 if args.precision == "split" else rd.RD_PREC_FP64
-    rd.rd_set_precision(h, prec, args.slices)
+    modes = {"split": rd.RD_PREC_SPLIT_BF16, "fp64": rd.RD_PREC_FP64}
 
     def step(i):
         kind, frac, _, g = wl[i % len(wl)]
@@ -234,39 +292,13 @@ def main():
         rd.rd_goal_solve(h, goals_dev, args.goals, rows)
         rd.rd_greedy_next(h, goals_dev, args.goals, rows, nxt)
 
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    st0 = rd.rd_get_stats(h)
-    rd.rd_set_profiling(h, True)
-    clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    ev[0].record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
-        ev[i + 1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    st1 = rd.rd_get_stats(h)
-    rd.rd_set_profiling(h, False)
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    ms_step = t_max / args.steps
+    # ---- the headline path
+    rd.rd_set_precision(h, modes[args.precision], args.slices)
+    per_step, total_ms, st0, st1, clk = time_path(rd, h, step, 0, args.steps, args.warmup, stream, local, world, dist)
+    ms_step = total_ms / args.steps
     flop_step = 2.0 * n ** 3
-    value = world * flop_step * args.steps / (t_max * 1e-3) / 1e12
-
-    # roofline of the dense-contraction kernel over the timed region
+    value = replica_throughput(world, flop_step, args.steps, total_ms)
+    launches = st1["launches"] - st0["launches"]
     pk, pk_kind = peaks()
     prof_ms, prof_fl = st1["prof_ms"], st1["prof_flops"]
     achieved = prof_fl / (prof_ms * 1e-3) / 1e12 if prof_ms > 0 else None
@@ -275,20 +307,35 @@ def main():
         # (152 SMs x 2 DFMA/clk x 2 flops); a DFMA probe measured 1.19 TFLOP/s at 2.07 GHz
         sm_mhz = clk.get("sm_mhz") or 2070.0
         peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": "gemm_f64_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "peak_source": f"FP64 pipe: 152 SMs x 4 flop/clk x {sm_mhz:.0f} MHz (unit counts)",
-                "launches": st1["prof_launches"], "kernel_ms": prof_ms,
-                "kernel_share_of_step": prof_ms / total_ms if total_ms else None}
+        roof = {"kernel": "gemm_f64_kernel", "bound": "alu", "peak_source":
+                f"FP64 pipe: 152 SMs x 4 flop/clk x {sm_mhz:.0f} MHz (unit counts)"}
     else:
+        # the split GEMM's algorithmic work is its digit products: s(s+1)/2 x 2 M N K per product
         peak = pk["bf16_tflops_sustained"]
-        roof = {"kernel": "split_gemm", "bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "peak_source": f"{pk_kind} bf16 sustained", "launches": st1["prof_launches"],
-                "kernel_ms": prof_ms, "kernel_share_of_step": prof_ms / total_ms if total_ms else None}
-    launches = st1["launches"] - st0["launches"]
+        roof = {"kernel": "split_gemm_kernel", "bound": "tensor",
+                "peak_source": f"{pk_kind} bf16 sustained (cuBLAS, seconds-long loop)",
+                "work": "issued BF16 digit products, s(s+1)/2 x 2MNK per split product"}
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": (achieved / peak) if achieved else None, "traffic": None,
+                 "launches": st1["prof_launches"], "kernel_ms": prof_ms,
+                 "kernel_share_of_step": prof_ms / total_ms if total_ms else None})
+    slices_used = st1["slices"]
 
-    # end-to-end through the C ABI with host buffers
+    # ---- the comparison path (the other precision), fewer steps
+    compare = None
+    other = "fp64" if args.precision == "split" else "split"
+    if args.compare_steps > 0:
+        rd.rd_set_precision(h, modes[other], 0)
+        cps, ctot, _, _, _ = time_path(rd, h, step, 100, args.compare_steps, 1, stream, local, world, dist,
+                                       profile=False)
+        compare = {"precision": other, "ms_per_step": ctot / args.compare_steps,
+                   "p50_ms": pct(cps, 0.5), "p99_ms": pct(cps, 0.99),
+                   "value": replica_throughput(world, flop_step, args.compare_steps, ctot), "unit": "TFLOP/s",
+                   "steps": args.compare_steps, "warmup": 1}
+        compare["speedup_of_headline"] = compare["ms_per_step"] / ms_step
+        rd.rd_set_precision(h, modes[args.precision], args.slices)
+
+    # ---- end-to-end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
         A_host = [torch.from_numpy(A).pin_memory() for (_, _, A, _) in wl[::2]]
@@ -312,33 +359,35 @@ def main():
         for i in range(args.e2e_steps):
             step_host(1 + i)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * flop_step * args.e2e_steps / te / 1e12, "unit": "TFLOP/s",
+        te = reduce_max(time.perf_counter() - t0, dist, world, dev)
+        e2e = {"value": replica_throughput(world, flop_step, args.e2e_steps, te * 1e3), "unit": "TFLOP/s",
                "ms_per_step": te * 1e3 / args.e2e_steps,
                "h2d_bytes_per_step": n * n + 4 * args.goals * 2 + 8 * args.goals * n,
                "d2h_bytes_per_step": 4 * n * n + 8 * args.goals * n + 4 * args.goals * n}
 
-    # D of every graph against the oracle's stored hash (tests/golden, written by the oracle)
+    # ---- D of every graph against the oracle's stored hash (tests/golden, written by the oracle)
     verify = None
     if args.verify and n == 8192:
-        ok, checked = 0, 0
-        for i, (kind, frac, _, g) in enumerate(wl):
-            path = os.path.join(GOLDEN, f"large_{kind}_{frac}.json")
-            if not os.path.exists(path):
-                continue
-            with open(path) as f:
-                gold = json.load(f)
-            rd.rd_load(h, A_dev[i // 2], None, g)
-            rd.rd_apsp(h, D)
-            torch.cuda.synchronize()
-            dh = hashlib.sha256(D.cpu().numpy().astype("<i4").tobytes()).hexdigest()
-            checked += 1
-            ok += int(dh == gold["sha256_D"])
-        verify = {"graphs_D_identical_to_oracle": ok, "graphs_checked": checked}
+        verify = {}
+        for name in ([args.precision, other] if compare else [args.precision]):
+            rd.rd_set_precision(h, modes[name], args.slices if name == args.precision else 0)
+            ok, checked, fell = 0, 0, 0
+            for i, (kind, frac, _, g) in enumerate(wl):
+                path = os.path.join(GOLDEN, f"large_{kind}_{frac}.json")
+                if not os.path.exists(path):
+                    continue
+                with open(path) as f:
+                    gold = json.load(f)
+                rd.rd_load(h, A_dev[i // 2], None, g)
+                rd.rd_apsp(h, D)
+                torch.cuda.synchronize()
+                fell += int(name == "split" and rd.rd_get_stats(h)["precision_used"] != rd.RD_PREC_SPLIT_BF16)
+                dh = hashlib.sha256(D.cpu().numpy().astype("<i4").tobytes()).hexdigest()
+                checked += 1
+                ok += int(dh == gold["sha256_D"])
+            verify[name] = {"graphs_D_identical_to_oracle": ok, "graphs_checked": checked}
+            if name == "split":
+                verify[name]["graphs_redone_in_fp64_by_self_check"] = fell
     rd.rd_destroy(h)
 
     if rank != 0:
@@ -346,22 +395,24 @@ def main():
             dist.destroy_process_group()
         return
     cpu = cpu_baseline(args, wl[0][2]) if world == 1 else None
-    ps = sorted(per_step)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "bf16-slices+f64",
+        "dtype": "f64" if args.precision == "fp64" else "bf16-digits+f64",
         "data": "synthetic",
         "config": {"workload": f"n={n} single graphs: ER p=0.01, grid 90x91 (+2), WS k=10 beta=0.1, "
                                f"gain 0.5 and 0.9 x 1/Delta; one graph per step, {args.goals} goals",
-                   "n": n, "precision": args.precision, "slices": args.slices, "goals": args.goals,
+                   "n": n, "precision": args.precision, "slices_requested": args.slices,
+                   "slices_last_graph": slices_used, "goals": args.goals,
                    "l2": "no flush: working set (M, LU, inverses) 1.3 GB > 129 MB L2",
                    "parallelism": f"replicas x{world}"},
-        "p50_ms": ps[len(ps) // 2], "p99_ms": ps[min(len(ps) - 1, int(round(0.99 * (len(ps) - 1))))],
+        "p50_ms": pct(per_step, 0.5), "p99_ms": pct(per_step, 0.99),
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-        "cpu_baseline": cpu, "verify": verify,
+        "cpu_baseline": cpu, "compare": compare, "verify": verify,
     }
+    if args.precision == "split":
+        line["steps_redone_in_fp64_by_self_check"] = st1["fallbacks"] - st0["fallbacks"]
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -88,7 +88,11 @@ typedef struct {
   int64_t launches;       /* kernel launches issued by this handle since it was created      */
   int64_t prof_launches;  /* profiled dense-contraction launches (see rd_set_profiling)      */
   double prof_ms;         /* their summed device time (CUDA events on the handle's stream)   */
-  double prof_flops;      /* their summed algorithmic flop count                             */
+  double prof_flops;      /* their summed flop count (split path: the issued digit products)  */
+  int32_t precision_used; /* precision that produced the current graph's result              */
+  int32_t fallbacks;      /* split results this handle redid (more digits or FP64)           */
+  double split_residual;  /* largest entrywise relative residual of the sampled rows of the  */
+                          /* last split result against M (the self-check; 1e-9 accepted)     */
 } rd_stats;
 
 /* Create a handle for the unweighted graph A (n x n bytes) and gain gamma: validates gamma
@@ -111,8 +115,12 @@ rd_status rd_load(rd_handle h, const uint8_t* A, const float* W, double gamma);
 /* Use the given cudaStream_t (passed as void*) for all later work of this handle. */
 rd_status rd_set_stream(rd_handle h, void* stream);
 
-/* Select RD_PREC_FP64 or RD_PREC_SPLIT_BF16; slices = 0 lets the library choose.
- * Drops cached factors when the mode changes. */
+/* Select RD_PREC_FP64 or RD_PREC_SPLIT_BF16.  slices in [2, 15] fixes the digit count (no
+ * self-check: the caller owns the precision); 0 lets the library choose per graph: it starts
+ * from 12 digits and checks itself -- the product epilogue flags terms below the range of its
+ * FP32 accumulators, and 64 sampled rows of Y must satisfy y^T M = e_g^T to a relative 1e-9 per
+ * entry (rd_stats.split_residual) -- and when a check fails recomputes the graph's inverse with
+ * 15 digits, then in FP64.  Drops cached factors when the mode changes. */
 rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices);
 
 /* Change the decode snap tau (>= 0, < 0.5). */
@@ -120,7 +128,10 @@ rd_status rd_set_tau(rd_handle h, double tau);
 
 /* All-pairs R-distance: D (n*n int32, row-major, D[i*n+j] = distance j -> i).  If Y is not
  * NULL it also receives Y (n*n float64).  Factors M on first use and keeps the factors for
- * rd_goal_solve. */
+ * rd_goal_solve.  In RD_PREC_SPLIT_BF16 with the digit count left to the library, the call
+ * reads the self-check flags (one synchronisation after the factorisation and one after the
+ * product) and recomputes with more digits or in FP64 when they fire; rd_stats.slices,
+ * precision_used and fallbacks report what was used. */
 rd_status rd_apsp(rd_handle h, int32_t* D, double* Y);
 
 /* Goal rows (the local mode of Sec. 4.2): for each goal g = goals[c], 0 <= c < k, writes row

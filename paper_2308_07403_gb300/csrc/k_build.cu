@@ -6,36 +6,47 @@
 // Delta) and, for weighted graphs, the column sum of X; the host accepts the gain when the
 // largest column sum of X is below one (strict column diagonal dominance of M).
 //
-// All three kernels are HBM-bound streams over the n x n byte matrix (and the N x N FP64 M):
-// one thread per column walks down the rows, so a warp reads 32 consecutive bytes of a row
+// The kernels are HBM-bound streams over the n x n byte matrix (and the N x N FP64 M): one
+// thread per column walks down a block of rows, so a warp reads 32 consecutive bytes of a row
 // per step and writes consecutive doubles of M.
 #include "rd_internal.cuh"
 
 namespace {
 
-__global__ void build_m_kernel(const uint8_t* __restrict__ A, const float* __restrict__ W,
-                               int n, int N, double gamma, double log_gamma, double* __restrict__ M,
-                               int32_t* __restrict__ deg, unsigned long long* __restrict__ red) {
+// M for the rows of one row block; per-column edge counts and column sums are added with atomics
+// (the column sums only feed the gain check, so their summation order does not matter).
+__global__ void build_m_kernel(const uint8_t* __restrict__ A, const float* __restrict__ W, int n, int N,
+                               int rows_per_block, double gamma, double* __restrict__ M,
+                               int32_t* __restrict__ deg, double* __restrict__ colsum) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;  // column of M
   if (j >= N) return;
+  const int r0 = blockIdx.y * rows_per_block;
+  const int r1 = min(N, r0 + rows_per_block);
   int cnt = 0;
-  double colsum = 0.0;
-  for (int i = 0; i < N; ++i) {
+  double cs = 0.0;
+  for (int i = r0; i < r1; ++i) {
     double x = 0.0;
     if (i < n && j < n && A[(long long)i * n + j]) {
       ++cnt;
       x = W ? pow(gamma, (double)W[(long long)i * n + j]) : gamma;
-      colsum += x;
+      cs += x;
     }
     M[(long long)i * N + j] = (i == j ? 1.0 : 0.0) - x;
   }
-  if (j < n) {
-    deg[j] = cnt;
-    atomicMax(&red[0], (unsigned long long)cnt);
-    atomicAdd(&red[2], (unsigned long long)cnt);
-    // non-negative doubles order like their bit patterns
-    atomicMax(&red[1], (unsigned long long)__double_as_longlong(colsum));
+  if (j < n && cnt) {
+    atomicAdd(&deg[j], cnt);
+    atomicAdd(&colsum[j], cs);
   }
+}
+
+// largest degree, largest column sum (bits of a non-negative double) and the edge count
+__global__ void build_reduce_kernel(const int32_t* __restrict__ deg, const double* __restrict__ colsum, int n,
+                                    unsigned long long* __restrict__ red) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  atomicMax(&red[0], (unsigned long long)deg[j]);
+  atomicMax(&red[1], (unsigned long long)__double_as_longlong(colsum[j]));
+  atomicAdd(&red[2], (unsigned long long)deg[j]);
 }
 
 // exclusive prefix sum of deg[0..n) into ptr[0..n] (single block; n is at most a few 10^5)
@@ -89,11 +100,19 @@ __global__ void copy_rows_kernel(const double* __restrict__ R, long long ldr, in
 cudaError_t rd_build_m(rd_ctx* h, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(h->dRed, 0, 3 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(h->dDeg, 0, (size_t)h->n * sizeof(int32_t), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(h->dColsum, 0, (size_t)h->n * sizeof(double), s)) != cudaSuccess) return e;
   const int threads = 128;
-  const int blocks = (h->N + threads - 1) / threads;
+  const int row_blocks = 16;
+  const int rows_per_block = (h->N + row_blocks - 1) / row_blocks;
+  dim3 grid((h->N + threads - 1) / threads, row_blocks);
   if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
-  build_m_kernel<<<blocks, threads, 0, s>>>(h->dA, h->weighted ? h->dW : nullptr, h->n, h->N,
-                                             h->gamma, log(h->gamma), h->dLU, h->dDeg, h->dRed);
+  build_m_kernel<<<grid, threads, 0, s>>>(h->dA, h->weighted ? h->dW : nullptr, h->n, h->N, rows_per_block,
+                                          h->gamma, h->dLU, h->dDeg, h->dColsum);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, false, 0.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
+  build_reduce_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(h->dDeg, h->dColsum, h->n, h->dRed);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, false, 0.0);
 }

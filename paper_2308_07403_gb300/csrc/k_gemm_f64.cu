@@ -8,7 +8,10 @@
 // FP64 throughput on this part is two orders of magnitude below its BF16 tensor rate, so the
 // kernel is bound by the FP64 pipe whatever the tiling: a 64x64 CTA tile with a 4x4 register
 // micro-tile per thread and a 16-deep K step in shared memory keeps the pipe fed while the
-// memory traffic stays three orders of magnitude below the HBM rate.
+// memory traffic stays three orders of magnitude below the HBM rate.  Small products (the low
+// levels of the split path's recursion, the goal solves) switch to 32x32 or 16x16 tiles so that
+// they still spread over every SM: with two FP64 FMAs per clock per SM, parallelism is what
+// small FP64 products lack.
 //
 // Operands may be read through a "triangular view" of the packed storage: the strict lower
 // part with an implied unit diagonal (L, L^-1) or the upper part including the diagonal
@@ -17,13 +20,14 @@
 // should (n^3/3 for a triangle times a full matrix).
 //
 // In-place use: C may alias A's row strip or B's column strip of the same CTA (the panel
-// products of the LU and the goal solves do this).  Every CTA reads all of its K range before
-// its epilogue writes, and reads no other CTA's output, so this is safe when beta == 0.
+// products of the LU and the goal solves do this, flagged with `aliased`).  Every CTA reads all
+// of its K range before its epilogue writes, and reads no other CTA's output, so this is safe
+// when beta == 0 and one CTA owns the whole strip: aliased products keep the 64 x 64 tile.
 #include "rd_internal.cuh"
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
 __device__ __forceinline__ double tri_load(const double* p, long long ld, int r, int c, int tri) {
   // r, c are indices inside the operand view; the view's diagonal is r == c
@@ -36,49 +40,54 @@ __device__ __forceinline__ double tri_load(const double* p, long long ld, int r,
   return p[(long long)r * ld + c];
 }
 
-__global__ void __launch_bounds__(NT) gemm_f64_kernel(const rd_gemm_f64_args* __restrict__ probs_dev,
-                                                      rd_gemm_f64_args p0, rd_gemm_f64_args p1) {
+// T x T output tile per CTA (T = 64, 32 or 16), 256 threads on a 16 x 16 grid, each owning a
+// (T/16) x (T/16) register micro-tile; K advances 16 at a time through shared memory with a
+// register prefetch of the next step.
+template <int T>
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(rd_gemm_f64_args p0, rd_gemm_f64_args p1) {
+  constexpr int R = T / 16;           // micro-tile edge
+  constexpr int LA = T * BK / NT;     // elements of A (and of B) each thread stages per K step
   const rd_gemm_f64_args& p = (blockIdx.z == 0) ? p0 : p1;
-  (void)probs_dev;
-  const int tiles_n = p.N / BN;
-  const int tiles = (p.M / BM) * tiles_n;
+  const int tiles_n = p.N / T;
+  const int tiles = (p.M / T) * tiles_n;
   const int tile = blockIdx.x;
   if (tile >= tiles) return;
-  const int r0 = (tile / tiles_n) * BM;
-  const int c0 = (tile % tiles_n) * BN;
+  const int r0 = (tile / tiles_n) * T;
+  const int c0 = (tile % tiles_n) * T;
 
   int kbeg = 0, kend = p.K;
-  if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, r0 + BM);
+  if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, r0 + T);
   if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, r0);
   if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, c0);
-  if (p.b_tri == RD_TRI_UPPER) kend = min(kend, c0 + BN);
+  if (p.b_tri == RD_TRI_UPPER) kend = min(kend, c0 + T);
+  kbeg = kbeg / BK * BK;
 
-  __shared__ double As[2][BK][BM];
-  __shared__ double Bs[2][BK][BN];
+  __shared__ double As[2][BK][T];
+  __shared__ double Bs[2][BK][T];
 
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  // global -> smem assignment: A tile 64 rows x 16 k, B tile 16 k x 64 cols, 4 elements each
-  const int a_r = tid / 4, a_k = (tid % 4) * 4;
-  const int b_k = tid / 16, b_c = (tid % 16) * 4;
+  // staging: A tile T rows x 16 k, B tile 16 k x T cols, LA consecutive elements per thread
+  const int a_r = (tid * LA) / BK, a_k = (tid * LA) % BK;
+  const int b_k = (tid * LA) / T, b_c = (tid * LA) % T;
 
-  double acc[4][4];
+  double acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
 
-  double ra[4], rb[4];
+  double ra[LA], rb[LA];
   auto load_regs = [&](int k0) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < LA; ++e) {
       ra[e] = tri_load(p.A, p.lda, r0 + a_r, k0 + a_k + e, p.a_tri);
       rb[e] = tri_load(p.B, p.ldb, k0 + b_k, c0 + b_c + e, p.b_tri);
     }
   };
   auto store_regs = [&](int buf) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < LA; ++e) {
       As[buf][a_k + e][a_r] = ra[e];
       Bs[buf][b_k][b_c + e] = rb[e];
     }
@@ -94,15 +103,15 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const rd_gemm_f64_args* __
       if (more) load_regs(k0 + BK);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double a[4], b[4];
+        double a[R], b[R];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+        for (int i = 0; i < R; ++i) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+        for (int j = 0; j < R; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < R; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
       if (more) {
         store_regs(buf ^ 1);
@@ -116,10 +125,10 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const rd_gemm_f64_args* __
   __syncthreads();
 
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     const int r = r0 + ty + 16 * i;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       const int c = c0 + tx + 16 * j;
       double v = p.alpha * acc[i][j];
       if (p.beta != 0.0) v = fma(p.beta, p.C[(long long)r * p.ldc + c], v);
@@ -143,19 +152,38 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const rd_gemm_f64_args* __
 cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cudaStream_t s,
                         double flops) {
   if (nprob < 1 || nprob > 2) return cudaErrorInvalidValue;
-  int maxtiles = 0;
+  // the largest tile (64, 32 or 16) that still gives two waves of CTAs over the 152 SMs
+  int T = 64;
+  long long work = 0;
+  bool aliased = false;
   for (int i = 0; i < nprob; ++i) {
     const rd_gemm_f64_args& p = probs[i];
-    if (p.M % BM || p.N % BN || p.K % BK || p.M < 0 || p.N < 0 || p.K < 0)
-      return cudaErrorInvalidValue;
-    int t = (p.M / BM) * (p.N / BN);
+    if (p.M % 16 || p.N % 16 || p.K % BK || p.M < 0 || p.N < 0 || p.K < 0) return cudaErrorInvalidValue;
+    if (p.M % 64 || p.N % 64) T = 16;
+    if (p.aliased) {
+      aliased = true;
+      if (p.beta != 0.0 || (p.M != 64 && p.N != 64)) return cudaErrorInvalidValue;
+    }
+    work += (long long)p.M * p.N;
+  }
+  if (aliased && T != 64) return cudaErrorInvalidValue;
+  while (!aliased && T > 16 && work / ((long long)T * T) < 2 * 152) T /= 2;
+  int maxtiles = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const int t = (probs[i].M / T) * (probs[i].N / T);
     if (t > maxtiles) maxtiles = t;
   }
   if (maxtiles == 0) return cudaSuccess;
   dim3 grid(maxtiles, 1, nprob);
   cudaError_t e = rd_prof_begin(h, s, true);
   if (e != cudaSuccess) return e;
-  gemm_f64_kernel<<<grid, NT, 0, s>>>(nullptr, probs[0], nprob > 1 ? probs[1] : probs[0]);
+  const rd_gemm_f64_args& q1 = nprob > 1 ? probs[1] : probs[0];
+  if (T == 64)
+    gemm_f64_kernel<64><<<grid, NT, 0, s>>>(probs[0], q1);
+  else if (T == 32)
+    gemm_f64_kernel<32><<<grid, NT, 0, s>>>(probs[0], q1);
+  else
+    gemm_f64_kernel<16><<<grid, NT, 0, s>>>(probs[0], q1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return rd_prof_end(h, s, true, flops);

@@ -81,7 +81,7 @@ cudaError_t rd_goal_f64(rd_ctx* h, const int32_t* dgoals, int k, double* out, cu
     p.A = R + K * B; p.lda = N;
     p.B = T + (long long)K * B * N + K * B; p.ldb = N; p.b_tri = RD_TRI_UPPER;
     p.C = R + K * B; p.ldc = N;
-    p.M = RD_MAX_GOALS; p.N = B; p.K = B; p.c_rows = RD_MAX_GOALS; p.c_cols = B;
+    p.M = RD_MAX_GOALS; p.N = B; p.K = B; p.c_rows = RD_MAX_GOALS; p.c_cols = B; p.aliased = 1;
     if ((e = rd_gemm_f64(h, &p, 1, s, fdiag_u)) != cudaSuccess) return e;
     const int rest = (int)(N - (K + 1) * B);
     if (rest == 0) continue;
@@ -98,7 +98,7 @@ cudaError_t rd_goal_f64(rd_ctx* h, const int32_t* dgoals, int k, double* out, cu
     p.A = R + K * B; p.lda = N;
     p.B = T + (long long)K * B * N + K * B; p.ldb = N; p.b_tri = RD_TRI_LOWER_UNIT;
     p.C = R + K * B; p.ldc = N;
-    p.M = RD_MAX_GOALS; p.N = B; p.K = B; p.c_rows = RD_MAX_GOALS; p.c_cols = B;
+    p.M = RD_MAX_GOALS; p.N = B; p.K = B; p.c_rows = RD_MAX_GOALS; p.c_cols = B; p.aliased = 1;
     if ((e = rd_gemm_f64(h, &p, 1, s, fdiag_l)) != cudaSuccess) return e;
     if (K == 0) continue;
     rd_gemm_f64_args u = blank();

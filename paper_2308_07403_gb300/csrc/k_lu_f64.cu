@@ -22,69 +22,124 @@ constexpr int B = RD_BF;
 
 // LU of the B x B diagonal block at (k0, k0) of LU (in place), then the inverses of its unit
 // lower factor and of its upper factor, written to the same block of T (strict lower = L^-1,
-// upper = U^-1).  One CTA of 256 threads; the block lives in shared memory.
+// upper = U^-1).  One CTA of 256 threads; thread t keeps the 4 x 4 tile at rows 4 (t / 16),
+// columns 4 (t % 16) of every matrix in registers.  Each elimination step publishes the pivot
+// row and column through shared memory (double-buffered, so one barrier per step) and one
+// thread forms the reciprocal of the pivot.  The two triangular inverses run in the same
+// 64-step loop: L^-1 by forward elimination (step q), U^-1 by back substitution (step 63 - q).
 __global__ void __launch_bounds__(256) lu_diag_kernel(double* __restrict__ LU, double* __restrict__ T,
                                                       long long ld, int k0, int* status) {
-  extern __shared__ double smem_diag[];
-  double(*a)[B + 1] = reinterpret_cast<double(*)[B + 1]>(smem_diag);
-  double(*li)[B + 1] = reinterpret_cast<double(*)[B + 1]>(smem_diag + B * (B + 1));
-  double(*ui)[B + 1] = reinterpret_cast<double(*)[B + 1]>(smem_diag + 2 * B * (B + 1));
+  __shared__ double rowb[2][B], colb[2][B], recip[2];
+  __shared__ double xrow[2][B], lcol[2][B], zrow[2][B], ucol[2][B], zrecip[2];
   const int t = threadIdx.x;
+  const int r0 = 4 * (t / 16), c0 = 4 * (t % 16);
+  double a[4][4];
   double* blk = LU + (long long)k0 * ld + k0;
-  for (int e = t; e < B * B; e += blockDim.x) a[e / B][e % B] = blk[(long long)(e / B) * ld + e % B];
-  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[i][j] = blk[(long long)(r0 + i) * ld + c0 + j];
 
+  // ---- LU without pivoting
   for (int k = 0; k < B; ++k) {
-    const double p = a[k][k];
-    const bool ok = (p > 0.0) && isfinite(p);
-    if (!ok && t == 0) rd_set_status(status, RD_DEV_PIVOT, k0 + k);
-    const double rp = ok ? 1.0 / p : 0.0;
-    for (int i = k + 1 + t; i < B; i += blockDim.x) a[i][k] *= rp;
-    __syncthreads();
-    const int m = B - 1 - k;
-    for (int e = t; e < m * m; e += blockDim.x) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      a[i][j] = fma(-a[i][k], a[k][j], a[i][j]);
+    const int bf = k & 1;
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      if (r0 + ii != k) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        rowb[bf][c0 + j] = a[ii][j];
+        if (c0 + j == k) {
+          const double p = a[ii][j];
+          const bool ok = (p > 0.0) && isfinite(p);
+          if (!ok) rd_set_status(status, RD_DEV_PIVOT, k0 + k);
+          recip[bf] = ok ? 1.0 / p : 0.0;
+        }
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      if (c0 + jj != k) continue;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) colb[bf][r0 + i] = a[i][jj];
     }
     __syncthreads();
+    const double ip = recip[bf];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gi = r0 + i;
+      if (gi <= k) continue;
+      const double l = colb[bf][gi] * ip;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gj = c0 + j;
+        if (gj > k) a[i][j] = fma(-l, rowb[bf][gj], a[i][j]);
+        else if (gj == k) a[i][j] = l;
+      }
+    }
   }
-  for (int e = t; e < B * B; e += blockDim.x) blk[(long long)(e / B) * ld + e % B] = a[e / B][e % B];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) blk[(long long)(r0 + i) * ld + c0 + j] = a[i][j];
 
-  // L^-1 (unit lower): X = I; for q: X[i][j] -= L[i][q] X[q][j], i > q, j <= q
-  // U^-1 (upper):      X = I; for q descending: X[q][j] /= U[q][q]; X[i][j] -= U[i][q] X[q][j], i < q
-  for (int e = t; e < B * B; e += blockDim.x) {
-    const int i = e / B, j = e % B;
-    li[i][j] = (i == j) ? 1.0 : 0.0;
-    ui[i][j] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  for (int q = 0; q < B; ++q) {
-    // lower: rows i in (q, B), columns j in [0, q]
-    const int rows = B - 1 - q, cols = q + 1;
-    for (int e = t; e < rows * cols; e += blockDim.x) {
-      const int i = q + 1 + e / cols, j = e % cols;
-      li[i][j] = fma(-a[i][q], li[q][j], li[i][j]);
+  // ---- L^-1 (x) and U^-1 (z), both starting from the identity
+  double x[4][4], z[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[i][j] = z[i][j] = (r0 + i == c0 + j) ? 1.0 : 0.0;
+  for (int st = 0; st < B; ++st) {
+    const int bf = st & 1;
+    const int q1 = st, q2 = B - 1 - st;
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      if (r0 + ii == q1) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xrow[bf][c0 + j] = x[ii][j];
+      }
+      if (r0 + ii == q2) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          zrow[bf][c0 + j] = z[ii][j];
+          if (c0 + j == q2) zrecip[bf] = 1.0 / a[ii][j];
+        }
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      if (c0 + jj == q1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) lcol[bf][r0 + i] = a[i][jj];
+      }
+      if (c0 + jj == q2) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ucol[bf][r0 + i] = a[i][jj];
+      }
     }
     __syncthreads();
-  }
-  for (int q = B - 1; q >= 0; --q) {
-    // upper: scale row q by 1/U[q][q] (row q of X is only nonzero for j >= q), then
-    // eliminate rows i < q over columns j in [q, B)
-    const double rq = 1.0 / a[q][q];
-    for (int j = q + t; j < B; j += blockDim.x) ui[q][j] *= rq;
-    __syncthreads();
-    const int rows = q, cols = B - q;
-    for (int e = t; e < rows * cols; e += blockDim.x) {
-      const int i = e / cols, j = q + e % cols;
-      ui[i][j] = fma(-a[i][q], ui[q][j], ui[i][j]);
+    const double dq = zrecip[bf];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gi = r0 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gj = c0 + j;
+        if (gi > q1 && gj <= q1) x[i][j] = fma(-lcol[bf][gi], xrow[bf][gj], x[i][j]);
+        if (gj >= q2) {
+          if (gi < q2)
+            z[i][j] = fma(-ucol[bf][gi], zrow[bf][gj] * dq, z[i][j]);
+          else if (gi == q2)
+            z[i][j] *= dq;
+        }
+      }
     }
-    __syncthreads();
   }
   double* tb = T + (long long)k0 * ld + k0;
-  for (int e = t; e < B * B; e += blockDim.x) {
-    const int i = e / B, j = e % B;
-    tb[(long long)i * ld + j] = (i > j) ? li[i][j] : ui[i][j];
-  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tb[(long long)(r0 + i) * ld + c0 + j] = (r0 + i > c0 + j) ? x[i][j] : z[i][j];
 }
 
 rd_gemm_f64_args blank() {
@@ -97,15 +152,10 @@ rd_gemm_f64_args blank() {
 
 }  // namespace
 
-constexpr size_t kDiagSmem = 3 * B * (B + 1) * sizeof(double);
-
 cudaError_t rd_lu_diag(rd_ctx* h, int k0, cudaStream_t s) {
   cudaError_t e;
-  e = cudaFuncSetAttribute(lu_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kDiagSmem);
-  if (e != cudaSuccess) return e;
   if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
-  lu_diag_kernel<<<1, 256, kDiagSmem, s>>>(h->dLU, h->dT, h->N, k0, h->dStatus);
+  lu_diag_kernel<<<1, 256, 0, s>>>(h->dLU, h->dT, h->N, k0, h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, false, 0.0);
 }
@@ -129,14 +179,14 @@ cudaError_t rd_lu_f64(rd_ctx* h, cudaStream_t s) {
     pr[0].B = LU + k0 * N + k0 + B; pr[0].ldb = N;
     pr[0].C = LU + k0 * N + k0 + B; pr[0].ldc = N;
     pr[0].M = B; pr[0].N = rest; pr[0].K = B;
-    pr[0].c_rows = B; pr[0].c_cols = rest;
+    pr[0].c_rows = B; pr[0].c_cols = rest; pr[0].aliased = 1;
     // column panel: C(rest x B) = M_Rk * Uinv_kk (upper view of T), in place
     pr[1] = blank();
     pr[1].A = LU + (k0 + B) * N + k0; pr[1].lda = N;
     pr[1].B = T + k0 * N + k0; pr[1].ldb = N; pr[1].b_tri = RD_TRI_UPPER;
     pr[1].C = LU + (k0 + B) * N + k0; pr[1].ldc = N;
     pr[1].M = rest; pr[1].N = B; pr[1].K = B;
-    pr[1].c_rows = rest; pr[1].c_cols = B;
+    pr[1].c_rows = rest; pr[1].c_cols = B; pr[1].aliased = 1;
     const double fpan = 2.0 * rest * (B * (B - 1) / 2 + B * (B + 1) / 2);
     if ((e = rd_gemm_f64(h, pr, 2, s, fpan)) != cudaSuccess) return e;
     // trailing update

@@ -4,7 +4,7 @@
 //
 // Arithmetic (an Ozaki-style splitting, written from the published scheme of Ozaki, Ogita,
 // Oishi and Rump, 2012, adapted to entrywise accuracy):
-//   * Each operand is cut into chunks of KAPPA = 128 along K.  Every (row, chunk) of A and
+//   * Each operand is cut into chunks of KAPPA = 256 along K.  Every (row, chunk) of A and
 //     every (chunk, column) of B gets its own power of two 2^e with |x| 2^-e < 1/2, so a chunk
 //     of small entries (far nodes, entries gamma^d) keeps its own scale.
 //   * x 2^-e is written in s balanced base-128 digits d_p in [-64, 64] (round to nearest):
@@ -12,8 +12,8 @@
 //     Every digit is an integer of at most 7 bits, exact in BF16.
 //   * For a chunk, the digit products of equal weight g = p + q (p, q < s, p + q < s) are
 //     summed by the tensor core into one FP32 accumulator in tensor memory: every product is
-//     an integer of magnitude <= 2^12 and a group holds at most s <= 16 of them per K entry,
-//     so a chunk sum stays below 128 * 16 * 2^12 = 2^23: exact.
+//     an integer of magnitude <= 2^12 and a group holds at most s <= 15 of them per K entry,
+//     so a chunk sum stays below 256 * 15 * 2^12 < 2^24: exact.
 //   * The epilogue warps read each group sum, scale it by 2^(eA + eB - 7 (g + 2)) relative to a
 //     per-row and per-column reference exponent, and add it into a float-float (two FP32)
 //     accumulator; FP64 is touched once per output entry at the end.
@@ -29,7 +29,9 @@
 // Every wait is bounded (about four seconds of %globaltimer); on expiry the CTA records
 // RD_DEV_TIMEOUT, every role leaves its loop, and the tensor memory is freed.
 //
-// The inverse is organised recursively so that the FP64 work stays at the 64 x 64 leaves:
+// The inverse is organised recursively so that the FP64 work stays at the bottom (64 x 64 leaves,
+// and FP64 products on small tiles for nodes of at most FP64_NODE rows, which are too small to
+// fill the tensor cores):
 //   factor(lo, hi):  factor the left half; U12 = L11^-1 A12; L21 = A21 U11^-1;
 //                    A22 -= L21 U12; factor the right half; then the off-diagonal blocks of
 //                    the inverses: L^-1_21 = -L22^-1 (L21 L11^-1), U^-1_12 = -U11^-1 (U12 U22^-1)
@@ -45,14 +47,14 @@
 namespace {
 
 constexpr int SIGMA = 7;          // bits per digit (balanced base 2^SIGMA)
-constexpr int KAPPA = 128;        // exponent / read-out chunk along K
+constexpr int KAPPA = 256;        // exponent / read-out chunk along K
 constexpr int TM = 128, TN = 128, TK = 64;
 constexpr int STAGES = 4;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr int TILE_BYTES = TM * TK * 2;            // one 128 x 64 BF16 tile: 16 KiB
 constexpr int EXP_ZERO = -16384;                   // exponent of an all-zero chunk
-constexpr int MAX_SLICES = 16;
+constexpr int MAX_SLICES = 15;                     // group sums exact: 256 * 15 * 2^12 < 2^24
 constexpr int LEAF = RD_BF;                        // FP64 diagonal leaves (64)
 constexpr unsigned long long WAIT_NS = 4000000000ull;
 
@@ -62,8 +64,11 @@ constexpr uint32_t IDESC = (1u << 4)               // D: FP32
                            | ((uint32_t)(TN >> 3) << 17)  // N
                            | ((uint32_t)(TM >> 4) << 24); // M  (A and B K-major)
 
-constexpr int LO_OFFSET = 2 * STAGES * TILE_BYTES + 256 + 2 * TN * 4;    // low words of the accumulators
-constexpr size_t SMEM_BYTES = 1024 + LO_OFFSET + TM * TN * 4;
+constexpr int RB_OFFSET = 2 * STAGES * TILE_BYTES + 256 + 2 * TN * 4;    // column reference exponents
+constexpr int LO_OFFSET = RB_OFFSET + TN * 4;                            // low words of the accumulators
+constexpr int FL_OFFSET = LO_OFFSET + TM * TN * 4;                        // flushed-term exponents (int8)
+constexpr int FLUSH_MARGIN = 48;  // a flushed term within 2^-48 of its final entry raises RD_FLAG_RANGE
+constexpr size_t SMEM_BYTES = 1024 + FL_OFFSET + TM * TN;
 
 // ---- PTX wrappers -----------------------------------------------------------------------
 
@@ -214,86 +219,78 @@ __device__ __forceinline__ void write_digits(double x, int e, int s, __nv_bfloat
   out[0] = __float2bfloat16_rn((float)(neg ? -d0 : d0));
 }
 
-// Role A (row chunks are contiguous in memory): one warp per output row, looping over chunks.
-// digits[p][row][k] (plane = rows_pad * k_pad), exps[chunk][row], rmax[row].
+// Role A (row chunks contiguous in memory): one warp per (row, chunk).
+// digits[p][row][k] (plane = rows_pad * k_pad), exps[chunk][row].
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, long long ld, int tri,
                                                          int rows, int cols, int rows_pad, int k_pad, int s,
                                                          __nv_bfloat16* __restrict__ dig, int* __restrict__ exps,
-                                                         int* __restrict__ rmax) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+                                                         int* status) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
-  if (warp >= rows_pad) return;
-  const int r = warp;
+  const int nch = k_pad / KAPPA;
+  if (w >= (long long)rows_pad * nch) return;
+  const int r = (int)(w / nch);
+  const int c0 = (int)(w % nch) * KAPPA;
   const long long plane = (long long)rows_pad * k_pad;
-  int best = EXP_ZERO;
-  for (int c0 = 0; c0 < k_pad; c0 += KAPPA) {
+  double v[KAPPA / 32];
+  double mx = 0.0;
+#pragma unroll
+  for (int t = 0; t < KAPPA / 32; ++t) {
+    v[t] = view_load(X, ld, r, c0 + lane + 32 * t, tri, rows, cols);
+    mx = fmax(mx, fabs(v[t]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int e = chunk_exponent(mx);
+  if (lane == 0) exps[(long long)(c0 / KAPPA) * rows_pad + r] = e;
+#pragma unroll
+  for (int t = 0; t < KAPPA / 32; ++t) write_digits(v[t], e, s, dig + (long long)r * k_pad + c0 + lane + 32 * t, plane);
+  (void)status;
+}
+
+// Role B (the operand is K x N row-major; digits are wanted K-major per column): a block of 256
+// threads owns 16 columns of one chunk, stages the KAPPA x 16 block through shared memory, and
+// each warp slices 2 columns.  digits[p][col][k], exps[chunk][col].
+__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ X, long long ld, int tri,
+                                                         int krows, int cols, int cols_pad, int k_pad, int s,
+                                                         __nv_bfloat16* __restrict__ dig, int* __restrict__ exps,
+                                                         int* status) {
+  __shared__ double tile[KAPPA][17];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * 16;
+  const int c0 = blockIdx.y * KAPPA;
+  const long long plane = (long long)cols_pad * k_pad;
+  for (int e = threadIdx.x; e < KAPPA * 16; e += 256) {
+    const int rr = e / 16, cc = e % 16;
+    tile[rr][cc] = view_load(X, ld, c0 + rr, n0 + cc, tri, krows, cols);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int cc = 0; cc < 2; ++cc) {
+    const int col = warp * 2 + cc;
     double v[KAPPA / 32];
     double mx = 0.0;
 #pragma unroll
     for (int t = 0; t < KAPPA / 32; ++t) {
-      v[t] = view_load(X, ld, r, c0 + lane + 32 * t, tri, rows, cols);
+      v[t] = tile[lane + 32 * t][col];
       mx = fmax(mx, fabs(v[t]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = chunk_exponent(mx);
-    if (lane == 0) exps[(long long)(c0 / KAPPA) * rows_pad + r] = e;
-    best = max(best, e);
+    const int n = n0 + col;
+    if (lane == 0) exps[(long long)(c0 / KAPPA) * cols_pad + n] = e;
 #pragma unroll
-    for (int t = 0; t < KAPPA / 32; ++t)
-      write_digits(v[t], e, s, dig + (long long)r * k_pad + c0 + lane + 32 * t, plane);
+    for (int t = 0; t < KAPPA / 32; ++t) write_digits(v[t], e, s, dig + (long long)n * k_pad + c0 + lane + 32 * t, plane);
   }
-  if (lane == 0) rmax[r] = best;
-}
-
-// Role B (the operand is K x N row-major; digits are wanted K-major per column): a block of 256
-// threads owns 32 columns, stages each 128 x 32 chunk through shared memory, and each warp
-// slices 4 columns.  digits[p][col][k], exps[chunk][col], rmax[col].
-__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ X, long long ld, int tri,
-                                                         int krows, int cols, int cols_pad, int k_pad, int s,
-                                                         __nv_bfloat16* __restrict__ dig, int* __restrict__ exps,
-                                                         int* __restrict__ rmax) {
-  __shared__ double tile[KAPPA][33];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n0 = blockIdx.x * 32;
-  const long long plane = (long long)cols_pad * k_pad;
-  int best[4] = {EXP_ZERO, EXP_ZERO, EXP_ZERO, EXP_ZERO};
-  for (int c0 = 0; c0 < k_pad; c0 += KAPPA) {
-    __syncthreads();
-    for (int rr = warp; rr < KAPPA; rr += 8) tile[rr][lane] = view_load(X, ld, c0 + rr, n0 + lane, tri, krows, cols);
-    __syncthreads();
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const int col = warp * 4 + cc;
-      double v[KAPPA / 32];
-      double mx = 0.0;
-#pragma unroll
-      for (int t = 0; t < KAPPA / 32; ++t) {
-        v[t] = tile[lane + 32 * t][col];
-        mx = fmax(mx, fabs(v[t]));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      const int e = chunk_exponent(mx);
-      const int n = n0 + col;
-      if (lane == 0) exps[(long long)(c0 / KAPPA) * cols_pad + n] = e;
-      best[cc] = max(best[cc], e);
-#pragma unroll
-      for (int t = 0; t < KAPPA / 32; ++t)
-        write_digits(v[t], e, s, dig + (long long)n * k_pad + c0 + lane + 32 * t, plane);
-    }
-  }
-  if (lane == 0)
-    for (int cc = 0; cc < 4; ++cc) rmax[n0 + warp * 4 + cc] = best[cc];
+  (void)status;
 }
 
 // ---- the split GEMM --------------------------------------------------------------------------
 
 struct SplitArgs {
   const int* eA;     // [K_pad / KAPPA][ma_pad]
-  const int* RA;     // [ma_pad]
   const int* eB;     // [K_pad / KAPPA][nb_pad]
-  const int* RB;     // [nb_pad]
   int ma_pad, nb_pad;
   int M, N, K;       // M, N, K multiples of 64
   int s;
@@ -306,9 +303,8 @@ struct SplitArgs {
   int32_t* D;        // fused decode (nullptr: off)
   long long ldd;
   int d_rows, d_cols;
-  int diag_off;      // global index offset of the tile origin, for D_ii = 0
   double log_gamma, tau;
-  int* status;
+  int* status;       // [0] first error, [1] detail, [2] precision flags (RD_FLAG_RANGE)
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -325,7 +321,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   int* ecol_s = (int*)(smem + 2 * STAGES * TILE_BYTES + 256);  // [2][TN]
+  int* rb_s = (int*)(smem + RB_OFFSET);                          // [TN]
   float* lo_s = (float*)(smem + LO_OFFSET);                      // [TN][TM], column-major
+  int8_t* fl_s = (int8_t*)(smem + FL_OFFSET);                    // [TN][TM], column-major
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int tiles_n = (p.N + TN - 1) / TN;
@@ -336,7 +334,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, m0);
   if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, n0);
   if (p.b_tri == RD_TRI_UPPER) kend = min(kend, n0 + TN);
-  const int nchunks = (kbeg < kend) ? (kend - kbeg + KAPPA - 1) / KAPPA : 0;
+  // chunks are aligned to absolute multiples of KAPPA; the first and last may be partial
+  const int cbeg = kbeg / KAPPA;
+  const int nchunks = (kbeg < kend) ? (kend + KAPPA - 1) / KAPPA - cbeg : 0;
   const int s = p.s;
 
   if (threadIdx.x == 0) {
@@ -369,8 +369,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       int it = 0;
       bool ok = true;
       for (int c = 0; c < nloop && ok; ++c) {
-        const int kc0 = kbeg + c * KAPPA;
-        const int ksteps = min(KAPPA, kend - kc0) / TK;
+        const int kc0 = max(kbeg, (cbeg + c) * KAPPA);
+        const int ksteps = (min(kend, (cbeg + c + 1) * KAPPA) - kc0) / TK;
         for (int g = 0; g < s && ok; ++g)
           for (int pa = 0; pa <= g && ok; ++pa)
             for (int ks = 0; ks < ksteps; ++ks, ++it) {
@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       int it = 0, gi = 0;
       bool ok = true;
       for (int c = 0; c < nloop && ok; ++c) {
-        const int kc0 = kbeg + c * KAPPA;
-        const int ksteps = min(KAPPA, kend - kc0) / TK;
+        const int kc0 = max(kbeg, (cbeg + c) * KAPPA);
+        const int ksteps = (min(kend, (cbeg + c + 1) * KAPPA) - kc0) / TK;
         for (int g = 0; g < s && ok; ++g, ++gi) {
           const int buf = gi & 1;
           const uint32_t use = (uint32_t)(gi >> 1);
@@ -431,23 +431,36 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int half = ew >> 2;          // column half of the tile
     const int lrow = quarter * 32 + lane;
     const int row = m0 + lrow;
-    const int ra = p.RA[row];
-    // float-float accumulators: high words in registers, low words in shared memory
+    // reference exponents of this tile: largest chunk exponent of the row (column) over the chunks
+    // the tile visits, so every scaled group term is at most 2^-14
+    int ra = EXP_ZERO;
+    for (int c = 0; c < nloop; ++c) ra = max(ra, p.eA[(long long)(cbeg + c) * p.ma_pad + row]);
+    if (ew < 4) {
+      const int t = ew * 32 + lane;
+      int rb = EXP_ZERO;
+      for (int c = 0; c < nloop; ++c) rb = max(rb, p.eB[(long long)(cbeg + c) * p.nb_pad + n0 + t]);
+      rb_s[t] = rb;
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+    // float-float accumulators: high words in registers, low words in shared memory; per entry,
+    // the largest exponent (relative to the tile reference) of a term flushed below FP32's range
     float hi[64];
-    float* lo = lo_s + (half * 64) * TM + lrow;  // lo[j * TM]
+    float* lo = lo_s + (half * 64) * TM + lrow;   // lo[j * TM]
+    int8_t* fl = fl_s + (half * 64) * TM + lrow;  // fl[j * TM]; -128 = nothing flushed
 #pragma unroll
     for (int j = 0; j < 64; ++j) {
       hi[j] = 0.f;
       lo[j * TM] = 0.f;
+      fl[j * TM] = -128;
     }
     int gi = 0;
     bool ok = true;
     for (int c = 0; c < nloop; ++c) {  // every warp passes the barrier once per chunk
-      const int kc = (kbeg + c * KAPPA) / KAPPA;
+      const int kc = cbeg + c;
       const int cb = c & 1;
       if (ew < 4) {
         const int t = ew * 32 + lane;  // 0..127: one column each
-        ecol_s[cb * TN + t] = p.eB[(long long)kc * p.nb_pad + n0 + t] - p.RB[n0 + t];
+        ecol_s[cb * TN + t] = p.eB[(long long)kc * p.nb_pad + n0 + t] - rb_s[t];
       }
       asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
       if (!ok) continue;
@@ -475,7 +488,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int j = t * 16 + jj;
             const float G = __uint_as_float(r[jj]);
             const int x = base + ecol_s[cb * TN + half * 64 + j];
-            const float sc = (x >= -126 && x <= 0) ? __int_as_float((x + 127) << 23) : 0.f;
+            float sc = 0.f;
+            if (x >= -126 && x <= 0) {
+              sc = __int_as_float((x + 127) << 23);
+            } else if (G != 0.f) {
+              const int fe = max(-127, x + ((__float_as_int(G) >> 23) & 0xFF) - 127);
+              if (fe > fl[j * TM]) fl[j * TM] = (int8_t)fe;
+            }
             const float term = G * sc;
             const float sum = hi[j] + term;
             const float bp = sum - hi[j];
@@ -494,16 +513,23 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
     if (ok && !*abort_flag) {
+      bool lost = false;
 #pragma unroll
       for (int j = 0; j < 64; ++j) {
         const int col = n0 + half * 64 + j;
         if (row >= p.M || col >= p.N) continue;
-        double v = ldexp((double)hi[j] + (double)lo[j * TM], ra + p.RB[col]);
+        const int ref = ra + rb_s[half * 64 + j];
+        double v = ldexp((double)hi[j] + (double)lo[j * TM], ref);
         v = p.alpha * v;
         if (p.C && row < p.c_rows && col < p.c_cols) {
           double* cp = p.C + (long long)row * p.ldc + col;
           if (p.beta != 0.0) v = fma(p.beta, *cp, v);
           if (p.store_c) *cp = v;
+        }
+        const int f = fl[j * TM];
+        if (f > -128) {  // something was flushed: does it matter next to the entry written?
+          const int ve = (v != 0.0) ? (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1023 : -4096;
+          lost |= (f + ref) > ve - FLUSH_MARGIN;
         }
         if (p.D && row < p.d_rows && col < p.d_cols) {
           int32_t d;
@@ -516,6 +542,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           p.D[(long long)row * p.ldd + col] = d;
         }
       }
+      if (lost && p.status) atomicOr(&p.status[2], RD_FLAG_RANGE);
     }
   }
   __syncthreads();
@@ -527,31 +554,36 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// Autotuner probe comparison: D mismatches and the largest relative error of Y over n x n.
-__global__ void probe_compare_kernel(const int32_t* __restrict__ D0, const int32_t* __restrict__ D1,
-                                     const double* __restrict__ Y0, const double* __restrict__ Y1, long long nn,
-                                     unsigned long long* __restrict__ res) {
-  unsigned long long mis = 0;
+// Entrywise relative residual of sampled rows y of Y against the exact M: y^T M = e_g^T, i.e.
+//   r_j = y_j - [j == g] - sum_{i : edge j -> i} X_ij y_i,   X = gamma A or gamma^W,
+// relative to |y_j - [j == g]| + sum |X_ij y_i|.  Every product is FP64 here.  Because M is an
+// M-matrix with Y >= 0, a small entrywise residual bounds the entrywise error of the row
+// (error^T = r^T Y), and a wrong region of a row shows up where it meets the right part.
+// The largest relative residual is OR-ed into res (bits of a non-negative double).
+__global__ void row_residual_kernel(const double* __restrict__ rows, const int32_t* __restrict__ goals, int k,
+                                    int n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ succ,
+                                    const uint8_t* __restrict__ A, const float* __restrict__ W, double gamma,
+                                    unsigned long long* __restrict__ res) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double worst = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
-    mis += (D0[t] != D1[t]);
-    const double y0 = Y0[t], y1 = Y1[t];
-    double r = 0.0;
-    if (y0 != 0.0)
-      r = fabs(y1 - y0) / fabs(y0);
-    else if (y1 != 0.0)
-      r = 1.0;
-    if (!(r <= 1e300)) r = 1e300;  // NaN or inf
-    worst = fmax(worst, r);
+  if (t < (long long)k * n) {
+    const int c = (int)(t / n), j = (int)(t % n);
+    const double* y = rows + (long long)c * n;
+    double acc = y[j] - (goals[c] == j ? 1.0 : 0.0);
+    double scale = fabs(acc);
+    for (int q = ptr[j]; q < ptr[j + 1]; ++q) {
+      const int i = succ[q];
+      const double x = W ? pow(gamma, (double)W[(long long)i * n + j]) : gamma;
+      const double term = x * y[i];
+      acc -= term;
+      scale += fabs(term);
+    }
+    (void)A;
+    worst = scale > 0.0 ? fabs(acc) / scale : (acc != 0.0 ? 1.0 : 0.0);
+    if (!(worst <= 1.0)) worst = 1.0;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    mis += __shfl_xor_sync(0xffffffffu, mis, o);
-    worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&res[0], mis);
-    atomicMax(&res[1], (unsigned long long)__double_as_longlong(worst));
-  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0 && worst > 0.0) atomicMax(res, (unsigned long long)__double_as_longlong(worst));
 }
 
 // ---- host side ---------------------------------------------------------------------------------
@@ -596,24 +628,10 @@ struct View {
 
 struct rd_split_plan {
   int N = 0, s = 0;
-  // probe of the slice-count autotuner (leading PM x PM block of M)
-  int pm = 0;
-  double* pM = nullptr;
-  double* pLU = nullptr;
-  double* pT = nullptr;
-  double* pS = nullptr;
-  double* pYref = nullptr;
-  double* pYs = nullptr;
-  int32_t* pDref = nullptr;
-  int32_t* pDs = nullptr;
-  unsigned long long* pRes = nullptr;  // [0] D mismatches, [1] bits of the largest relative Y error
-  int* pStatus = nullptr;
   __nv_bfloat16* digA = nullptr;
   __nv_bfloat16* digB = nullptr;
   int* eA = nullptr;
   int* eB = nullptr;
-  int* RA = nullptr;
-  int* RB = nullptr;
   int64_t bytes = 0;
 };
 
@@ -624,9 +642,10 @@ cudaError_t slice_a(rd_ctx* h, const View& v, int rows_pad, int k_pad, cudaStrea
   rd_split_plan* P = h->split;
   cudaError_t e = rd_prof_begin(h, st, false);
   if (e != cudaSuccess) return e;
-  const int blocks = (rows_pad * 32 + 255) / 256;
+  const long long warps = (long long)rows_pad * (k_pad / KAPPA);
+  const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
   slice_rows_kernel<<<blocks, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, rows_pad, k_pad, P->s, P->digA, P->eA,
-                                            P->RA);
+                                            h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, st, false, 0.0);
 }
@@ -636,19 +655,23 @@ cudaError_t slice_b(rd_ctx* h, const View& v, int cols_pad, int k_pad, cudaStrea
   rd_split_plan* P = h->split;
   cudaError_t e = rd_prof_begin(h, st, false);
   if (e != cudaSuccess) return e;
-  slice_cols_kernel<<<cols_pad / 32, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, cols_pad, k_pad, P->s, P->digB,
-                                                   P->eB, P->RB);
+  slice_cols_kernel<<<dim3(cols_pad / 16, k_pad / KAPPA), 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, cols_pad,
+                                                                        k_pad, P->s, P->digB, P->eB, h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, st, false, 0.0);
 }
 
 // C (M x N) = alpha * A (M x K) * B (K x N) + beta * C, or the decode of the product into D.
+// C (c_rows x c_cols, ldc) = alpha * A (M x K) * B (K x N) + beta * C; with D != nullptr the product is
+// decoded into D (n x n) instead and Ystore (n x n, may be null) receives Y.  `flops` is the
+// algorithmic count of one product; the profile counts the issued digit products.
 cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, int K, double alpha, double beta,
-                       double* C, long long ldc, int32_t* D, double* Ystore, double flops, cudaStream_t st) {
+                       double* C, long long ldc, int c_rows, int c_cols, int32_t* D, double* Ystore, double flops,
+                       cudaStream_t st) {
   rd_split_plan* P = h->split;
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   if (M % 64 || N % 64 || K % 64) return cudaErrorInvalidValue;
-  const int ma_pad = round_up(M, TM), nb_pad = round_up(N, TN), k_pad = round_up(K, KAPPA);
+  const int ma_pad = round_up(M, TM), nb_pad = round_up(N, TN), k_pad = round_up(K, KAPPA);  // k_pad <= N + 128
   cudaError_t e;
   if ((e = slice_a(h, A, ma_pad, k_pad, st)) != cudaSuccess) return e;
   if ((e = slice_b(h, B, nb_pad, k_pad, st)) != cudaSuccess) return e;
@@ -657,9 +680,7 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   if ((e = make_map(&tb, P->digB, k_pad, (long long)P->s * nb_pad)) != cudaSuccess) return e;
   SplitArgs a{};
   a.eA = P->eA;
-  a.RA = P->RA;
   a.eB = P->eB;
-  a.RB = P->RB;
   a.ma_pad = ma_pad;
   a.nb_pad = nb_pad;
   a.M = M;
@@ -673,8 +694,8 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   a.C = D ? Ystore : C;
   a.ldc = D ? h->n : ldc;
   a.store_c = (a.C != nullptr);
-  a.c_rows = D ? h->n : M;
-  a.c_cols = D ? h->n : N;
+  a.c_rows = D ? h->n : c_rows;
+  a.c_cols = D ? h->n : c_cols;
   a.D = D;
   a.ldd = h->n;
   a.d_rows = D ? h->n : 0;
@@ -693,16 +714,45 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   if ((e = rd_prof_begin(h, st, true)) != cudaSuccess) return e;
   split_gemm_kernel<<<tiles, THREADS, SMEM_BYTES, st>>>(ta, tb, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, st, true, flops);
+  return rd_prof_end(h, st, true, flops * (double)P->s * (P->s + 1) / 2.0);
 }
 
 inline View full(const double* p, long long ld, int rows, int cols) { return View{p, ld, rows, cols, RD_TRI_FULL}; }
 inline View tri(const double* p, long long ld, int n, int mode) { return View{p, ld, n, n, mode}; }
 
+// Below this node size the recursion's products run in FP64 with small tiles: they are too
+// small to fill the tensor cores (one or a few 128 x 128 tiles), while an FP64 product on 16 x 16
+// tiles spreads over every SM.
+constexpr int FP64_NODE = 1024;
+
+cudaError_t product(rd_ctx* h, bool fp64, const View& A, const View& B, int M, int N, int K, double alpha,
+                    double beta, double* C, long long ldc, double flops, cudaStream_t st) {
+  if (!fp64) return split_gemm(h, A, B, M, N, K, alpha, beta, C, ldc, M, N, nullptr, nullptr, flops, st);
+  rd_gemm_f64_args g{};
+  g.A = A.p;
+  g.lda = A.ld;
+  g.a_tri = A.tri;
+  g.B = B.p;
+  g.ldb = B.ld;
+  g.b_tri = B.tri;
+  g.C = C;
+  g.ldc = ldc;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.store_c = 1;
+  g.c_rows = M;
+  g.c_cols = N;
+  return rd_gemm_f64(h, &g, 1, st, flops);
+}
+
 // Recursive factorisation of the diagonal range [lo, hi) (see the header comment).
 cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
   const int m = hi - lo;
   if (m <= LEAF) return rd_lu_diag(h, lo, st);
+  const bool f64 = m <= FP64_NODE;
   const int mid = lo + ((m / 2 + LEAF - 1) / LEAF) * LEAF;
   const int m1 = mid - lo, m2 = hi - mid;
   const long long N = h->N;
@@ -713,117 +763,71 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
   double* A12 = LU + (long long)lo * N + mid;
   double* A21 = LU + (long long)mid * N + lo;
   double* A22 = LU + (long long)mid * N + mid;
+  double* T11 = T + (long long)lo * N + lo;
+  double* T22 = T + (long long)mid * N + mid;
   const double t1 = (double)m1 * (m1 + 1) / 2, t2 = (double)m2 * (m2 + 1) / 2;
-  // U12 = L11^-1 A12 ; L21 = A21 U11^-1
-  if ((e = split_gemm(h, tri(T + (long long)lo * N + lo, N, m1, RD_TRI_LOWER_UNIT), full(A12, N, m1, m2), m1, m2, m1,
-                      1.0, 0.0, A12, N, nullptr, nullptr, 2.0 * t1 * m2, st)) != cudaSuccess)
-    return e;
-  if ((e = split_gemm(h, full(A21, N, m2, m1), tri(T + (long long)lo * N + lo, N, m1, RD_TRI_UPPER), m2, m1, m1, 1.0,
-                      0.0, A21, N, nullptr, nullptr, 2.0 * t1 * m2, st)) != cudaSuccess)
-    return e;
+  // U12 = L11^-1 A12 ; L21 = A21 U11^-1.  The split products slice their operands before they
+  // write, so they run in place; the small-tile FP64 products do not own whole strips, so they
+  // write to the scratch and the result is copied back.
+  double* W0 = h->dS;  // free until the inverse products below
+  if (f64) {
+    if ((e = product(h, true, tri(T11, N, m1, RD_TRI_LOWER_UNIT), full(A12, N, m1, m2), m1, m2, m1, 1.0, 0.0, W0, m2,
+                     2.0 * t1 * m2, st)) != cudaSuccess)
+      return e;
+    if ((e = rd_copy_rows_out(h, W0, m2, m1, m2, A12, N, st)) != cudaSuccess) return e;
+    if ((e = product(h, true, full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_UPPER), m2, m1, m1, 1.0, 0.0, W0, m1,
+                     2.0 * t1 * m2, st)) != cudaSuccess)
+      return e;
+    if ((e = rd_copy_rows_out(h, W0, m1, m2, m1, A21, N, st)) != cudaSuccess) return e;
+  } else {
+    if ((e = product(h, false, tri(T11, N, m1, RD_TRI_LOWER_UNIT), full(A12, N, m1, m2), m1, m2, m1, 1.0, 0.0, A12,
+                     N, 2.0 * t1 * m2, st)) != cudaSuccess)
+      return e;
+    if ((e = product(h, false, full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_UPPER), m2, m1, m1, 1.0, 0.0, A21, N,
+                     2.0 * t1 * m2, st)) != cudaSuccess)
+      return e;
+  }
   // A22 -= L21 U12
-  if ((e = split_gemm(h, full(A21, N, m2, m1), full(A12, N, m1, m2), m2, m2, m1, -1.0, 1.0, A22, N, nullptr, nullptr,
-                      2.0 * m2 * (double)m2 * m1, st)) != cudaSuccess)
+  if ((e = product(h, f64, full(A21, N, m2, m1), full(A12, N, m1, m2), m2, m2, m1, -1.0, 1.0, A22, N,
+                   2.0 * m2 * (double)m2 * m1, st)) != cudaSuccess)
     return e;
   if ((e = factor(h, mid, hi, st)) != cudaSuccess) return e;
   // L^-1_21 = -L22^-1 (L21 L11^-1) ; U^-1_12 = -U11^-1 (U12 U22^-1)
   double* SL = h->dS;                         // m2 x m1
   double* SU = h->dS + (long long)m1 * m2;    // m1 x m2
-  if ((e = split_gemm(h, full(A21, N, m2, m1), tri(T + (long long)lo * N + lo, N, m1, RD_TRI_LOWER_UNIT), m2, m1, m1,
-                      1.0, 0.0, SL, m1, nullptr, nullptr, 2.0 * t1 * m2, st)) != cudaSuccess)
+  if ((e = product(h, f64, full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_LOWER_UNIT), m2, m1, m1, 1.0, 0.0, SL, m1,
+                   2.0 * t1 * m2, st)) != cudaSuccess)
     return e;
-  if ((e = split_gemm(h, tri(T + (long long)mid * N + mid, N, m2, RD_TRI_LOWER_UNIT), full(SL, m1, m2, m1), m2, m1,
-                      m2, -1.0, 0.0, T + (long long)mid * N + lo, N, nullptr, nullptr, 2.0 * t2 * m1, st)) !=
-      cudaSuccess)
+  if ((e = product(h, f64, tri(T22, N, m2, RD_TRI_LOWER_UNIT), full(SL, m1, m2, m1), m2, m1, m2, -1.0, 0.0,
+                   T + (long long)mid * N + lo, N, 2.0 * t2 * m1, st)) != cudaSuccess)
     return e;
-  if ((e = split_gemm(h, full(A12, N, m1, m2), tri(T + (long long)mid * N + mid, N, m2, RD_TRI_UPPER), m1, m2, m2,
-                      1.0, 0.0, SU, m2, nullptr, nullptr, 2.0 * t2 * m1, st)) != cudaSuccess)
+  if ((e = product(h, f64, full(A12, N, m1, m2), tri(T22, N, m2, RD_TRI_UPPER), m1, m2, m2, 1.0, 0.0, SU, m2,
+                   2.0 * t2 * m1, st)) != cudaSuccess)
     return e;
-  return split_gemm(h, tri(T + (long long)lo * N + lo, N, m1, RD_TRI_UPPER), full(SU, m2, m1, m2), m1, m2, m1, -1.0,
-                    0.0, T + (long long)lo * N + mid, N, nullptr, nullptr, 2.0 * t1 * m2, st);
+  return product(h, f64, tri(T11, N, m1, RD_TRI_UPPER), full(SU, m2, m1, m2), m1, m2, m1, -1.0, 0.0,
+                 T + (long long)lo * N + mid, N, 2.0 * t1 * m2, st);
 }
 
-}  // namespace
-
-namespace {
-
-constexpr int PROBE_M = 256;           // probe block (leading PROBE_M x PROBE_M of M)
-constexpr double PROBE_TOL = 1e-11;    // largest accepted relative error of Y on the probe
-const int kCandidates[] = {8, 12, 16};
-
-// Run the probe through the FP64 path once and through the split path with increasing digit
-// counts; keep the first count whose decoded D equals the FP64 one and whose Y agrees within
-// PROBE_TOL.  The probe is the leading block of M (itself a strictly diagonally dominant
-// M-matrix of the same graph), so it sees the same within-chunk ranges as the full inverse.
-rd_status autotune(rd_ctx* h, int* chosen) {
-  rd_split_plan* P = h->split;
-  cudaStream_t st = h->stream;
-  const int m = P->pm;
-  const size_t mm = (size_t)m * m;
-  rd_ctx v;  // a view of the probe buffers; owns nothing
-  v.device = h->device;
-  v.n = h->n < m ? h->n : m;
-  v.N = m;
-  v.gamma = h->gamma;
-  v.tau = h->tau;
-  v.stream = st;
-  v.dLU = P->pLU;
-  v.dT = P->pT;
-  v.dS = P->pS;
-  v.dStatus = P->pStatus;
-  v.split = P;
-#define AT_CK(call)                                        \
-  do {                                                     \
-    cudaError_t _e = (call);                               \
-    if (_e != cudaSuccess) {                               \
-      v.split = nullptr;                                   \
-      h->err = std::string("slice autotuner: ") + #call + ": " + cudaGetErrorString(_e); \
-      return RD_ERR_CUDA;                                  \
-    }                                                      \
-  } while (0)
-  AT_CK(cudaMemcpy2DAsync(P->pM, m * sizeof(double), h->dLU, (size_t)h->N * sizeof(double), m * sizeof(double), m,
-                          cudaMemcpyDeviceToDevice, st));
-  AT_CK(cudaMemsetAsync(P->pStatus, 0, 2 * sizeof(int), st));
-  AT_CK(cudaMemcpyAsync(P->pLU, P->pM, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  AT_CK(rd_lu_f64(&v, st));
-  AT_CK(rd_trtri_f64(&v, st));
-  AT_CK(rd_trmm_decode_f64(&v, P->pDref, P->pYref, st));
-  *chosen = kCandidates[sizeof(kCandidates) / sizeof(int) - 1];
-  for (int cand : kCandidates) {
-    P->s = cand;
-    AT_CK(cudaMemcpyAsync(P->pLU, P->pM, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    AT_CK(rd_lu_split(&v, st));
-    AT_CK(rd_trmm_decode_split(&v, P->pDs, P->pYs, st));
-    AT_CK(cudaMemsetAsync(P->pRes, 0, 2 * sizeof(unsigned long long), st));
-    probe_compare_kernel<<<64, 256, 0, st>>>(P->pDref, P->pDs, P->pYref, P->pYs, (long long)v.n * v.n, P->pRes);
-    AT_CK(cudaGetLastError());
-    h->launches += v.launches + 1;
-    v.launches = 0;
-    unsigned long long res[2];
-    int pst[2];
-    AT_CK(cudaMemcpyAsync(res, P->pRes, sizeof(res), cudaMemcpyDeviceToHost, st));
-    AT_CK(cudaMemcpyAsync(pst, P->pStatus, sizeof(pst), cudaMemcpyDeviceToHost, st));
-    AT_CK(cudaStreamSynchronize(st));
-    double worst;
-    memcpy(&worst, &res[1], sizeof(double));
-    if (pst[0] != RD_DEV_OK) break;  // the probe itself failed: take the largest count
-    if (res[0] == 0 && worst <= PROBE_TOL) {
-      *chosen = cand;
-      break;
-    }
+// rows goals[c] of U^-1 (upper part of T, zero left of the diagonal) into R (64 x N)
+__global__ void gather_uinv_rows_kernel(const double* __restrict__ T, long long N, const int32_t* __restrict__ goals,
+                                        int k, double* __restrict__ R) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)RD_MAX_GOALS * N) return;
+  const int c = (int)(t / N);
+  const long long j = t % N;
+  double v = 0.0;
+  if (c < k) {
+    const long long g = goals[c];
+    if (j >= g) v = T[g * N + j];
   }
-  h->launches += v.launches;
-  v.split = nullptr;
-#undef AT_CK
-  return RD_OK;
+  R[t] = v;
 }
 
 }  // namespace
 
-rd_status rd_split_prepare(rd_ctx* h) {
-  const int s_req = h->slices_req;
-  if (s_req != 0 && (s_req < 2 || s_req > MAX_SLICES)) {
-    h->err = "split precision needs 2..16 slices (0 = autotune)";
+rd_status rd_split_prepare(rd_ctx* h, int s) {
+  if (s < 2 || s > MAX_SLICES) {
+    h->err = "split precision needs 2..15 digits (0 = chosen by the library)";
     return RD_ERR_ARG;
   }
   if (!encode_fn()) {
@@ -835,12 +839,9 @@ rd_status rd_split_prepare(rd_ctx* h) {
     rd_split_plan* P = new rd_split_plan();
     h->split = P;
     P->N = h->N;
-    P->pm = h->N < PROBE_M ? h->N : PROBE_M;
-    const size_t NN = (size_t)h->N * h->N;
-    const size_t mm = (size_t)P->pm * P->pm;
-    const size_t dig = (size_t)MAX_SLICES * NN * sizeof(__nv_bfloat16);
-    const size_t ex = (NN / KAPPA + 64) * sizeof(int);
-    const size_t rm = ((size_t)h->N + 256) * sizeof(int);
+    const size_t NK = (size_t)h->N * ((size_t)h->N + KAPPA);  // rows x K padded to whole chunks
+    const size_t dig = (size_t)MAX_SLICES * NK * sizeof(__nv_bfloat16);
+    const size_t ex = (NK / KAPPA + 64) * sizeof(int);
     cudaError_t e = cudaSuccess;
     auto get = [&](void** ptr, size_t bytes) {
       if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
@@ -850,29 +851,12 @@ rd_status rd_split_prepare(rd_ctx* h) {
     get((void**)&P->digB, dig);
     get((void**)&P->eA, ex);
     get((void**)&P->eB, ex);
-    get((void**)&P->RA, rm);
-    get((void**)&P->RB, rm);
-    get((void**)&P->pM, mm * sizeof(double));
-    get((void**)&P->pLU, mm * sizeof(double));
-    get((void**)&P->pT, mm * sizeof(double));
-    get((void**)&P->pS, mm * sizeof(double));
-    get((void**)&P->pYref, mm * sizeof(double));
-    get((void**)&P->pYs, mm * sizeof(double));
-    get((void**)&P->pDref, mm * sizeof(int32_t));
-    get((void**)&P->pDs, mm * sizeof(int32_t));
-    get((void**)&P->pRes, 2 * sizeof(unsigned long long));
-    get((void**)&P->pStatus, 2 * sizeof(int));
     if (e != cudaSuccess) {
       rd_split_release(h);
       h->err = std::string("split workspace: ") + cudaGetErrorString(e);
       return e == cudaErrorMemoryAllocation ? RD_ERR_OOM : RD_ERR_CUDA;
     }
     h->bytes += P->bytes;
-  }
-  int s = s_req;
-  if (s == 0) {
-    rd_status st = autotune(h, &s);
-    if (st != RD_OK) return st;
   }
   h->split->s = s;
   h->slices = s;
@@ -882,8 +866,7 @@ rd_status rd_split_prepare(rd_ctx* h) {
 void rd_split_release(rd_ctx* h) {
   rd_split_plan* P = h->split;
   if (!P) return;
-  void* ptrs[] = {P->digA, P->digB, P->eA, P->eB, P->RA, P->RB, P->pM, P->pLU, P->pT, P->pS,
-                  P->pYref, P->pYs, P->pDref, P->pDs, P->pRes, P->pStatus};
+  void* ptrs[] = {P->digA, P->digB, P->eA, P->eB};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   h->bytes -= (h->bytes >= P->bytes) ? P->bytes : 0;
@@ -900,5 +883,54 @@ cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t 
   const int N = h->N;
   const double Nd = (double)N;
   return split_gemm(h, tri(h->dT, N, N, RD_TRI_UPPER), tri(h->dT, N, N, RD_TRI_LOWER_UNIT), N, N, N, 1.0, 0.0,
-                    nullptr, 0, D, Y, 2.0 * Nd * (Nd + 1) * (2 * Nd + 1) / 6.0, s);
+                    nullptr, 0, 0, 0, D, Y, 2.0 * Nd * (Nd + 1) * (2 * Nd + 1) / 6.0, s);
+}
+
+// Self-check of the split result: 64 rows of Y spread over the graph, computed like the goal
+// rows (rows of U^-1 times L^-1, the same digit products as the inverse product), and their
+// largest entrywise relative residual against M.  Synchronises; *worst receives it.
+cudaError_t rd_split_row_check(rd_ctx* h, double* worst, cudaStream_t s) {
+  *worst = 0.0;
+  if (!h->dSucc) return cudaSuccess;  // no successor lists (more than 2^31 edges): not checked
+  const int k = h->n < RD_MAX_GOALS ? h->n : RD_MAX_GOALS;
+  int32_t goals[RD_MAX_GOALS];
+  for (int c = 0; c < k; ++c) goals[c] = (int32_t)(((long long)c * h->n) / k + (h->n / k) / 2);
+  cudaError_t e = cudaMemcpyAsync(h->dGoals, goals, k * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  double* rows = h->dS;  // free after the factorisation (64 x n doubles)
+  if ((e = rd_goal_split(h, h->dGoals, k, rows, s)) != cudaSuccess) return e;
+  if (!h->succ_ready) {
+    if ((e = rd_build_succ(h, s)) != cudaSuccess) return e;
+    h->succ_ready = 1;
+  }
+  unsigned long long* res = reinterpret_cast<unsigned long long*>(h->dRed);  // [0] reused after load
+  if ((e = cudaMemsetAsync(res, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  const long long total = (long long)k * h->n;
+  if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
+  row_residual_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(rows, h->dGoals, k, h->n, h->dDeg + (h->n + 1),
+                                                                       h->dSucc, h->dA, h->weighted ? h->dW : nullptr,
+                                                                       h->gamma, res);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, false, 0.0)) != cudaSuccess) return e;
+  unsigned long long bits = 0;
+  if ((e = cudaMemcpyAsync(&bits, res, sizeof(bits), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  memcpy(worst, &bits, sizeof(double));
+  return cudaSuccess;
+}
+
+// Goal rows from the resident inverses: Y[g, :] = U^-1[g, :] L^-1, all goals in one product
+// (64 x N times the lower-unit view of T), written straight into out (k x n).
+cudaError_t rd_goal_split(rd_ctx* h, const int32_t* dgoals, int k, double* out, cudaStream_t s) {
+  const long long N = h->N;
+  cudaError_t e = rd_prof_begin(h, s, false);
+  if (e != cudaSuccess) return e;
+  const long long total = RD_MAX_GOALS * N;
+  gather_uinv_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->dT, N, dgoals, k, h->dR);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, false, 0.0)) != cudaSuccess) return e;
+  const double Nd = (double)N;
+  return split_gemm(h, full(h->dR, N, RD_MAX_GOALS, (int)N), tri(h->dT, N, (int)N, RD_TRI_LOWER_UNIT), RD_MAX_GOALS,
+                    (int)N, (int)N, 1.0, 0.0, out, h->n, k, h->n, nullptr, nullptr, RD_MAX_GOALS * Nd * (Nd + 1),
+                    s);
 }

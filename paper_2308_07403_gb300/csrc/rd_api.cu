@@ -76,7 +76,7 @@ void free_all(rd_ctx* h) {
     delete[] h->prof_ev;
     h->prof_ev = nullptr;
   }
-  void* ptrs[] = {h->dA, h->dW, h->dLU, h->dT, h->dS, h->dR, h->dStatus, h->dRed, h->dDeg,
+  void* ptrs[] = {h->dA, h->dW, h->dLU, h->dT, h->dS, h->dR, h->dStatus, h->dRed, h->dDeg, h->dColsum,
                   h->dSucc, h->dGoals, h->dNext, h->dYrows, h->dDout, h->dYout};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -119,8 +119,9 @@ rd_status load_impl(rd_ctx* h, const uint8_t* A, const float* W, double gamma) {
   }
   h->gamma = gamma;
   h->factored = h->inverted = 0;
+  h->split_floor = 0;
   h->succ_ready = 0;
-  RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 2 * sizeof(int), h->stream));
+  RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 4 * sizeof(int), h->stream));
   RD_CK(h, rd_build_m(h, h->stream));
   unsigned long long red[3];
   RD_CK(h, cudaMemcpyAsync(red, h->dRed, sizeof(red), cudaMemcpyDeviceToHost, h->stream));
@@ -184,9 +185,10 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
   RD_ALLOC(h->dT, N * N);
   RD_ALLOC(h->dS, N * N / 2);
   RD_ALLOC(h->dR, (size_t)RD_MAX_GOALS * N);
-  RD_ALLOC(h->dStatus, 2);
+  RD_ALLOC(h->dStatus, 4);
   RD_ALLOC(h->dRed, 3);
   RD_ALLOC(h->dDeg, 2 * (size_t)n + 2);
+  RD_ALLOC(h->dColsum, (size_t)n);
   RD_ALLOC(h->dGoals, RD_MAX_GOALS);
 #undef RD_ALLOC
   for (auto& ev : h->ev)
@@ -206,20 +208,63 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
   return RD_OK;
 }
 
+// The split path's self-check (RD_FLAG_RANGE in status word 2, see k_split.cu): read it
+// (synchronises) and clear it.
+rd_status read_split_flags(rd_ctx* h, int* flags) {
+  int st[4];
+  RD_CK(h, cudaMemcpyAsync(st, h->dStatus, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  RD_CK(h, cudaStreamSynchronize(h->stream));
+  *flags = st[2];
+  if (st[2]) RD_CK(h, cudaMemsetAsync(h->dStatus + 2, 0, sizeof(int), h->stream));
+  return RD_OK;
+}
+
+// Split mode with the self-check (RD_FLAG_RANGE from the product epilogue, and the residual of
+// 64 sampled rows of Y against M after the inverse product): when the caller leaves the digit
+// count open, the library starts from RD_SPLIT_START digits; a failed residual raises the floor
+// of the current graph to RD_SPLIT_MAX digits, and a range flag, or a failure at RD_SPLIT_MAX,
+// moves the graph to FP64.  The inverse is then recomputed from M.
+bool split_auto(const rd_ctx* h) { return h->precision == RD_PREC_SPLIT_BF16 && h->slices_req == 0; }
+
+// range: a term left the FP32 accumulators' range -- more digits cannot help, go to FP64;
+// otherwise (the sampled rows' residual failed) try RD_SPLIT_MAX digits first.
+rd_status escalate(rd_ctx* h, bool range) {
+  h->fallbacks++;
+  h->split_floor = (!range && h->slices < RD_SPLIT_MAX) ? RD_SPLIT_MAX : -1;
+  RD_CK(h, cudaMemsetAsync(h->dStatus + 2, 0, sizeof(int), h->stream));
+  RD_CK(h, rd_build_m(h, h->stream));  // M again (the factorisation overwrote it)
+  h->factored = h->inverted = 0;
+  return RD_OK;
+}
+
 rd_status ensure_factored(rd_ctx* h) {
   if (h->factored) return RD_OK;
   RD_CK(h, cudaEventRecord(h->ev[0], h->stream));
-  if (h->precision == RD_PREC_SPLIT_BF16) {
-    rd_status st = rd_split_prepare(h);
+  for (;;) {
+    const bool split = h->precision == RD_PREC_SPLIT_BF16 && h->split_floor >= 0;
+    if (!split) {
+      RD_CK(h, rd_lu_f64(h, h->stream));
+      h->used_precision = RD_PREC_FP64;
+      h->factored = 1;
+      h->inverted = 0;
+      break;
+    }
+    int s = h->slices_req > 0 ? h->slices_req : RD_SPLIT_START;
+    if (h->split_floor > s) s = h->split_floor;
+    rd_status st = rd_split_prepare(h, s);
     if (st != RD_OK) return st;
-    RD_CK(h, rd_lu_split(h, h->stream));
-  } else {
-    RD_CK(h, rd_lu_f64(h, h->stream));
+    RD_CK(h, rd_lu_split(h, h->stream));  // LU and both triangular inverses
+    h->used_precision = RD_PREC_SPLIT_BF16;
+    h->factored = 1;
+    h->inverted = 1;
+    if (!split_auto(h)) break;
+    int flags = 0;
+    if ((st = read_split_flags(h, &flags)) != RD_OK) return st;
+    if (!flags) break;
+    if ((st = escalate(h, true)) != RD_OK) return st;
   }
   RD_CK(h, cudaEventRecord(h->ev[1], h->stream));
   h->ev_used[0] = 1;
-  h->factored = 1;
-  h->inverted = 0;
   return RD_OK;
 }
 
@@ -329,8 +374,9 @@ rd_status rd_set_stream(rd_handle h, void* stream) {
 rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices) {
   if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
   if (mode != RD_PREC_FP64 && mode != RD_PREC_SPLIT_BF16) return fail(h, RD_ERR_ARG, "unknown precision mode");
-  if (slices < 0 || slices > 16) return fail(h, RD_ERR_ARG, "slices must lie in [0, 16]");
+  if (slices < 0 || slices > 15 || slices == 1) return fail(h, RD_ERR_ARG, "slices must be 0 or lie in [2, 15]");
   if (mode != h->precision || slices != h->slices_req) {
+    h->split_floor = 0;
     if (h->factored) {
       // the factors in dLU belong to the old mode: rebuild M from the resident graph
       RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 2 * sizeof(int), h->stream));
@@ -366,14 +412,26 @@ rd_status rd_apsp(rd_handle h, int32_t* D, double* Y) {
   int32_t* dD = d_host ? h->dDout : D;
   double* dY = Y ? (y_host ? h->dYout : Y) : nullptr;
   RD_CK(h, cudaEventRecord(h->ev[2], h->stream));
-  if (h->precision == RD_PREC_SPLIT_BF16) {
-    if (!h->inverted) RD_CK(h, rd_trtri_split(h, h->stream));
-    h->inverted = 1;
-    RD_CK(h, rd_trmm_decode_split(h, dD, dY, h->stream));
-  } else {
+  for (;;) {
+    if (h->used_precision == RD_PREC_SPLIT_BF16) {
+      RD_CK(h, rd_trmm_decode_split(h, dD, dY, h->stream));
+      if (!split_auto(h)) break;
+      int flags = 0;
+      if ((st = read_split_flags(h, &flags)) != RD_OK) return st;
+      if (!flags) {
+        double worst = 0.0;  // residual of sampled rows of Y against M
+        RD_CK(h, rd_split_row_check(h, &worst, h->stream));
+        h->last_residual = worst;
+        if (worst <= RD_SPLIT_RESIDUAL) break;
+      }
+      if ((st = escalate(h, flags != 0)) != RD_OK) return st;
+      if ((st = ensure_factored(h)) != RD_OK) return st;
+      continue;
+    }
     if (!h->inverted) RD_CK(h, rd_trtri_f64(h, h->stream));
     h->inverted = 1;
     RD_CK(h, rd_trmm_decode_f64(h, dD, dY, h->stream));
+    break;
   }
   RD_CK(h, cudaEventRecord(h->ev[3], h->stream));
   h->ev_used[1] = 1;
@@ -395,7 +453,10 @@ rd_status rd_goal_solve(rd_handle h, const int32_t* goals, int32_t k, double* Y_
   if (host && !h->dYrows) RD_CK(h, dalloc(h, &h->dYrows, (size_t)RD_MAX_GOALS * h->n));
   double* dst = host ? h->dYrows : Y_out;
   RD_CK(h, cudaEventRecord(h->ev[4], h->stream));
-  RD_CK(h, rd_goal_f64(h, h->dGoals, k, dst, h->stream));
+  if (h->used_precision == RD_PREC_SPLIT_BF16 && h->inverted)
+    RD_CK(h, rd_goal_split(h, h->dGoals, k, dst, h->stream));  // rows of U^-1 times L^-1
+  else
+    RD_CK(h, rd_goal_f64(h, h->dGoals, k, dst, h->stream));
   RD_CK(h, cudaEventRecord(h->ev[5], h->stream));
   h->ev_used[2] = 1;
   if (host) {
@@ -450,6 +511,9 @@ rd_status rd_get_stats(rd_handle h, rd_stats* s) {
   s->n_padded = h->N;
   s->precision = h->precision;
   s->slices = h->precision == RD_PREC_SPLIT_BF16 ? h->slices : 0;
+  s->precision_used = h->used_precision;
+  s->fallbacks = h->fallbacks;
+  s->split_residual = h->last_residual;
   s->gamma = h->gamma;
   s->max_column_sum = h->max_colsum;
   s->tau = h->tau;

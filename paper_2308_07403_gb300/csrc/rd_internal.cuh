@@ -27,6 +27,10 @@
 #define RD_DEV_PIVOT 1      // non-positive or non-finite pivot
 #define RD_DEV_NONFINITE 2  // non-finite entry of Y
 #define RD_DEV_TIMEOUT 3    // a bounded wait expired
+// precision flags, OR-ed into status word [2] (not errors: the split path's self-check)
+#define RD_FLAG_RANGE 1     // a digit-product term fell out of the FP32 accumulator range
+#define RD_SPLIT_START 12   // digit count the split mode starts from when the caller leaves it open
+#define RD_SPLIT_MAX 15     // largest digit count (exact group sums)
 
 struct rd_split_plan;       // defined by the split path
 
@@ -45,9 +49,10 @@ struct rd_ctx {
   double* dT = nullptr;
   double* dS = nullptr;
   double* dR = nullptr;
-  int* dStatus = nullptr;      // [0] code, [1] detail
+  int* dStatus = nullptr;      // [0] code, [1] detail, [2] precision flags, [3] spare
   unsigned long long* dRed = nullptr;  // reductions: [0] max degree, [1] max column sum bits
   int32_t* dDeg = nullptr;     // n+1: out-degree, then exclusive prefix (successor CSR ptr)
+  double* dColsum = nullptr;   // n: column sums of X (gain check)
   int32_t* dSucc = nullptr;    // successor CSR indices
   int64_t succ_cap = 0;
   int succ_ready = 0;
@@ -59,6 +64,10 @@ struct rd_ctx {
 
   int factored = 0;            // dLU holds the factors of the current graph
   int inverted = 0;            // dT holds the triangular inverses
+  int used_precision = RD_PREC_FP64;  // precision that produced the current factors
+  int split_floor = 0;         // per graph: least digit count to use, -1 = FP64 (self-check history)
+  int fallbacks = 0;           // split results redone (more digits or FP64) after the self-check
+  double last_residual = 0.0;  // largest sampled-row residual of the last split result
 
   rd_split_plan* split = nullptr;
 
@@ -110,6 +119,10 @@ struct rd_gemm_f64_args {
   int d_rows, d_cols;
   double log_gamma, tau;
   int* status;
+  // C overwrites A's row strip or B's column strip of the same product (beta must be 0): every
+  // CTA must then own the whole strip it reads, so the 64 x 64 tile is kept and the aliased
+  // extent (N when C aliases A, M when C aliases B) must be 64
+  int aliased;
 };
 
 // flops: algorithmic flop count of the launch (for the profile), computed by the caller
@@ -134,11 +147,14 @@ cudaError_t rd_greedy(rd_ctx* h, const int32_t* dgoals, int k, const double* yro
                       int32_t* next, cudaStream_t s);
 
 // ---- split path (k_split.cu) -----------------------------------------------------------------
-rd_status rd_split_prepare(rd_ctx* h);
+rd_status rd_split_prepare(rd_ctx* h, int slices);
 void rd_split_release(rd_ctx* h);
 cudaError_t rd_lu_split(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_trtri_split(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s);
+cudaError_t rd_goal_split(rd_ctx* h, const int32_t* dgoals, int k, double* out, cudaStream_t s);
+cudaError_t rd_split_row_check(rd_ctx* h, double* worst, cudaStream_t s);
+#define RD_SPLIT_RESIDUAL 1e-9  // largest accepted entrywise relative residual of the sampled rows
 
 // ---- errors of calls without a handle (read back through rd_last_error(NULL)) -----------------
 void rd_record_error(const std::string& msg);

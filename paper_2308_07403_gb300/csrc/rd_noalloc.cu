@@ -102,12 +102,14 @@ extern "C" rd_status rd_apsp_noalloc(const uint8_t* A, int32_t n, double gamma, 
   h.dT = base + NN;
   h.dS = base + 2 * NN;
   int* words = reinterpret_cast<int*>(base + 2 * kMatDoubles + kMatDoubles / 2);
-  h.dStatus = words;                                                     // 2 ints
+  h.dStatus = words;                                                     // 4 ints
   h.dRed = reinterpret_cast<unsigned long long*>(words + 8);             // 3 words
   h.dDeg = words + 16;                                                   // 2n + 2 ints
-  static_assert(16 + 2 * kMaxN + 2 <= kIntWords, "integer words do not fit");
+  h.dColsum = reinterpret_cast<double*>(words + 1280);                   // n doubles
+  static_assert(16 + 2 * kMaxN + 2 <= 1280, "integer words do not fit");
+  static_assert(1280 + 2 * kMaxN <= kIntWords, "column sums do not fit");
 
-  NA_CK(cudaMemsetAsync(h.dStatus, 0, 2 * sizeof(int), h.stream));
+  NA_CK(cudaMemsetAsync(h.dStatus, 0, 4 * sizeof(int), h.stream));
   NA_CK(rd_build_m(&h, h.stream));
   unsigned long long red[3];
   NA_CK(cudaMemcpyAsync(red, h.dRed, sizeof(red), cudaMemcpyDeviceToHost, h.stream));

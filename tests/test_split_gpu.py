@@ -56,8 +56,8 @@ def rel_err(Yg, Yo):
 
 
 # (name, graph and gain, digit count): the directed path puts a 2^-68 range of Y inside one
-# 128-node chunk, which 12 digits of 7 bits cannot resolve to 1e-10; 16 digits do.
-SLICES = {"dpath40": 16}
+# 256-node chunk, which 12 digits of 7 bits cannot resolve to 1e-10; 15 digits do.
+SLICES = {"dpath40": 15}
 CASES = [
     ("er128", lambda: (graphs.er(128, 0.06, 1), None)),
     ("dpath40", lambda: (graphs.directed_path(40), 0.3)),
@@ -115,25 +115,40 @@ def test_split_goal_rows_and_greedy(rd):
 def test_split_rejects_bad_slice_counts(rd):
     A, g = graphs.workload_small()
     with rd.Handle(A, g) as h:
-        with pytest.raises(rd.RDError):
-            h.set_precision(rd.RD_PREC_SPLIT_BF16, 17)
-        h.set_precision(rd.RD_PREC_SPLIT_BF16, 1)
+        for bad in (16, 1, -1):
+            with pytest.raises(rd.RDError) as ei:
+                h.set_precision(rd.RD_PREC_SPLIT_BF16, bad)
+            assert ei.value.status == rd.RD_ERR_ARG
         D = np.empty((512, 512), np.int32)
-        with pytest.raises(rd.RDError) as ei:
-            h.apsp(D)
-        assert ei.value.status == rd.RD_ERR_ARG
+        h.apsp(D)  # the handle is unharmed
+        assert np.array_equal(D, oracle.rdistance(A, g))
+
+
+def test_self_check_falls_back_to_fp64(rd):
+    """A directed path at a small gain spans 2^-600 within one 256-chunk: the far entries of Y
+    are lost to the digit truncation, the residual of the sampled rows against M exposes it at
+    12 and at 15 digits, and the library recomputes the graph in FP64 -- D stays exact."""
+    A, g = graphs.directed_path(200), 0.125
+    Do = oracle.rdistance(A, g)
+    Dg, _, st = run(rd, A, g, want_y=False)
+    assert st["precision_used"] == rd.RD_PREC_FP64 and st["fallbacks"] >= 1
+    assert np.array_equal(Dg, Do)
 
 
 @pytest.mark.parametrize("kind,frac", [(k, f) for k in graphs.LARGE_KINDS for f in graphs.LARGE_FRACS])
 def test_split_full_size_D_identical(rd, kind, frac):
-    """n = 8192: the split path's D hashes to the oracle's D."""
+    """n = 8192: the D of the split mode hashes to the oracle's D.  ER and WS stay on the split
+    path; the 90 x 91 grid (Y down to 2^-540) may be redone in FP64 by the self-check."""
     p = os.path.join(HERE, "golden", f"large_{kind}_{frac}.json")
     if not os.path.exists(p):
         pytest.skip("golden file missing")
     with open(p) as f:
         rec = json.load(f)
     A, g = graphs.workload_large(kind, frac)
-    Dg, _, _ = run(rd, A, g, want_y=False)
+    Dg, _, st = run(rd, A, g, want_y=False)
+    if kind != "grid":
+        assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16, st
+        assert st["split_residual"] < 1e-9
     digest = hashlib.sha256(np.ascontiguousarray(Dg, dtype="<i4").tobytes()).hexdigest()
     if digest != rec["sha256_D"]:
         B = rec["block_rows"]
