@@ -300,7 +300,10 @@ def main():
     value = replica_throughput(world, flop_step, args.steps, total_ms)
     launches = st1["launches"] - st0["launches"]
     pk, pk_kind = peaks()
-    prof_ms, prof_fl = st1["prof_ms"], st1["prof_flops"]
+    if args.precision == "fp64":
+        prof_ms, prof_fl, prof_n = st1["prof_ms"], st1["prof_flops"], st1["prof_launches"]
+    else:  # the split GEMM's own launches (a step the screen sends to FP64 runs the FP64 GEMM)
+        prof_ms, prof_fl, prof_n = st1["prof_split_ms"], st1["prof_split_flops"], st1["prof_split_launches"]
     achieved = prof_fl / (prof_ms * 1e-3) / 1e12 if prof_ms > 0 else None
     if args.precision == "fp64":
         # FP64 SIMT GEMM, bound by the FP64 pipe: peak from unit counts and the sampled clock
@@ -317,7 +320,7 @@ def main():
                 "work": "issued BF16 digit products, s(s+1)/2 x 2MNK per split product"}
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                  "frac": (achieved / peak) if achieved else None, "traffic": None,
-                 "launches": st1["prof_launches"], "kernel_ms": prof_ms,
+                 "launches": prof_n, "kernel_ms": prof_ms,
                  "kernel_share_of_step": prof_ms / total_ms if total_ms else None})
     slices_used = st1["slices"]
 
@@ -371,7 +374,7 @@ def main():
         verify = {}
         for name in ([args.precision, other] if compare else [args.precision]):
             rd.rd_set_precision(h, modes[name], args.slices if name == args.precision else 0)
-            ok, checked, fell = 0, 0, 0
+            ok, checked, fell, screened, bits = 0, 0, 0, 0, {}
             for i, (kind, frac, _, g) in enumerate(wl):
                 path = os.path.join(GOLDEN, f"large_{kind}_{frac}.json")
                 if not os.path.exists(path):
@@ -379,15 +382,23 @@ def main():
                 with open(path) as f:
                     gold = json.load(f)
                 rd.rd_load(h, A_dev[i // 2], None, g)
+                f0 = rd.rd_get_stats(h)["fallbacks"]
                 rd.rd_apsp(h, D)
                 torch.cuda.synchronize()
-                fell += int(name == "split" and rd.rd_get_stats(h)["precision_used"] != rd.RD_PREC_SPLIT_BF16)
+                sg = rd.rd_get_stats(h)
+                if name == "split":
+                    redone = sg["fallbacks"] > f0
+                    bits[f"{kind}_{frac}"] = round(sg["split_screen_bits"], 1)
+                    fell += int(sg["precision_used"] != rd.RD_PREC_SPLIT_BF16 and redone)
+                    screened += int(sg["precision_used"] != rd.RD_PREC_SPLIT_BF16 and not redone)
                 dh = hashlib.sha256(D.cpu().numpy().astype("<i4").tobytes()).hexdigest()
                 checked += 1
                 ok += int(dh == gold["sha256_D"])
             verify[name] = {"graphs_D_identical_to_oracle": ok, "graphs_checked": checked}
             if name == "split":
+                verify[name]["graphs_fp64_by_range_screen"] = screened
                 verify[name]["graphs_redone_in_fp64_by_self_check"] = fell
+                verify[name]["range_screen_bits"] = bits
     rd.rd_destroy(h)
 
     if rank != 0:

@@ -87,6 +87,56 @@ __global__ void succ_fill_kernel(const uint8_t* __restrict__ A, int n, const int
     if (A[(long long)j * n + v]) idx[w++] = j;
 }
 
+// Hop distances from sampled sources and their spread within chunks of consecutive nodes (the
+// split path's range screen).  One CTA per source: a level-synchronous BFS along the successor
+// lists (dist: n ints per source, -1 = not reached; at most n levels), then, one warp per chunk
+// of `chunk` consecutive nodes, the spread max d - min d over the chunk's reached nodes.  The
+// largest spread over chunks and sources is atomicMax-ed into *out.  Sources: nodes
+// b n / nsrc + n / (2 nsrc), b = blockIdx.x.
+__global__ void __launch_bounds__(1024) chunk_spread_kernel(const int32_t* __restrict__ ptr,
+                                                            const int32_t* __restrict__ succ, int n,
+                                                            int nsrc, int chunk, int32_t* __restrict__ dist,
+                                                            unsigned long long* out) {
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int src = (int)(((long long)b * n) / nsrc + (n / nsrc) / 2);
+  int32_t* d = dist + (long long)b * n;
+  for (int v = t; v < n; v += blockDim.x) d[v] = (v == src) ? 0 : -1;
+  __syncthreads();
+  for (int L = 0; L < n; ++L) {
+    int grew = 0;
+    for (int v = t; v < n; v += blockDim.x) {
+      if (d[v] != L) continue;
+      const int e1 = ptr[v + 1];
+      for (int e = ptr[v]; e < e1; ++e) {
+        const int w = succ[e];
+        if (d[w] < 0) {  // every writer of this level writes the same L + 1
+          d[w] = L + 1;
+          grew = 1;
+        }
+      }
+    }
+    if (!__syncthreads_or(grew)) break;
+  }
+  const int warp = t >> 5, lane = t & 31, nwarps = blockDim.x >> 5;
+  const int nch = (n + chunk - 1) / chunk;
+  for (int c = warp; c < nch; c += nwarps) {
+    int lo = 0x7fffffff, hi = -1;
+    const int v1 = min(n, (c + 1) * chunk);
+    for (int v = c * chunk + lane; v < v1; v += 32) {
+      const int x = d[v];
+      if (x >= 0) {
+        lo = min(lo, x);
+        hi = max(hi, x);
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0 && hi >= 0) atomicMax(out, (unsigned long long)(hi - lo));
+  }
+}
+
 __global__ void copy_rows_kernel(const double* __restrict__ R, long long ldr, int rows, int cols,
                                  double* __restrict__ out, long long ldo) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -106,29 +156,29 @@ cudaError_t rd_build_m(rd_ctx* h, cudaStream_t s) {
   const int row_blocks = 16;
   const int rows_per_block = (h->N + row_blocks - 1) / row_blocks;
   dim3 grid((h->N + threads - 1) / threads, row_blocks);
-  if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
+  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
   build_m_kernel<<<grid, threads, 0, s>>>(h->dA, h->weighted ? h->dW : nullptr, h->n, h->N, rows_per_block,
                                           h->gamma, h->dLU, h->dDeg, h->dColsum);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = rd_prof_end(h, s, false, 0.0)) != cudaSuccess) return e;
-  if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
   build_reduce_kernel<<<(h->n + 255) / 256, 256, 0, s>>>(h->dDeg, h->dColsum, h->n, h->dRed);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, s, false, 0.0);
+  return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }
 
 cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s) {
   // ptr lives after the degrees: dDeg[0..n) degrees, dDeg[n+1 .. 2n+1] prefix
   int32_t* ptr = h->dDeg + (h->n + 1);
-  cudaError_t e = rd_prof_begin(h, s, false);
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   scan_kernel<<<1, 1024, 0, s>>>(h->dDeg, h->n, ptr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = rd_prof_end(h, s, false, 0.0)) != cudaSuccess) return e;
-  if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
   succ_fill_kernel<<<(h->n + 127) / 128, 128, 0, s>>>(h->dA, h->n, ptr, h->dSucc);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, s, false, 0.0);
+  return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }
 
 cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows, int cols,
@@ -136,10 +186,19 @@ cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows
   const long long total = (long long)rows * cols;
   if (total == 0) return cudaSuccess;
   const int threads = 256;
-  cudaError_t e = rd_prof_begin(h, s, false);
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   copy_rows_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(R, ldr, rows, cols,
                                                                                  out, ldo);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, s, false, 0.0);
+  return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
+}
+
+cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, int32_t* dist, unsigned long long* out,
+                            cudaStream_t s) {
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
+  if (e != cudaSuccess) return e;
+  chunk_spread_kernel<<<nsrc, 1024, 0, s>>>(h->dDeg + (h->n + 1), h->dSucc, h->n, nsrc, chunk, dist, out);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }

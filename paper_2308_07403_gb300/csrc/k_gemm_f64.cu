@@ -175,7 +175,7 @@ cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cud
   }
   if (maxtiles == 0) return cudaSuccess;
   dim3 grid(maxtiles, 1, nprob);
-  cudaError_t e = rd_prof_begin(h, s, true);
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_F64);
   if (e != cudaSuccess) return e;
   const rd_gemm_f64_args& q1 = nprob > 1 ? probs[1] : probs[0];
   if (T == 64)
@@ -186,5 +186,5 @@ cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cud
     gemm_f64_kernel<16><<<grid, NT, 0, s>>>(probs[0], q1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return rd_prof_end(h, s, true, flops);
+  return rd_prof_end(h, s, RD_PROF_F64, flops);
 }

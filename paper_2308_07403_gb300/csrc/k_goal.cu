@@ -68,11 +68,11 @@ cudaError_t rd_goal_f64(rd_ctx* h, const int32_t* dgoals, int k, double* out, cu
   const double* LU = h->dLU;
   const double* T = h->dT;
   const long long total = RD_MAX_GOALS * N;
-  cudaError_t e = rd_prof_begin(h, s, false);
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   init_rhs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(R, N, dgoals, k);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = rd_prof_end(h, s, false, 0.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   const double fdiag_u = 2.0 * RD_MAX_GOALS * (B * (B + 1) / 2);
   const double fdiag_l = 2.0 * RD_MAX_GOALS * (B * (B - 1) / 2);
   const int nb = (int)(N / B);
@@ -117,10 +117,10 @@ cudaError_t rd_greedy(rd_ctx* h, const int32_t* dgoals, int k, const double* yro
   const long long total = (long long)k * h->n;
   if (total == 0) return cudaSuccess;
   const int32_t* ptr = h->dDeg + (h->n + 1);
-  cudaError_t e = rd_prof_begin(h, s, false);
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   greedy_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ptr, h->dSucc, h->n, dgoals, k, yrows,
                                                                 next);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, s, false, 0.0);
+  return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }

@@ -20,126 +20,126 @@ namespace {
 
 constexpr int B = RD_BF;
 
-// LU of the B x B diagonal block at (k0, k0) of LU (in place), then the inverses of its unit
-// lower factor and of its upper factor, written to the same block of T (strict lower = L^-1,
-// upper = U^-1).  One CTA of 256 threads; thread t keeps the 4 x 4 tile at rows 4 (t / 16),
-// columns 4 (t % 16) of every matrix in registers.  Each elimination step publishes the pivot
-// row and column through shared memory (double-buffered, so one barrier per step) and one
-// thread forms the reciprocal of the pivot.  The two triangular inverses run in the same
-// 64-step loop: L^-1 by forward elimination (step q), U^-1 by back substitution (step 63 - q).
-__global__ void __launch_bounds__(256) lu_diag_kernel(double* __restrict__ LU, double* __restrict__ T,
-                                                      long long ld, int k0, int* status) {
-  __shared__ double rowb[2][B], colb[2][B], recip[2];
-  __shared__ double xrow[2][B], lcol[2][B], zrow[2][B], ucol[2][B], zrecip[2];
-  const int t = threadIdx.x;
-  const int r0 = 4 * (t / 16), c0 = 4 * (t % 16);
-  double a[4][4];
+// LU of the B x B diagonal block at (k0, k0) of LU, in place (strict lower = the multipliers of
+// L, upper = U), by rank-1 elimination without pivoting.  One CTA of 256 threads.
+//
+// The FP64 pipe of one SM retires about two FMAs per clock, so the block is bound by the number
+// of warp-level FP64 instructions issued, live lanes or not.  Thread t owns the 16 elements
+// (r + 16 a, c + 16 b), r = t / 16, c = t % 16, a, b in 0..3: a cyclic distribution, so the
+// shrinking active window of the elimination stays spread over every thread.  The 64 steps run
+// as four chunks of 16 (template KB = k / 16), which makes the slot indices compile-time; slots
+// left of or above the window are never touched, and a slot row whose two warp rows (2w, 2w+1)
+// are both done is skipped by the whole warp.  The pivot row and column are published through
+// shared memory (double-buffered: one barrier per step), with the reciprocal of the pivot.
+struct LeafLuShared {
+  double row[2][B];
+  double col[2][B];
+  double rcp[2];
+};
+
+template <int KB>
+__device__ __forceinline__ void leaf_lu_chunk(double (&a)[4][4], LeafLuShared& sm, int r, int c,
+                                              int w, int k0, int* status) {
+#pragma unroll 1
+  for (int kk = 0; kk < 16; ++kk) {
+    const int bf = kk & 1;
+    if (r == kk) {
+#pragma unroll
+      for (int b = KB; b < 4; ++b) sm.row[bf][c + 16 * b] = a[KB][b];
+      if (c == kk) {
+        const double p = a[KB][KB];
+        const bool ok = (p > 0.0) && isfinite(p);
+        if (!ok) rd_set_status(status, RD_DEV_PIVOT, k0 + 16 * KB + kk);
+        sm.rcp[bf] = ok ? 1.0 / p : 0.0;
+      }
+    }
+    if (c == kk) {
+#pragma unroll
+      for (int i = KB; i < 4; ++i) sm.col[bf][r + 16 * i] = a[i][KB];
+    }
+    __syncthreads();
+    const double rp = sm.rcp[bf];
+    double u[4];
+#pragma unroll
+    for (int b = KB; b < 4; ++b) u[b] = sm.row[bf][c + 16 * b];
+#pragma unroll
+    for (int i = KB; i < 4; ++i) {
+      if (i == KB && 2 * w + 1 <= kk) continue;  // no row of this warp below the pivot
+      const bool live_r = (i > KB) || (r > kk);
+      const double l = sm.col[bf][r + 16 * i] * rp;
+#pragma unroll
+      for (int b = KB; b < 4; ++b) {
+        if (b == KB && kk == 15) continue;       // no column right of the pivot in this slot
+        if (live_r && ((b > KB) || (c > kk))) a[i][b] = fma(-l, u[b], a[i][b]);
+      }
+      if (live_r && c == kk) a[i][KB] = l;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) leaf_lu_kernel(double* __restrict__ LU, long long ld, int k0,
+                                                      int* status) {
+  static_assert(B == 64, "the leaf kernels are laid out for 64 x 64 blocks");
+  __shared__ LeafLuShared sm;
+  const int t = threadIdx.x, r = t >> 4, c = t & 15, w = t >> 5;
   double* blk = LU + (long long)k0 * ld + k0;
+  double a[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) a[i][j] = blk[(long long)(r0 + i) * ld + c0 + j];
+    for (int b = 0; b < 4; ++b) a[i][b] = blk[(long long)(r + 16 * i) * ld + c + 16 * b];
+  leaf_lu_chunk<0>(a, sm, r, c, w, k0, status);
+  leaf_lu_chunk<1>(a, sm, r, c, w, k0, status);
+  leaf_lu_chunk<2>(a, sm, r, c, w, k0, status);
+  leaf_lu_chunk<3>(a, sm, r, c, w, k0, status);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) blk[(long long)(r + 16 * i) * ld + c + 16 * b] = a[i][b];
+}
 
-  // ---- LU without pivoting
-  for (int k = 0; k < B; ++k) {
-    const int bf = k & 1;
-#pragma unroll
-    for (int ii = 0; ii < 4; ++ii) {
-      if (r0 + ii != k) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        rowb[bf][c0 + j] = a[ii][j];
-        if (c0 + j == k) {
-          const double p = a[ii][j];
-          const bool ok = (p > 0.0) && isfinite(p);
-          if (!ok) rd_set_status(status, RD_DEV_PIVOT, k0 + k);
-          recip[bf] = ok ? 1.0 / p : 0.0;
-        }
-      }
-    }
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      if (c0 + jj != k) continue;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) colb[bf][r0 + i] = a[i][jj];
-    }
-    __syncthreads();
-    const double ip = recip[bf];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int gi = r0 + i;
-      if (gi <= k) continue;
-      const double l = colb[bf][gi] * ip;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int gj = c0 + j;
-        if (gj > k) a[i][j] = fma(-l, rowb[bf][gj], a[i][j]);
-        else if (gj == k) a[i][j] = l;
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) blk[(long long)(r0 + i) * ld + c0 + j] = a[i][j];
-
-  // ---- L^-1 (x) and U^-1 (z), both starting from the identity
-  double x[4][4], z[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) x[i][j] = z[i][j] = (r0 + i == c0 + j) ? 1.0 : 0.0;
-  for (int st = 0; st < B; ++st) {
-    const int bf = st & 1;
-    const int q1 = st, q2 = B - 1 - st;
-#pragma unroll
-    for (int ii = 0; ii < 4; ++ii) {
-      if (r0 + ii == q1) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) xrow[bf][c0 + j] = x[ii][j];
-      }
-      if (r0 + ii == q2) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          zrow[bf][c0 + j] = z[ii][j];
-          if (c0 + j == q2) zrecip[bf] = 1.0 / a[ii][j];
-        }
-      }
-    }
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      if (c0 + jj == q1) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) lcol[bf][r0 + i] = a[i][jj];
-      }
-      if (c0 + jj == q2) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) ucol[bf][r0 + i] = a[i][jj];
-      }
-    }
-    __syncthreads();
-    const double dq = zrecip[bf];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int gi = r0 + i;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int gj = c0 + j;
-        if (gi > q1 && gj <= q1) x[i][j] = fma(-lcol[bf][gi], xrow[bf][gj], x[i][j]);
-        if (gj >= q2) {
-          if (gi < q2)
-            z[i][j] = fma(-ucol[bf][gi], zrow[bf][gj] * dq, z[i][j]);
-          else if (gi == q2)
-            z[i][j] *= dq;
-        }
-      }
-    }
-  }
+// Inverses of the two triangular factors of the factored diagonal block at (k0, k0), written to
+// the same block of T (strict lower = L^-1, upper = U^-1).  The 2 B columns are independent
+// problems: column j of L^-1 solves L x = e_j by forward substitution, column j of U^-1 solves
+// U z = e_j by back substitution.  One warp per column, lanes owning rows l and l + 32; each
+// step's pivot entry reaches the warp by shuffle and the factor is read from shared memory
+// (padded rows: column reads are conflict-free).  32 CTAs of 4 warps: CTAs 0..15 take the
+// columns of L^-1, 16..31 those of U^-1, so the FP64 work is spread over 32 SMs.
+__global__ void __launch_bounds__(128) leaf_inv_kernel(const double* __restrict__ LU,
+                                                       double* __restrict__ T, long long ld, int k0) {
+  __shared__ double f[B][B + 1];
+  __shared__ double rcp[B];
+  const int t = threadIdx.x, lane = t & 31;
+  const double* blk = LU + (long long)k0 * ld + k0;
+  for (int e = t; e < B * B; e += blockDim.x) f[e / B][e % B] = blk[(long long)(e / B) * ld + e % B];
+  const bool lower = blockIdx.x < 16;
+  __syncthreads();
+  if (!lower && t < B) rcp[t] = 1.0 / f[t][t];
+  __syncthreads();
+  const int j = 4 * (blockIdx.x & 15) + (t >> 5);
+  double x0 = (lane == j) ? 1.0 : 0.0, x1 = (lane + 32 == j) ? 1.0 : 0.0;
   double* tb = T + (long long)k0 * ld + k0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) tb[(long long)(r0 + i) * ld + c0 + j] = (r0 + i > c0 + j) ? x[i][j] : z[i][j];
+  if (lower) {
+    // x_i -= L_iq x_q for i > q, q = j .. B-2 (x_q is final once step q starts)
+    for (int q = j; q < B - 1; ++q) {
+      const double xq = __shfl_sync(0xffffffffu, q < 32 ? x0 : x1, q & 31);
+      if (q < 31 && lane > q) x0 = fma(-f[lane][q], xq, x0);
+      if (lane + 32 > q) x1 = fma(-f[lane + 32][q], xq, x1);
+    }
+    if (lane > j) tb[(long long)lane * ld + j] = x0;
+    if (lane + 32 > j) tb[(long long)(lane + 32) * ld + j] = x1;
+  } else {
+    // z_q = z_q / U_qq, then z_i -= U_iq z_q for i < q, q = j .. 0
+    for (int q = j; q >= 0; --q) {
+      const double zq = __shfl_sync(0xffffffffu, q < 32 ? x0 : x1, q & 31) * rcp[q];
+      if (lane == q) x0 = zq;
+      if (lane + 32 == q) x1 = zq;
+      if (lane < q) x0 = fma(-f[lane][q], zq, x0);
+      if (q > 32 && lane + 32 < q) x1 = fma(-f[lane + 32][q], zq, x1);
+    }
+    if (lane <= j) tb[(long long)lane * ld + j] = x0;
+    if (lane + 32 <= j) tb[(long long)(lane + 32) * ld + j] = x1;
+  }
 }
 
 rd_gemm_f64_args blank() {
@@ -154,10 +154,14 @@ rd_gemm_f64_args blank() {
 
 cudaError_t rd_lu_diag(rd_ctx* h, int k0, cudaStream_t s) {
   cudaError_t e;
-  if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
-  lu_diag_kernel<<<1, 256, 0, s>>>(h->dLU, h->dT, h->N, k0, h->dStatus);
+  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
+  leaf_lu_kernel<<<1, 256, 0, s>>>(h->dLU, h->N, k0, h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, s, false, 0.0);
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
+  leaf_inv_kernel<<<32, 128, 0, s>>>(h->dLU, h->dT, h->N, k0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }
 
 // Right-looking blocked LU: for each diagonal block k, factor it (and invert its factors),

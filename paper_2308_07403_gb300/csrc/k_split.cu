@@ -57,6 +57,7 @@ constexpr int EXP_ZERO = -16384;                   // exponent of an all-zero ch
 constexpr int MAX_SLICES = 15;                     // group sums exact: 256 * 15 * 2^12 < 2^24
 constexpr int LEAF = RD_BF;                        // FP64 diagonal leaves (64)
 constexpr unsigned long long WAIT_NS = 4000000000ull;
+static_assert(SIGMA == RD_SPLIT_DIGIT_BITS && KAPPA == RD_SCREEN_CHUNK, "range screen out of step with the digits");
 
 constexpr uint32_t IDESC = (1u << 4)               // D: FP32
                            | (1u << 7)             // A: BF16
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // Entrywise relative residual of sampled rows y of Y against the exact M: y^T M = e_g^T, i.e.
 //   r_j = y_j - [j == g] - sum_{i : edge j -> i} X_ij y_i,   X = gamma A or gamma^W,
-// relative to |y_j - [j == g]| + sum |X_ij y_i|.  Every product is FP64 here.  Because M is an
+// relative to (|y^T| |M|)_j = |y_j| + sum |X_ij y_i| (the componentwise backward error).  Every product is FP64 here.  Because M is an
 // M-matrix with Y >= 0, a small entrywise residual bounds the entrywise error of the row
 // (error^T = r^T Y), and a wrong region of a row shows up where it meets the right part.
 // The largest relative residual is OR-ed into res (bits of a non-negative double).
@@ -570,7 +571,7 @@ __global__ void row_residual_kernel(const double* __restrict__ rows, const int32
     const int c = (int)(t / n), j = (int)(t % n);
     const double* y = rows + (long long)c * n;
     double acc = y[j] - (goals[c] == j ? 1.0 : 0.0);
-    double scale = fabs(acc);
+    double scale = fabs(y[j]);  // componentwise: (|y^T| |M|)_j
     for (int q = ptr[j]; q < ptr[j + 1]; ++q) {
       const int i = succ[q];
       const double x = W ? pow(gamma, (double)W[(long long)i * n + j]) : gamma;
@@ -640,25 +641,25 @@ namespace {
 // Slice the A operand (rows x k) into digA/eA/RA.
 cudaError_t slice_a(rd_ctx* h, const View& v, int rows_pad, int k_pad, cudaStream_t st) {
   rd_split_plan* P = h->split;
-  cudaError_t e = rd_prof_begin(h, st, false);
+  cudaError_t e = rd_prof_begin(h, st, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   const long long warps = (long long)rows_pad * (k_pad / KAPPA);
   const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
   slice_rows_kernel<<<blocks, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, rows_pad, k_pad, P->s, P->digA, P->eA,
                                             h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, st, false, 0.0);
+  return rd_prof_end(h, st, RD_PROF_NONE, 0.0);
 }
 
 // Slice the B operand (k x cols, row-major) into digB/eB/RB (K-major per column).
 cudaError_t slice_b(rd_ctx* h, const View& v, int cols_pad, int k_pad, cudaStream_t st) {
   rd_split_plan* P = h->split;
-  cudaError_t e = rd_prof_begin(h, st, false);
+  cudaError_t e = rd_prof_begin(h, st, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   slice_cols_kernel<<<dim3(cols_pad / 16, k_pad / KAPPA), 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, cols_pad,
                                                                         k_pad, P->s, P->digB, P->eB, h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, st, false, 0.0);
+  return rd_prof_end(h, st, RD_PROF_NONE, 0.0);
 }
 
 // C (M x N) = alpha * A (M x K) * B (K x N) + beta * C, or the decode of the product into D.
@@ -711,10 +712,10 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
     attr = true;
   }
   const int tiles = (ma_pad / TM) * (nb_pad / TN);
-  if ((e = rd_prof_begin(h, st, true)) != cudaSuccess) return e;
+  if ((e = rd_prof_begin(h, st, RD_PROF_SPLIT)) != cudaSuccess) return e;
   split_gemm_kernel<<<tiles, THREADS, SMEM_BYTES, st>>>(ta, tb, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, st, true, flops * (double)P->s * (P->s + 1) / 2.0);
+  return rd_prof_end(h, st, RD_PROF_SPLIT, flops * (double)P->s * (P->s + 1) / 2.0);
 }
 
 inline View full(const double* p, long long ld, int rows, int cols) { return View{p, ld, rows, cols, RD_TRI_FULL}; }
@@ -906,12 +907,12 @@ cudaError_t rd_split_row_check(rd_ctx* h, double* worst, cudaStream_t s) {
   unsigned long long* res = reinterpret_cast<unsigned long long*>(h->dRed);  // [0] reused after load
   if ((e = cudaMemsetAsync(res, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
   const long long total = (long long)k * h->n;
-  if ((e = rd_prof_begin(h, s, false)) != cudaSuccess) return e;
+  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
   row_residual_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(rows, h->dGoals, k, h->n, h->dDeg + (h->n + 1),
                                                                        h->dSucc, h->dA, h->weighted ? h->dW : nullptr,
                                                                        h->gamma, res);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = rd_prof_end(h, s, false, 0.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   unsigned long long bits = 0;
   if ((e = cudaMemcpyAsync(&bits, res, sizeof(bits), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
@@ -923,12 +924,12 @@ cudaError_t rd_split_row_check(rd_ctx* h, double* worst, cudaStream_t s) {
 // (64 x N times the lower-unit view of T), written straight into out (k x n).
 cudaError_t rd_goal_split(rd_ctx* h, const int32_t* dgoals, int k, double* out, cudaStream_t s) {
   const long long N = h->N;
-  cudaError_t e = rd_prof_begin(h, s, false);
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   const long long total = RD_MAX_GOALS * N;
   gather_uinv_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->dT, N, dgoals, k, h->dR);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = rd_prof_end(h, s, false, 0.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   const double Nd = (double)N;
   return split_gemm(h, full(h->dR, N, RD_MAX_GOALS, (int)N), tri(h->dT, N, (int)N, RD_TRI_LOWER_UNIT), RD_MAX_GOALS,
                     (int)N, (int)N, 1.0, 0.0, out, h->n, k, h->n, nullptr, nullptr, RD_MAX_GOALS * Nd * (Nd + 1),

@@ -120,6 +120,8 @@ rd_status load_impl(rd_ctx* h, const uint8_t* A, const float* W, double gamma) {
   h->gamma = gamma;
   h->factored = h->inverted = 0;
   h->split_floor = 0;
+  h->screened = 0;
+  h->screen_bits = -1.0;
   h->succ_ready = 0;
   RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 4 * sizeof(int), h->stream));
   RD_CK(h, rd_build_m(h, h->stream));
@@ -219,11 +221,14 @@ rd_status read_split_flags(rd_ctx* h, int* flags) {
   return RD_OK;
 }
 
-// Split mode with the self-check (RD_FLAG_RANGE from the product epilogue, and the residual of
-// 64 sampled rows of Y against M after the inverse product): when the caller leaves the digit
-// count open, the library starts from RD_SPLIT_START digits; a failed residual raises the floor
-// of the current graph to RD_SPLIT_MAX digits, and a range flag, or a failure at RD_SPLIT_MAX,
-// moves the graph to FP64.  The inverse is then recomputed from M.
+// Split mode with the self-check: after the inverse product, 64 sampled rows of Y (computed with
+// the same digit products) must satisfy y^T M = e_g^T to RD_SPLIT_RESIDUAL per entry.  When the
+// caller leaves the digit count open, the library starts from RD_SPLIT_START digits; a failed
+// check raises the floor of the current graph to RD_SPLIT_MAX digits, or moves it to FP64 when
+// the products also reported terms lost below their FP32 accumulators' range (RD_FLAG_RANGE:
+// more digits cannot recover those) or when RD_SPLIT_MAX digits already failed.  The inverse is
+// then recomputed from M.  RD_FLAG_RANGE alone is not a failure: the LU's Schur updates lose
+// fill-in terms far below the entries they update without harming Y.
 bool split_auto(const rd_ctx* h) { return h->precision == RD_PREC_SPLIT_BF16 && h->slices_req == 0; }
 
 // range: a term left the FP32 accumulators' range -- more digits cannot help, go to FP64;
@@ -237,8 +242,43 @@ rd_status escalate(rd_ctx* h, bool range) {
   return RD_OK;
 }
 
+// Range screen of the split path, run once per graph when the caller leaves the digit count open
+// (unweighted graphs).  The digits of a KAPPA-wide chunk of an operand row are scaled to the
+// chunk's largest entry, and the entries of Y fall by log2(1/gamma) bits per hop (Y_ij ~ gamma^d
+// for distance d), so a chunk whose nodes lie S hops apart as seen from one node costs about
+// S log2(1/gamma) of the 7 s bits the digits carry.  The largest S over the chunks, seen from 8
+// sampled sources, picks where the attempt starts: RD_SPLIT_START digits when they cover the
+// spread plus RD_SCREEN_RESULT_BITS bits of result, RD_SPLIT_MAX digits when those do, FP64
+// otherwise.  It only steers: the residual self-check still judges every split result.
+rd_status screen_split(rd_ctx* h) {
+  h->screened = 1;
+  h->screen_bits = -1.0;
+  if (h->weighted || !h->dSucc) return RD_OK;
+  if (!h->succ_ready) {
+    RD_CK(h, rd_build_succ(h, h->stream));
+    h->succ_ready = 1;
+  }
+  RD_CK(h, cudaMemsetAsync(h->dRed, 0, sizeof(unsigned long long), h->stream));
+  RD_CK(h, rd_chunk_spread(h, RD_SCREEN_SOURCES, RD_SCREEN_CHUNK, reinterpret_cast<int32_t*>(h->dS), h->dRed,
+                           h->stream));
+  unsigned long long spread = 0;
+  RD_CK(h, cudaMemcpyAsync(&spread, h->dRed, sizeof(spread), cudaMemcpyDeviceToHost, h->stream));
+  RD_CK(h, cudaStreamSynchronize(h->stream));
+  const double bits = (double)spread * std::log2(1.0 / h->gamma);
+  h->screen_bits = bits;
+  if (bits + RD_SCREEN_RESULT_BITS > (double)RD_SPLIT_DIGIT_BITS * RD_SPLIT_MAX)
+    h->split_floor = -1;
+  else if (bits + RD_SCREEN_RESULT_BITS > (double)RD_SPLIT_DIGIT_BITS * RD_SPLIT_START)
+    h->split_floor = RD_SPLIT_MAX;
+  return RD_OK;
+}
+
 rd_status ensure_factored(rd_ctx* h) {
   if (h->factored) return RD_OK;
+  if (split_auto(h) && !h->screened && h->split_floor == 0) {
+    rd_status st = screen_split(h);
+    if (st != RD_OK) return st;
+  }
   RD_CK(h, cudaEventRecord(h->ev[0], h->stream));
   for (;;) {
     const bool split = h->precision == RD_PREC_SPLIT_BF16 && h->split_floor >= 0;
@@ -257,11 +297,7 @@ rd_status ensure_factored(rd_ctx* h) {
     h->used_precision = RD_PREC_SPLIT_BF16;
     h->factored = 1;
     h->inverted = 1;
-    if (!split_auto(h)) break;
-    int flags = 0;
-    if ((st = read_split_flags(h, &flags)) != RD_OK) return st;
-    if (!flags) break;
-    if ((st = escalate(h, true)) != RD_OK) return st;
+    break;  // the self-check runs on the result (rd_apsp)
   }
   RD_CK(h, cudaEventRecord(h->ev[1], h->stream));
   h->ev_used[0] = 1;
@@ -293,9 +329,9 @@ double event_ms(rd_ctx* h, int slot) {
 
 void rd_record_error(const std::string& msg) { g_create_err = msg; }
 
-cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, bool contraction) {
+cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, int kind) {
   h->launches++;
-  if (!h->prof_on || !contraction) return cudaSuccess;
+  if (!h->prof_on || kind == RD_PROF_NONE) return cudaSuccess;
   if (h->prof_used == rd_ctx::kProfPairs) {
     cudaError_t e = rd_prof_collect(h);
     if (e != cudaSuccess) return e;
@@ -303,12 +339,13 @@ cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, bool contraction) {
   return cudaEventRecord(h->prof_ev[2 * h->prof_used], s);
 }
 
-cudaError_t rd_prof_end(rd_ctx* h, cudaStream_t s, bool contraction, double flops) {
-  if (!h->prof_on || !contraction) return cudaSuccess;
+cudaError_t rd_prof_end(rd_ctx* h, cudaStream_t s, int kind, double flops) {
+  if (!h->prof_on || kind == RD_PROF_NONE) return cudaSuccess;
   cudaError_t e = cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
   if (e != cudaSuccess) return e;
+  h->prof_kind[h->prof_used] = (int8_t)kind;
+  h->prof_pair_flops[h->prof_used] = flops;
   h->prof_used++;
-  h->prof_pending_flops += flops;
   return cudaSuccess;
 }
 
@@ -316,17 +353,19 @@ cudaError_t rd_prof_collect(rd_ctx* h) {
   if (!h->prof_ev || h->prof_used == 0) return cudaSuccess;
   cudaError_t e = cudaEventSynchronize(h->prof_ev[2 * h->prof_used - 1]);
   if (e != cudaSuccess) return e;
-  double sum = 0.0;
   for (int i = 0; i < h->prof_used; ++i) {
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]);
     if (e != cudaSuccess) return e;
-    sum += ms;
+    h->prof_ms += ms;
+    h->prof_flops += h->prof_pair_flops[i];
+    h->prof_launches++;
+    if (h->prof_kind[i] == RD_PROF_SPLIT) {
+      h->prof_split_ms += ms;
+      h->prof_split_flops += h->prof_pair_flops[i];
+      h->prof_split_launches++;
+    }
   }
-  h->prof_ms += sum;
-  h->prof_flops += h->prof_pending_flops;
-  h->prof_launches += h->prof_used;
-  h->prof_pending_flops = 0.0;
   h->prof_used = 0;
   return cudaSuccess;
 }
@@ -343,8 +382,10 @@ rd_status rd_set_profiling(rd_handle h, int32_t on) {
   RD_CK(h, cudaStreamSynchronize(h->stream));
   h->prof_on = on ? 1 : 0;
   h->prof_used = 0;
-  h->prof_ms = h->prof_flops = h->prof_pending_flops = 0.0;
+  h->prof_ms = h->prof_flops = 0.0;
   h->prof_launches = 0;
+  h->prof_split_ms = h->prof_split_flops = 0.0;
+  h->prof_split_launches = 0;
   return RD_OK;
 }
 
@@ -377,6 +418,8 @@ rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices) {
   if (slices < 0 || slices > 15 || slices == 1) return fail(h, RD_ERR_ARG, "slices must be 0 or lie in [2, 15]");
   if (mode != h->precision || slices != h->slices_req) {
     h->split_floor = 0;
+    h->screened = 0;
+    h->screen_bits = -1.0;
     if (h->factored) {
       // the factors in dLU belong to the old mode: rebuild M from the resident graph
       RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 2 * sizeof(int), h->stream));
@@ -416,15 +459,16 @@ rd_status rd_apsp(rd_handle h, int32_t* D, double* Y) {
     if (h->used_precision == RD_PREC_SPLIT_BF16) {
       RD_CK(h, rd_trmm_decode_split(h, dD, dY, h->stream));
       if (!split_auto(h)) break;
+      double worst = 0.0;  // residual of sampled rows of Y against M
+      RD_CK(h, rd_split_row_check(h, &worst, h->stream));
+      h->last_residual = worst;
       int flags = 0;
       if ((st = read_split_flags(h, &flags)) != RD_OK) return st;
-      if (!flags) {
-        double worst = 0.0;  // residual of sampled rows of Y against M
-        RD_CK(h, rd_split_row_check(h, &worst, h->stream));
-        h->last_residual = worst;
-        if (worst <= RD_SPLIT_RESIDUAL) break;
-      }
-      if ((st = escalate(h, flags != 0)) != RD_OK) return st;
+      h->last_flags = flags;
+      if (worst <= RD_SPLIT_RESIDUAL) break;
+      // the result failed: with terms lost below the accumulators' range, or a residual far
+      // beyond what three more digits (21 bits) could close, go straight to FP64
+      if ((st = escalate(h, (flags & RD_FLAG_RANGE) != 0 || worst > 1e-3)) != RD_OK) return st;
       if ((st = ensure_factored(h)) != RD_OK) return st;
       continue;
     }
@@ -514,6 +558,8 @@ rd_status rd_get_stats(rd_handle h, rd_stats* s) {
   s->precision_used = h->used_precision;
   s->fallbacks = h->fallbacks;
   s->split_residual = h->last_residual;
+  s->split_flags = h->last_flags;
+  s->split_screen_bits = h->screen_bits;
   s->gamma = h->gamma;
   s->max_column_sum = h->max_colsum;
   s->tau = h->tau;
@@ -528,6 +574,9 @@ rd_status rd_get_stats(rd_handle h, rd_stats* s) {
   s->prof_launches = h->prof_launches;
   s->prof_ms = h->prof_ms;
   s->prof_flops = h->prof_flops;
+  s->prof_split_launches = h->prof_split_launches;
+  s->prof_split_ms = h->prof_split_ms;
+  s->prof_split_flops = h->prof_split_flops;
   return st;
 }
 

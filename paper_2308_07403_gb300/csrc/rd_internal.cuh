@@ -31,6 +31,10 @@
 #define RD_FLAG_RANGE 1     // a digit-product term fell out of the FP32 accumulator range
 #define RD_SPLIT_START 12   // digit count the split mode starts from when the caller leaves it open
 #define RD_SPLIT_MAX 15     // largest digit count (exact group sums)
+#define RD_SPLIT_DIGIT_BITS 7  // bits per digit of the split operands
+#define RD_SCREEN_SOURCES 8  // BFS sources of the split path's range screen
+#define RD_SCREEN_CHUNK 256  // operand chunk along K that shares one scale (the split path's KAPPA)
+#define RD_SCREEN_RESULT_BITS 34  // bits the digits must keep below a chunk's spread (2^-34 ~ 6e-11)
 
 struct rd_split_plan;       // defined by the split path
 
@@ -66,8 +70,11 @@ struct rd_ctx {
   int inverted = 0;            // dT holds the triangular inverses
   int used_precision = RD_PREC_FP64;  // precision that produced the current factors
   int split_floor = 0;         // per graph: least digit count to use, -1 = FP64 (self-check history)
+  int screened = 0;            // the range screen ran for the current graph and mode
+  double screen_bits = -1.0;   // its estimate of the bits a chunk's spread costs (-1: not screened)
   int fallbacks = 0;           // split results redone (more digits or FP64) after the self-check
   double last_residual = 0.0;  // largest sampled-row residual of the last split result
+  int last_flags = 0;          // precision flags raised while computing it
 
   rd_split_plan* split = nullptr;
 
@@ -85,14 +92,19 @@ struct rd_ctx {
   static constexpr int kProfPairs = 4096;
   cudaEvent_t* prof_ev = nullptr;  // 2 * kProfPairs
   int prof_used = 0;
-  double prof_ms = 0.0, prof_flops = 0.0, prof_pending_flops = 0.0;
+  double prof_ms = 0.0, prof_flops = 0.0;
   int64_t prof_launches = 0;
+  double prof_split_ms = 0.0, prof_split_flops = 0.0;  // the split GEMM's share of the above
+  int64_t prof_split_launches = 0;
+  int8_t prof_kind[kProfPairs] = {};           // RD_PROF_* of each pending event pair
+  double prof_pair_flops[kProfPairs] = {};
 };
 
-// Launch accounting around one kernel launch (see rd_ctx).  `contraction` marks the dense
-// GEMM kernels whose time and algorithmic flops are profiled.
-cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, bool contraction);
-cudaError_t rd_prof_end(rd_ctx* h, cudaStream_t s, bool contraction, double flops);
+// Launch accounting around one kernel launch (see rd_ctx).  `kind` marks the dense GEMM kernels
+// whose time and algorithmic flops are profiled (RD_PROF_NONE for every other kernel).
+enum { RD_PROF_NONE = 0, RD_PROF_F64 = 1, RD_PROF_SPLIT = 2 };
+cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, int kind);
+cudaError_t rd_prof_end(rd_ctx* h, cudaStream_t s, int kind, double flops);
 cudaError_t rd_prof_collect(rd_ctx* h);  // fold finished event pairs into prof_ms
 
 // ---- FP64 GEMM (k_gemm_f64.cu) ----------------------------------------------------------
@@ -132,6 +144,10 @@ cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cud
 // ---- kernels in k_build.cu ----------------------------------------------------------------
 cudaError_t rd_build_m(rd_ctx* h, cudaStream_t s);       // M into dLU, degrees, column sums
 cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s);    // successor CSR from dA
+// largest hop spread within chunks of `chunk` consecutive nodes, BFS from nsrc sampled sources
+// (needs the successor lists; dist: nsrc * n ints of scratch) -> atomicMax into *out
+cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, int32_t* dist, unsigned long long* out,
+                            cudaStream_t s);
 cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows, int cols,
                              double* out, long long ldo, cudaStream_t s);
 

@@ -126,19 +126,76 @@ def test_split_rejects_bad_slice_counts(rd):
 
 def test_self_check_falls_back_to_fp64(rd):
     """A directed path at a small gain spans 2^-600 within one 256-chunk: the far entries of Y
-    are lost to the digit truncation, the residual of the sampled rows against M exposes it at
-    12 and at 15 digits, and the library recomputes the graph in FP64 -- D stays exact."""
+    are lost to the digit truncation.  Given as a weighted graph (unit weights: the same X) it
+    skips the range screen, so the residual of the sampled rows against M must expose the loss;
+    the library then recomputes the graph in FP64 -- D stays exact."""
     A, g = graphs.directed_path(200), 0.125
+    W = A.astype(np.float32)
     Do = oracle.rdistance(A, g)
-    Dg, _, st = run(rd, A, g, want_y=False)
+    n = A.shape[0]
+    D = np.empty((n, n), np.int32)
+    with rd.Handle(A, g, W=W) as h:
+        h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
+        h.apsp(D)
+        st = h.stats()
+    assert st["split_screen_bits"] == -1.0
     assert st["precision_used"] == rd.RD_PREC_FP64 and st["fallbacks"] >= 1
-    assert np.array_equal(Dg, Do)
+    assert st["split_residual"] > 1e-9
+    assert np.array_equal(D, Do)
+
+
+def screen_spread(A):
+    """The range screen's hop spread from the oracle's BFS: sources b n / 8 + n / 16 (b < 8),
+    chunks of 256 consecutive nodes, the largest max - min distance over a chunk's reached
+    nodes."""
+    n = A.shape[0]
+    srcs = np.array([(b * n) // 8 + (n // 8) // 2 for b in range(8)], np.int32)
+    dist, _ = oracle.bfs(A, srcs)
+    worst = 0
+    for row in dist:
+        for c0 in range(0, n, 256):
+            d = row[c0:c0 + 256]
+            d = d[(d >= 0) & (d < np.iinfo(np.int32).max)]
+            if d.size:
+                worst = max(worst, int(d.max()) - int(d.min()))
+    return worst
+
+
+SCREEN_CASES = {  # (graph, gain): the branch follows from spread x log2(1/gamma)
+    "grid1000x40": lambda: (graphs.grid4(1000, 40), None),   # ~95 bits: FP64
+    "grid600x16": lambda: (graphs.grid4(600, 16), None),     # ~65 bits: 15 digits
+    "dpath300_g0.85": lambda: (graphs.directed_path(300), 0.85),  # ~56 bits: 15 digits
+    "dpath300_g0.9": lambda: (graphs.directed_path(300), 0.9),    # ~36 bits: 12 digits
+    "tree700": lambda: (graphs.binary_tree(700), None),      # a few levels per chunk
+    "ws1000": lambda: (graphs.ws(1000, 10, 0.1, 5), None),   # small world: 12 digits
+    "er800": lambda: (graphs.er(800, 0.02, 2), None),        # small world: 12 digits
+}
+
+
+@pytest.mark.parametrize("name", list(SCREEN_CASES))
+def test_range_screen_matches_bfs(rd, name):
+    """The screen's hop spread equals the one computed from the oracle's BFS (integer work: exact),
+    the digit count or FP64 follows from it as documented, and D is exact on every branch."""
+    A, g = SCREEN_CASES[name]()
+    if g is None:
+        g = graphs.gamma_frac(A, 0.9)
+    spread = screen_spread(A)
+    bits = spread * np.log2(1.0 / g)
+    Dg, _, st = run(rd, A, g, want_y=False)
+    assert st["split_screen_bits"] == pytest.approx(bits, rel=1e-12, abs=0.0)
+    if bits + 34 > 7 * 15:
+        assert st["precision_used"] == rd.RD_PREC_FP64 and st["fallbacks"] == 0
+    elif st["fallbacks"] == 0:
+        assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16
+        assert st["slices"] == (15 if bits + 34 > 7 * 12 else 12)
+    assert np.array_equal(Dg, oracle.rdistance(A, g)), name
 
 
 @pytest.mark.parametrize("kind,frac", [(k, f) for k in graphs.LARGE_KINDS for f in graphs.LARGE_FRACS])
 def test_split_full_size_D_identical(rd, kind, frac):
     """n = 8192: the D of the split mode hashes to the oracle's D.  ER and WS stay on the split
-    path; the 90 x 91 grid (Y down to 2^-540) may be redone in FP64 by the self-check."""
+    path; the 90 x 91 grid (a 256-node chunk spans ~47 hops of Y) goes to FP64 at the range screen,
+    without a wasted split attempt."""
     p = os.path.join(HERE, "golden", f"large_{kind}_{frac}.json")
     if not os.path.exists(p):
         pytest.skip("golden file missing")
@@ -148,7 +205,9 @@ def test_split_full_size_D_identical(rd, kind, frac):
     Dg, _, st = run(rd, A, g, want_y=False)
     if kind != "grid":
         assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16, st
-        assert st["split_residual"] < 1e-9
+        assert 0 < st["split_residual"] < 1e-9, st
+    else:
+        assert st["precision_used"] == rd.RD_PREC_FP64 and st["fallbacks"] == 0, st
     digest = hashlib.sha256(np.ascontiguousarray(Dg, dtype="<i4").tobytes()).hexdigest()
     if digest != rec["sha256_D"]:
         B = rec["block_rows"]
