@@ -374,7 +374,7 @@ def main():
         verify = {}
         for name in ([args.precision, other] if compare else [args.precision]):
             rd.rd_set_precision(h, modes[name], args.slices if name == args.precision else 0)
-            ok, checked, fell, screened, bits = 0, 0, 0, 0, {}
+            ok, checked, fell, screened, bits, resid = 0, 0, 0, 0, {}, {}
             for i, (kind, frac, _, g) in enumerate(wl):
                 path = os.path.join(GOLDEN, f"large_{kind}_{frac}.json")
                 if not os.path.exists(path):
@@ -389,6 +389,7 @@ def main():
                 if name == "split":
                     redone = sg["fallbacks"] > f0
                     bits[f"{kind}_{frac}"] = round(sg["split_screen_bits"], 1)
+                    resid[f"{kind}_{frac}"] = (sg["slices"], sg["split_residual"]) if sg["precision_used"] else None
                     fell += int(sg["precision_used"] != rd.RD_PREC_SPLIT_BF16 and redone)
                     screened += int(sg["precision_used"] != rd.RD_PREC_SPLIT_BF16 and not redone)
                 dh = hashlib.sha256(D.cpu().numpy().astype("<i4").tobytes()).hexdigest()
@@ -399,6 +400,7 @@ def main():
                 verify[name]["graphs_fp64_by_range_screen"] = screened
                 verify[name]["graphs_redone_in_fp64_by_self_check"] = fell
                 verify[name]["range_screen_bits"] = bits
+                verify[name]["digits_and_sampled_row_residual"] = resid
     rd.rd_destroy(h)
 
     if rank != 0:

@@ -130,6 +130,27 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// the same load delivered to the CTAs of `mask` in the cluster, at this CTA's smem offsets, each
+// completing its own barrier at the offset of `bar`
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%3, "
+      "%4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -156,6 +177,15 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+// arrive on the barrier at the offset of `bar` in every CTA of `mask` once the prior MMAs complete
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -308,9 +338,20 @@ struct SplitArgs {
   int* status;       // [0] first error, [1] detail, [2] precision flags (RD_FLAG_RANGE)
 };
 
+// CM x CN clusters (launched as 1-D clusters of CM * CN CTAs, rank = ri * CN + rj) own a block of
+// CM x CN output tiles.  The A tile of a tile row is needed by the CN CTAs of that cluster row:
+// each of them loads one 128/CN-row slice and multicasts it to the row; likewise each CTA of a
+// cluster column loads one 128/CM-row slice of the column's B tile.  The L2 reads per CTA fall from
+// two tiles to 1/CN + 1/CM tiles per stage.  A stage of CTA X is written by the CTAs of X's row and
+// column, so X's `empty` barrier counts CM + CN - 1 releases, and every MMA warp releases a stage in
+// all of them (multicast commit).  All CTAs of a cluster walk the union of their K-ranges, which
+// keeps their stage sequences in step (the digits outside a tile's triangle are zero).
+template <int CM, int CN>
 __global__ void __launch_bounds__(THREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const SplitArgs p) {
+  constexpr int CS = CM * CN;
+  constexpr int A_SLICE = TM / CN, B_SLICE = TN / CM;  // rows of the slices this CTA loads
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -327,14 +368,23 @@ __global__ void __launch_bounds__(THREADS, 1)
   int8_t* fl_s = (int8_t*)(smem + FL_OFFSET);                    // [TN][TM], column-major
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int tiles_n = (p.N + TN - 1) / TN;
-  const int m0 = (blockIdx.x / tiles_n) * TM;
-  const int n0 = (blockIdx.x % tiles_n) * TN;
+  const int rank = CS > 1 ? (int)cluster_rank() : 0;
+  const int ri = rank / CN, rj = rank % CN;
+  const int clusters_n = p.nb_pad / (TN * CN);  // the padded extents are multiples of the cluster block
+  const int cm0 = (int)(blockIdx.x / CS / clusters_n) * (TM * CM);
+  const int cn0 = (int)(blockIdx.x / CS % clusters_n) * (TN * CN);
+  const int m0 = cm0 + ri * TM;
+  const int n0 = cn0 + rj * TN;
+  // the cluster's multicast groups: its row (same ri) and its column (same rj)
+  const uint16_t row_mask = (uint16_t)(((1u << CN) - 1u) << (ri * CN));
+  uint16_t col_mask = 0;
+#pragma unroll
+  for (int i = 0; i < CM; ++i) col_mask |= (uint16_t)(1u << (i * CN + rj));
   int kbeg = 0, kend = p.K;
-  if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, m0 + TM);
-  if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, m0);
-  if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, n0);
-  if (p.b_tri == RD_TRI_UPPER) kend = min(kend, n0 + TN);
+  if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, cm0 + CM * TM);
+  if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, cm0);
+  if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, cn0);
+  if (p.b_tri == RD_TRI_UPPER) kend = min(kend, cn0 + CN * TN);
   // chunks are aligned to absolute multiples of KAPPA; the first and last may be partial
   const int cbeg = kbeg / KAPPA;
   const int nchunks = (kbeg < kend) ? (kend + KAPPA - 1) / KAPPA - cbeg : 0;
@@ -343,7 +393,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+      mbar_init(&empty[i], CM + CN - 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
@@ -360,6 +410,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (CS > 1) cluster_sync();  // every CTA's barriers exist before a peer loads or commits into them
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const unsigned long long deadline = globaltimer() + WAIT_NS;
@@ -381,11 +432,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                 ok = false;
                 break;
               }
-              mbar_arrive_expect_tx(&full[st], 2 * TILE_BYTES);
-              tma_load_2d(sA + st * TILE_BYTES, &tmA, &full[st], kc0 + ks * TK, pa * p.ma_pad + m0);
-              tma_load_2d(sB + st * TILE_BYTES, &tmB, &full[st], kc0 + ks * TK, (g - pa) * p.nb_pad + n0);
+              mbar_arrive_expect_tx(&full[st], 2 * TILE_BYTES);  // this CTA's stage: both whole tiles
+              if (CS == 1) {
+                tma_load_2d(sA + st * TILE_BYTES, &tmA, &full[st], kc0 + ks * TK, pa * p.ma_pad + m0);
+                tma_load_2d(sB + st * TILE_BYTES, &tmB, &full[st], kc0 + ks * TK, (g - pa) * p.nb_pad + n0);
+              } else {
+                tma_load_2d_mc(sA + st * TILE_BYTES + rj * A_SLICE * 128, &tmA, &full[st], kc0 + ks * TK,
+                               pa * p.ma_pad + m0 + rj * A_SLICE, row_mask);
+                tma_load_2d_mc(sB + st * TILE_BYTES + ri * B_SLICE * 128, &tmB, &full[st], kc0 + ks * TK,
+                               (g - pa) * p.nb_pad + n0 + ri * B_SLICE, col_mask);
+              }
             }
       }
+      // producer tail: every stage released by every CTA this one writes into, so no peer commit
+      // or load into this CTA is still in flight when it exits
+      if (CS > 1)
+        for (int k = 0; k < STAGES && ok; ++k, ++it)
+          ok = mbar_wait(&empty[it % STAGES], ((uint32_t)(it / STAGES) + 1) & 1u, abort_flag, deadline);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
@@ -420,7 +483,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 umma_bf16(dt, sdesc_sw128(a_addr + k16 * 32), sdesc_sw128(b_addr + k16 * 32), acc);
                 acc = 1;
               }
-              umma_commit(&empty[st]);
+              if (CS == 1)
+                umma_commit(&empty[st]);
+              else
+                umma_commit_mc(&empty[st], (uint16_t)(row_mask | col_mask));
             }
           if (ok) umma_commit(&acc_full[buf]);
         }
@@ -548,6 +614,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) rd_set_status(p.status, RD_DEV_TIMEOUT, blockIdx.x);
+  if (CS > 1) {
+    if (*abort_flag) {  // loads a peer issued before giving up land within microseconds
+      const unsigned long long until = globaltimer() + 50000ull;
+      while (globaltimer() < until) {
+      }
+    }
+    cluster_sync();  // no CTA leaves while a peer may still address its shared memory
+  }
   // (the status word is only read at the start of a CTA: a stale value merely skips work)
   if (warp == 1) {
     tc_fence_after();
@@ -602,13 +676,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D map over digit planes: inner dim k_pad (contiguous), outer dim s * rows_pad
-cudaError_t make_map(CUtensorMap* m, const void* base, int k_pad, long long rows) {
+// 2D map over digit planes: inner dim k_pad (contiguous), outer dim s * rows_pad; boxes of TK x
+// box_rows (a whole tile, or the slice of a tile one CTA of a cluster loads)
+cudaError_t make_map(CUtensorMap* m, const void* base, int k_pad, long long rows, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
-  cuuint32_t box[2] = {TK, TM};
+  cuuint32_t box[2] = {TK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -666,19 +741,91 @@ cudaError_t slice_b(rd_ctx* h, const View& v, int cols_pad, int k_pad, cudaStrea
 // C (c_rows x c_cols, ldc) = alpha * A (M x K) * B (K x N) + beta * C; with D != nullptr the product is
 // decoded into D (n x n) instead and Ystore (n x n, may be null) receives Y.  `flops` is the
 // algorithmic count of one product; the profile counts the issued digit products.
+// Cluster shapes of the split GEMM (see split_gemm_kernel).  With one CTA per SM, a cluster needs
+// CM * CN SMs of one GPC; the 2 x 2 shape is taken only when whole clusters still cover nearly every
+// SM, else 2 x 1.  Products with a single tile row run without clusters.
+struct Shape {
+  int cm, cn;
+};
+
+template <int CM, int CN>
+cudaError_t launch_split(const CUtensorMap& ta, const CUtensorMap& tb, const SplitArgs& a, int ctas, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<CM, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CM * CN;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, split_gemm_kernel<CM, CN>, ta, tb, a);
+}
+
+template <int CM, int CN>
+int active_cluster_sms() {
+  if (cudaFuncSetAttribute(split_gemm_kernel<CM, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SMEM_BYTES) != cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CM * CN * 1024);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CM * CN;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, split_gemm_kernel<CM, CN>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n * CM * CN;
+}
+
+Shape cluster_shape(int device) {
+  static int cached_dev = -1;
+  static Shape cached{1, 1};
+  if (cached_dev == device) return cached;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const int s22 = active_cluster_sms<2, 2>(), s21 = active_cluster_sms<2, 1>();
+  cached = (s22 >= sms - sms / 32) ? Shape{2, 2} : (s21 > 0 ? Shape{2, 1} : Shape{1, 1});
+  cached_dev = device;
+  return cached;
+}
+
+// C (c_rows x c_cols, ldc) = alpha * A (M x K) * B (K x N) + beta * C; with D != nullptr the product is
+// decoded into D (n x n) instead and Ystore (n x n, may be null) receives Y.  `flops` is the
+// algorithmic count of one product; the profile counts the issued digit products.
 cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, int K, double alpha, double beta,
                        double* C, long long ldc, int c_rows, int c_cols, int32_t* D, double* Ystore, double flops,
                        cudaStream_t st) {
   rd_split_plan* P = h->split;
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   if (M % 64 || N % 64 || K % 64) return cudaErrorInvalidValue;
-  const int ma_pad = round_up(M, TM), nb_pad = round_up(N, TN), k_pad = round_up(K, KAPPA);  // k_pad <= N + 128
+  Shape sh = (M > TM && N > TN) ? cluster_shape(h->device) : Shape{1, 1};
+  // the padded extents are whole cluster blocks (<= N + 128 each, within the digit buffers)
+  const int ma_pad = round_up(M, TM * sh.cm), nb_pad = round_up(N, TN * sh.cn), k_pad = round_up(K, KAPPA);
   cudaError_t e;
   if ((e = slice_a(h, A, ma_pad, k_pad, st)) != cudaSuccess) return e;
   if ((e = slice_b(h, B, nb_pad, k_pad, st)) != cudaSuccess) return e;
   CUtensorMap ta, tb;
-  if ((e = make_map(&ta, P->digA, k_pad, (long long)P->s * ma_pad)) != cudaSuccess) return e;
-  if ((e = make_map(&tb, P->digB, k_pad, (long long)P->s * nb_pad)) != cudaSuccess) return e;
+  if ((e = make_map(&ta, P->digA, k_pad, (long long)P->s * ma_pad, TM / sh.cn)) != cudaSuccess) return e;
+  if ((e = make_map(&tb, P->digB, k_pad, (long long)P->s * nb_pad, TN / sh.cm)) != cudaSuccess) return e;
   SplitArgs a{};
   a.eA = P->eA;
   a.eB = P->eB;
@@ -704,16 +851,15 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   a.log_gamma = log(h->gamma);
   a.tau = h->tau;
   a.status = h->dStatus;
-  static bool attr = false;
-  if (!attr) {
-    if ((e = cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SMEM_BYTES)) != cudaSuccess)
-      return e;
-    attr = true;
-  }
-  const int tiles = (ma_pad / TM) * (nb_pad / TN);
+  const int ctas = (ma_pad / TM) * (nb_pad / TN);
   if ((e = rd_prof_begin(h, st, RD_PROF_SPLIT)) != cudaSuccess) return e;
-  split_gemm_kernel<<<tiles, THREADS, SMEM_BYTES, st>>>(ta, tb, a);
+  if (sh.cm == 2 && sh.cn == 2)
+    e = launch_split<2, 2>(ta, tb, a, ctas, st);
+  else if (sh.cm == 2)
+    e = launch_split<2, 1>(ta, tb, a, ctas, st);
+  else
+    e = launch_split<1, 1>(ta, tb, a, ctas, st);
+  if (e != cudaSuccess) return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, st, RD_PROF_SPLIT, flops * (double)P->s * (P->s + 1) / 2.0);
 }
@@ -840,7 +986,8 @@ rd_status rd_split_prepare(rd_ctx* h, int s) {
     rd_split_plan* P = new rd_split_plan();
     h->split = P;
     P->N = h->N;
-    const size_t NK = (size_t)h->N * ((size_t)h->N + KAPPA);  // rows x K padded to whole chunks
+    // rows and K padded to whole cluster blocks and chunks: each at most N + 128
+    const size_t NK = ((size_t)h->N + KAPPA) * ((size_t)h->N + KAPPA);
     const size_t dig = (size_t)MAX_SLICES * NK * sizeof(__nv_bfloat16);
     const size_t ex = (NK / KAPPA + 64) * sizeof(int);
     cudaError_t e = cudaSuccess;
