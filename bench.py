@@ -242,6 +242,78 @@ def replica_throughput(world, flop_per_step, steps, total_ms):
     return world * flop_per_step * steps / (total_ms * 1e-3) / 1e12
 
 
+def bfs_fraction(A, D, sources):
+    """Fraction of the D entries of the sampled source columns equal to BFS hop distance (scipy:
+    a library BFS, not the oracle); D[i, j] is the distance j -> i, unreachable = INT32_MAX."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import shortest_path
+
+    G = sp.csr_matrix(np.ascontiguousarray(A.T))  # G[u, v] = 1 for the edge u -> v
+    dist = shortest_path(G, unweighted=True, indices=sources)  # dist[k, i]: sources[k] -> i
+    truth = np.where(np.isinf(dist), np.iinfo(np.int32).max, dist).astype(np.int64)
+    got = D[:, sources].T.astype(np.int64)
+    return float(np.mean(got == truth))
+
+
+def verify_graphs(rd, h, wl, A_dev, modes, args, other, D, dev):
+    import torch
+
+    names = [args.precision] + ([other] if other else [])
+    out = {nm: {"graphs_D_identical_to_oracle": 0, "graphs_checked": 0} for nm in names}
+    per_graph = {}
+    sources = np.linspace(0, args.n - 1, 256).astype(np.int64)
+    n = args.n
+    Ys = {nm: torch.empty((n, n), dtype=torch.float64, device=dev) for nm in names}
+    Ds = {nm: torch.empty((n, n), dtype=torch.int32, device=dev) for nm in names}
+    for i, (kind, frac, A, g) in enumerate(wl):
+        path = os.path.join(GOLDEN, f"large_{kind}_{frac}.json")
+        if not os.path.exists(path):
+            continue
+        with open(path) as f:
+            gold = json.load(f)
+        rec = {}
+        for nm in names:
+            rd.rd_set_precision(h, modes[nm], args.slices if nm == args.precision else 0)
+            rd.rd_load(h, A_dev[i // 2], None, g)
+            f0 = rd.rd_get_stats(h)["fallbacks"]
+            rd.rd_apsp(h, Ds[nm], Ys[nm])
+            torch.cuda.synchronize()
+            sg = rd.rd_get_stats(h)
+            Dh = Ds[nm].cpu().numpy()
+            same = hashlib.sha256(Dh.astype("<i4").tobytes()).hexdigest() == gold["sha256_D"]
+            out[nm]["graphs_checked"] += 1
+            out[nm]["graphs_D_identical_to_oracle"] += int(same)
+            if nm == "split":
+                redone = sg["fallbacks"] > f0
+                rec["split"] = {"precision_used": "split" if sg["precision_used"] else "fp64",
+                                "digits": sg["slices"] if sg["precision_used"] else None,
+                                "screen_bits": round(sg["split_screen_bits"], 1),
+                                "locality_order": bool(sg["split_order"]),
+                                "sampled_row_residual": sg["split_residual"] if sg["precision_used"] else None,
+                                "redone_by_self_check": bool(redone)}
+            if nm == args.precision:
+                rec["bfs_match_fraction"] = bfs_fraction(A, Dh, sources)
+        if other:
+            Yf, Yo = Ys["fp64"], Ys["split"]
+            pos = Yf > 0
+            rel = torch.where(pos, (Yo - Yf).abs() / torch.where(pos, Yf, torch.ones_like(Yf)), torch.zeros_like(Yf))
+            rec["split_vs_fp64"] = {"max_rel_err_Y": float(rel.max().item()),
+                                    "zero_pattern_equal": bool(torch.equal(Yo == 0, Yf == 0)),
+                                    "D_mismatches": int((Ds["split"] != Ds["fp64"]).sum().item())}
+        per_graph[f"{kind}_{frac}"] = rec
+    for nm in names:
+        if nm == "split":
+            recs = [r["split"] for r in per_graph.values() if "split" in r]
+            out[nm]["graphs_fp64_by_range_screen"] = sum(r["precision_used"] == "fp64" and not r["redone_by_self_check"]
+                                                         for r in recs)
+            out[nm]["graphs_redone_in_fp64_by_self_check"] = sum(r["precision_used"] == "fp64" and
+                                                                 r["redone_by_self_check"] for r in recs)
+    out["per_graph"] = per_graph
+    out["bfs_sample"] = "256 evenly spaced source columns per graph (scipy shortest_path, unweighted)"
+    rd.rd_set_precision(h, modes[args.precision], args.slices)
+    return out
+
+
 def pct(xs, q):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
@@ -368,39 +440,12 @@ def main():
                "h2d_bytes_per_step": n * n + 4 * args.goals * 2 + 8 * args.goals * n,
                "d2h_bytes_per_step": 4 * n * n + 8 * args.goals * n + 4 * args.goals * n}
 
-    # ---- D of every graph against the oracle's stored hash (tests/golden, written by the oracle)
+    # ---- every graph in both precisions: D against the oracle's stored hash (tests/golden, written by
+    # the oracle), the split path's Y against the FP64 path's Y, D against BFS truth (scipy, sampled
+    # source columns)
     verify = None
     if args.verify and n == 8192:
-        verify = {}
-        for name in ([args.precision, other] if compare else [args.precision]):
-            rd.rd_set_precision(h, modes[name], args.slices if name == args.precision else 0)
-            ok, checked, fell, screened, bits, resid = 0, 0, 0, 0, {}, {}
-            for i, (kind, frac, _, g) in enumerate(wl):
-                path = os.path.join(GOLDEN, f"large_{kind}_{frac}.json")
-                if not os.path.exists(path):
-                    continue
-                with open(path) as f:
-                    gold = json.load(f)
-                rd.rd_load(h, A_dev[i // 2], None, g)
-                f0 = rd.rd_get_stats(h)["fallbacks"]
-                rd.rd_apsp(h, D)
-                torch.cuda.synchronize()
-                sg = rd.rd_get_stats(h)
-                if name == "split":
-                    redone = sg["fallbacks"] > f0
-                    bits[f"{kind}_{frac}"] = round(sg["split_screen_bits"], 1)
-                    resid[f"{kind}_{frac}"] = (sg["slices"], sg["split_residual"]) if sg["precision_used"] else None
-                    fell += int(sg["precision_used"] != rd.RD_PREC_SPLIT_BF16 and redone)
-                    screened += int(sg["precision_used"] != rd.RD_PREC_SPLIT_BF16 and not redone)
-                dh = hashlib.sha256(D.cpu().numpy().astype("<i4").tobytes()).hexdigest()
-                checked += 1
-                ok += int(dh == gold["sha256_D"])
-            verify[name] = {"graphs_D_identical_to_oracle": ok, "graphs_checked": checked}
-            if name == "split":
-                verify[name]["graphs_fp64_by_range_screen"] = screened
-                verify[name]["graphs_redone_in_fp64_by_self_check"] = fell
-                verify[name]["range_screen_bits"] = bits
-                verify[name]["digits_and_sampled_row_residual"] = resid
+        verify = verify_graphs(rd, h, wl, A_dev, modes, args, other if compare else None, D, dev)
     rd.rd_destroy(h)
 
     if rank != 0:

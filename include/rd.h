@@ -101,6 +101,9 @@ typedef struct {
   int64_t prof_split_launches; /* the split GEMM's share of the profile: its launches,     */
   double prof_split_ms;   /* device time and issued digit-product flops (the rest of prof_*  */
   double prof_split_flops;/* is the FP64 GEMM)                                               */
+  int32_t split_order;    /* 1: the split path ran on P M P^T with the library's locality     */
+                          /* order (compact 64-node parts, 64-wide chunks); D, Y and goal    */
+                          /* rows are returned in the caller's node order either way         */
 } rd_stats;
 
 /* Create a handle for the unweighted graph A (n x n bytes) and gain gamma: validates gamma

@@ -9,6 +9,8 @@
 // The kernels are HBM-bound streams over the n x n byte matrix (and the N x N FP64 M): one
 // thread per column walks down a block of rows, so a warp reads 32 consecutive bytes of a row
 // per step and writes consecutive doubles of M.
+#include <vector>
+
 #include "rd_internal.cuh"
 
 namespace {
@@ -87,16 +89,17 @@ __global__ void succ_fill_kernel(const uint8_t* __restrict__ A, int n, const int
     if (A[(long long)j * n + v]) idx[w++] = j;
 }
 
-// Hop distances from sampled sources and their spread within chunks of consecutive nodes (the
-// split path's range screen).  One CTA per source: a level-synchronous BFS along the successor
-// lists (dist: n ints per source, -1 = not reached; at most n levels), then, one warp per chunk
-// of `chunk` consecutive nodes, the spread max d - min d over the chunk's reached nodes.  The
+// Hop distances from sampled sources and their spread within chunks of consecutive positions (the
+// split path's range screen; the node at position q is ord[q], or q without an order).  One CTA
+// per source: a level-synchronous BFS along the successor lists (dist: n ints per source, -1 = not
+// reached; at most n levels), then, one warp per chunk of `chunk` consecutive positions, the spread
+// max d - min d over the chunk's reached nodes.  The
 // largest spread over chunks and sources is atomicMax-ed into *out.  Sources: nodes
 // b n / nsrc + n / (2 nsrc), b = blockIdx.x.
 __global__ void __launch_bounds__(1024) chunk_spread_kernel(const int32_t* __restrict__ ptr,
                                                             const int32_t* __restrict__ succ, int n,
-                                                            int nsrc, int chunk, int32_t* __restrict__ dist,
-                                                            unsigned long long* out) {
+                                                            int nsrc, int chunk, const int32_t* __restrict__ ord,
+                                                            int32_t* __restrict__ dist, unsigned long long* out) {
   const int b = blockIdx.x, t = threadIdx.x;
   const int src = (int)(((long long)b * n) / nsrc + (n / nsrc) / 2);
   int32_t* d = dist + (long long)b * n;
@@ -122,8 +125,8 @@ __global__ void __launch_bounds__(1024) chunk_spread_kernel(const int32_t* __res
   for (int c = warp; c < nch; c += nwarps) {
     int lo = 0x7fffffff, hi = -1;
     const int v1 = min(n, (c + 1) * chunk);
-    for (int v = c * chunk + lane; v < v1; v += 32) {
-      const int x = d[v];
+    for (int q = c * chunk + lane; q < v1; q += 32) {
+      const int x = d[ord ? ord[q] : q];
       if (x >= 0) {
         lo = min(lo, x);
         hi = max(hi, x);
@@ -135,6 +138,238 @@ __global__ void __launch_bounds__(1024) chunk_spread_kernel(const int32_t* __res
     }
     if (lane == 0 && hi >= 0) atomicMax(out, (unsigned long long)(hi - lo));
   }
+}
+
+// Block-wide exclusive prefix sum of one count per thread (blockDim.x <= 1024); returns the
+// thread's offset and writes the total to *total.
+__device__ int block_exclusive_scan(int v, int* sh, int* total) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = (blockDim.x + 31) >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < nw ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) sh[lane] = s;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int before = (w > 0 ? sh[w - 1] : 0) + x - v;
+  *total = sh[nw - 1];
+  __syncthreads();
+  return before;
+}
+
+// Whole-graph BFS from `src` by one CTA (dist[v] = hops, -1 if not reached; at most n levels).
+__device__ void cta_bfs(const int32_t* __restrict__ ptr, const int32_t* __restrict__ succ, int n, int src,
+                        int32_t* dist) {
+  for (int v = threadIdx.x; v < n; v += blockDim.x) dist[v] = (v == src) ? 0 : -1;
+  __syncthreads();
+  for (int L = 0; L < n; ++L) {
+    int grew = 0;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      if (dist[v] != L) continue;
+      for (int x = ptr[v]; x < ptr[v + 1]; ++x) {
+        const int w = succ[x];
+        if (dist[w] < 0) {  // every writer of this level writes L + 1
+          dist[w] = L + 1;
+          grew = 1;
+        }
+      }
+    }
+    if (!__syncthreads_or(grew)) break;
+  }
+}
+
+// Smallest node maximising score[v] (score < 0: not a candidate); node 0 if there is none.
+__device__ int cta_argmax(const int32_t* score, int n, int* sh) {
+  long long best = -1;  // (score << 32) | (INT_MAX - v): the largest is the smallest v of the top score
+  for (int v = threadIdx.x; v < n; v += blockDim.x)
+    if (score[v] >= 0) best = max(best, ((long long)score[v] << 32) | (long long)(0x7fffffff - v));
+  for (int o = 16; o; o >>= 1) best = max(best, (long long)__shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ long long red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long b = -1;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = max(b, red[w]);
+    *sh = b < 0 ? 0 : 0x7fffffff - (int)(b & 0xffffffffll);
+  }
+  __syncthreads();
+  const int r = *sh;
+  __syncthreads();
+  return r;
+}
+
+// Landmark coordinates of the split path's locality order, by one CTA: L1 = the farthest node from
+// node 0, L2 = the farthest from L1, L3 = the node farthest from both (largest min(d_L1, d_L2));
+// each node gets cu = d_L1 - d_L3 and cv = d_L1 + d_L3 (on a mesh these are its two axes), or
+// cv = -1 when L1 or L3 does not reach it.  d0..d3: n ints each of scratch.
+__global__ void __launch_bounds__(1024) landmark_kernel(const int32_t* __restrict__ ptr,
+                                                        const int32_t* __restrict__ succ, int n, int32_t* d0,
+                                                        int32_t* d1, int32_t* d2, int32_t* cu, int32_t* cv) {
+  __shared__ int sh;
+  cta_bfs(ptr, succ, n, 0, d0);
+  const int L1 = cta_argmax(d0, n, &sh);
+  cta_bfs(ptr, succ, n, L1, d1);
+  const int L2 = cta_argmax(d1, n, &sh);
+  cta_bfs(ptr, succ, n, L2, d2);
+  for (int v = threadIdx.x; v < n; v += blockDim.x) d0[v] = (d1[v] >= 0 && d2[v] >= 0) ? min(d1[v], d2[v]) : -1;
+  __syncthreads();
+  const int L3 = cta_argmax(d0, n, &sh);
+  cta_bfs(ptr, succ, n, L3, d2);
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    const bool r = d1[v] >= 0 && d2[v] >= 0;
+    cu[v] = r ? d1[v] - d2[v] : 0;
+    cv[v] = r ? d1[v] + d2[v] : -1;
+  }
+}
+
+// One level of the recursive coordinate bisection behind the split path's locality order.  CTA c
+// splits the part [parts[2c], parts[2c+1]) of the order `ord` (node at each position) into a first
+// part of m0 = 64 ceil(m / 128) positions and the rest, along the landmark axis (cu or cv) with the
+// larger extent over the part: the first part takes the m0 smallest coordinates, ties in order of
+// position; nodes without coordinates go last.  Both parts keep their nodes' relative order (a
+// stable partition), so the result is deterministic.  Coordinates are counted in a histogram
+// (hist: 2m + 2 ints of scratch at 2 b + 2 c; offsets past 2m share the last real bucket).
+__global__ void __launch_bounds__(1024) rcb_kernel(const int32_t* __restrict__ parts, const int32_t* __restrict__ cu,
+                                                   const int32_t* __restrict__ cv, int32_t* ord, int32_t* tmp,
+                                                   int32_t* hist_all) {
+  __shared__ int sh[32];
+  __shared__ int sh_cut;
+  const int b = parts[2 * blockIdx.x], e = parts[2 * blockIdx.x + 1];
+  const int m = e - b, m0 = 64 * ((m + 127) / 128);
+  const int t = threadIdx.x, T = blockDim.x;
+  if (m0 >= m) return;
+  // extents of both axes over the part's reached nodes
+  int umin = 0x7fffffff, umax = -0x7fffffff, vmin = 0x7fffffff, vmax = -0x7fffffff;
+  for (int q = b + t; q < e; q += T) {
+    const int v = ord[q];
+    if (cv[v] < 0) continue;
+    umin = min(umin, cu[v]);
+    umax = max(umax, cu[v]);
+    vmin = min(vmin, cv[v]);
+    vmax = max(vmax, cv[v]);
+  }
+  for (int o = 16; o; o >>= 1) {
+    umin = min(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+    umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+    vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+    vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  }
+  __shared__ int ext[4][32];
+  if ((t & 31) == 0) {
+    ext[0][t >> 5] = umin;
+    ext[1][t >> 5] = umax;
+    ext[2][t >> 5] = vmin;
+    ext[3][t >> 5] = vmax;
+  }
+  __syncthreads();
+  if (t == 0) {
+    for (int w = 1; w < (T >> 5); ++w) {
+      ext[0][0] = min(ext[0][0], ext[0][w]);
+      ext[1][0] = max(ext[1][0], ext[1][w]);
+      ext[2][0] = min(ext[2][0], ext[2][w]);
+      ext[3][0] = max(ext[3][0], ext[3][w]);
+    }
+  }
+  __syncthreads();
+  const bool use_u = (ext[1][0] - ext[0][0]) >= (ext[3][0] - ext[2][0]);
+  const int lo = use_u ? ext[0][0] : ext[2][0];
+  const int cap = 2 * m;  // last real bucket; bucket cap + 1 holds nodes without coordinates
+  auto key_of = [&](int q) {
+    const int v = ord[q];
+    if (cv[v] < 0) return cap + 1;
+    return min(cap, (use_u ? cu[v] : cv[v]) - lo);
+  };
+  int32_t* hist = hist_all + 2 * b + 2 * blockIdx.x;
+  for (int k = t; k < cap + 2; k += T) hist[k] = 0;
+  __syncthreads();
+  for (int q = b + t; q < e; q += T) atomicAdd(&hist[key_of(q)], 1);
+  __syncthreads();
+  // the cut key: the smallest k with count(key <= k) >= m0
+  {
+    const int nb = cap + 2, seg = (nb + T - 1) / T, k0 = t * seg, k1 = min(nb, k0 + seg);
+    int c = 0;
+    for (int k = k0; k < k1; ++k) c += hist[k];
+    int tot;
+    int before = block_exclusive_scan(c, sh, &tot);
+    if (before < m0 && before + c >= m0) {
+      for (int k = k0; k < k1; ++k) {
+        before += hist[k];
+        if (before >= m0) {
+          sh_cut = k;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int Ks = sh_cut;
+  // contiguous segment of positions per thread, so that "earlier position" is a prefix count
+  const int per = (m + T - 1) / T;
+  const int q0 = b + t * per, q1 = min(e, q0 + per);
+  int below = 0, tied = 0;
+  for (int q = q0; q < q1; ++q) {
+    const int k = key_of(q);
+    below += (k < Ks);
+    tied += (k == Ks);
+  }
+  int nbelow, ntied;
+  block_exclusive_scan(below, sh, &nbelow);
+  const int tied_before = block_exclusive_scan(tied, sh, &ntied);
+  const int take = m0 - nbelow;  // tied nodes that join the first part, by position
+  int first = 0;
+  {
+    int k = tied_before;
+    for (int q = q0; q < q1; ++q) {
+      const int key = key_of(q);
+      const bool in0 = (key < Ks) || (key == Ks && k < take);
+      if (key == Ks) ++k;
+      first += in0;
+    }
+  }
+  int nfirst;
+  const int first_before = block_exclusive_scan(first, sh, &nfirst);
+  {
+    int k = tied_before, i0 = b + first_before, i1 = b + m0 + (q0 - b - first_before);
+    for (int q = q0; q < q1; ++q) {
+      const int key = key_of(q);
+      const bool in0 = (key < Ks) || (key == Ks && k < take);
+      if (key == Ks) ++k;
+      if (in0)
+        tmp[i0++] = ord[q];
+      else
+        tmp[i1++] = ord[q];
+    }
+  }
+  __syncthreads();
+  for (int q = b + t; q < e; q += T) ord[q] = tmp[q];
+}
+
+__global__ void iota_kernel(int n, int32_t* __restrict__ ord) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) ord[q] = q;
+}
+
+__global__ void inverse_perm_kernel(const int32_t* __restrict__ ord, int n, int32_t* __restrict__ pos) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) pos[ord[q]] = q;
+}
+
+// M'[i][j] = M[ord[i]][ord[j]] for i, j < n; the identity padding (rows/columns n..N-1) is kept
+__global__ void permute_m_kernel(const double* __restrict__ M, const int32_t* __restrict__ ord, int n, int N,
+                                 double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * N) return;
+  const int i = (int)(t / N), j = (int)(t % N);
+  out[t] = (i < n && j < n) ? M[(long long)ord[i] * N + ord[j]] : (i == j ? 1.0 : 0.0);
 }
 
 __global__ void copy_rows_kernel(const double* __restrict__ R, long long ldr, int rows, int cols,
@@ -194,11 +429,87 @@ cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }
 
-cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, int32_t* dist, unsigned long long* out,
-                            cudaStream_t s) {
+cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, const int32_t* ord, int32_t* dist,
+                            unsigned long long* out, cudaStream_t s) {
   cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
-  chunk_spread_kernel<<<nsrc, 1024, 0, s>>>(h->dDeg + (h->n + 1), h->dSucc, h->n, nsrc, chunk, dist, out);
+  chunk_spread_kernel<<<nsrc, 1024, 0, s>>>(h->dDeg + (h->n + 1), h->dSucc, h->n, nsrc, chunk, ord, dist, out);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
+}
+
+// Locality order of the split path: landmark coordinates (landmark_kernel), then recursive
+// coordinate bisection into parts of 64 consecutive positions (rcb_kernel), h->dOrd[position] =
+// node, h->dPos[node] = position.  The part boundaries depend on n alone, so the host lists them;
+// one launch per depth.
+cudaError_t rd_locality_order(rd_ctx* h, cudaStream_t s) {
+  const int n = h->n;
+  int32_t* w = reinterpret_cast<int32_t*>(h->dS);  // free before the factorisation (>= N^2 ints)
+  int32_t* d0 = w;
+  int32_t* d1 = w + (size_t)n;
+  int32_t* d2 = w + 2 * (size_t)n;
+  int32_t* cu = w + 3 * (size_t)n;
+  int32_t* cv = w + 4 * (size_t)n;
+  int32_t* tmp = w + 5 * (size_t)n;
+  int32_t* dparts = w + 6 * (size_t)n;  // < 4 n / 64 + 4 ints
+  std::vector<int32_t> all;             // every depth's list of parts to split, concatenated
+  std::vector<std::pair<int, int>> depth_span;
+  std::vector<std::pair<int, int>> cur{{0, n}};
+  while (true) {
+    std::vector<std::pair<int, int>> next;
+    const int first = (int)all.size() / 2;
+    for (auto& pr : cur) {
+      const int m = pr.second - pr.first, m0 = 64 * ((m + 127) / 128);
+      if (m0 >= m) continue;
+      all.push_back(pr.first);
+      all.push_back(pr.second);
+      next.push_back({pr.first, pr.first + m0});
+      next.push_back({pr.first + m0, pr.second});
+    }
+    const int count = (int)all.size() / 2 - first;
+    if (count == 0) break;
+    depth_span.push_back({first, count});
+    cur.swap(next);
+  }
+  // histograms: 2 m + 2 ints per part at 2 b + 2 c, after the part list
+  int32_t* hist = dparts + all.size() + 4;
+  cudaError_t e;
+  if (!all.empty() &&
+      (e = cudaMemcpyAsync(dparts, all.data(), all.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+    return e;
+  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
+  landmark_kernel<<<1, 1024, 0, s>>>(h->dDeg + (n + 1), h->dSucc, n, d0, d1, d2, cu, cv);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
+  iota_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, h->dOrd);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  for (auto& d : depth_span) {
+    if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
+    rcb_kernel<<<d.second, 1024, 0, s>>>(dparts + 2 * d.first, cu, cv, h->dOrd, tmp, hist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  }
+  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
+  inverse_perm_kernel<<<(n + 255) / 256, 256, 0, s>>>(h->dOrd, n, h->dPos);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the host list must outlive the copy: wait here (once per graph that needs the order)
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
+}
+
+// M' = P M P^T in place of M (through the inverse buffer, free before the factorisation)
+cudaError_t rd_permute_m(rd_ctx* h, cudaStream_t s) {
+  const long long NN = (long long)h->N * h->N;
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
+  if (e != cudaSuccess) return e;
+  permute_m_kernel<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(h->dLU, h->dOrd, h->n, h->N, h->dT);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  double* t = h->dLU;
+  h->dLU = h->dT;
+  h->dT = t;
+  return cudaSuccess;
 }

@@ -4,7 +4,8 @@
 //
 // Arithmetic (an Ozaki-style splitting, written from the published scheme of Ozaki, Ogita,
 // Oishi and Rump, 2012, adapted to entrywise accuracy):
-//   * Each operand is cut into chunks of KAPPA = 256 along K.  Every (row, chunk) of A and
+//   * Each operand is cut into chunks of KAPPA = 256 along K (64 when the graph runs in the
+//     locality order, whose 64-node parts are compact).  Every (row, chunk) of A and
 //     every (chunk, column) of B gets its own power of two 2^e with |x| 2^-e < 1/2, so a chunk
 //     of small entries (far nodes, entries gamma^d) keeps its own scale.
 //   * x 2^-e is written in s balanced base-128 digits d_p in [-64, 64] (round to nearest):
@@ -47,7 +48,8 @@
 namespace {
 
 constexpr int SIGMA = 7;          // bits per digit (balanced base 2^SIGMA)
-constexpr int KAPPA = 256;        // exponent / read-out chunk along K
+constexpr int KAPPA_WIDE = 256;   // exponent / read-out chunk along K (natural order)
+constexpr int KAPPA_NARROW = 64;  // the same with the locality order (compact 64-node parts)
 constexpr int TM = 128, TN = 128, TK = 64;
 constexpr int STAGES = 4;
 constexpr int EPI_WARPS = 8;
@@ -57,7 +59,8 @@ constexpr int EXP_ZERO = -16384;                   // exponent of an all-zero ch
 constexpr int MAX_SLICES = 15;                     // group sums exact: 256 * 15 * 2^12 < 2^24
 constexpr int LEAF = RD_BF;                        // FP64 diagonal leaves (64)
 constexpr unsigned long long WAIT_NS = 4000000000ull;
-static_assert(SIGMA == RD_SPLIT_DIGIT_BITS && KAPPA == RD_SCREEN_CHUNK, "range screen out of step with the digits");
+static_assert(SIGMA == RD_SPLIT_DIGIT_BITS && KAPPA_WIDE == RD_SCREEN_CHUNK && KAPPA_NARROW == RD_SCREEN_CHUNK_ORDERED,
+              "range screen out of step with the digits");
 
 constexpr uint32_t IDESC = (1u << 4)               // D: FP32
                            | (1u << 7)             // A: BF16
@@ -130,27 +133,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// the same load delivered to the CTAs of `mask` in the cluster, at this CTA's smem offsets, each
-// completing its own barrier at the offset of `bar`
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%3, "
-      "%4}], [%2], %5;" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -177,15 +159,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-}
-
-// arrive on the barrier at the offset of `bar` in every CTA of `mask` once the prior MMAs complete
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -252,46 +225,48 @@ __device__ __forceinline__ void write_digits(double x, int e, int s, __nv_bfloat
 
 // Role A (row chunks contiguous in memory): one warp per (row, chunk).
 // digits[p][row][k] (plane = rows_pad * k_pad), exps[chunk][row].
+template <int KP>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, long long ld, int tri,
                                                          int rows, int cols, int rows_pad, int k_pad, int s,
                                                          __nv_bfloat16* __restrict__ dig, int* __restrict__ exps,
                                                          int* status) {
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
-  const int nch = k_pad / KAPPA;
+  const int nch = k_pad / KP;
   if (w >= (long long)rows_pad * nch) return;
   const int r = (int)(w / nch);
-  const int c0 = (int)(w % nch) * KAPPA;
+  const int c0 = (int)(w % nch) * KP;
   const long long plane = (long long)rows_pad * k_pad;
-  double v[KAPPA / 32];
+  double v[KP / 32];
   double mx = 0.0;
 #pragma unroll
-  for (int t = 0; t < KAPPA / 32; ++t) {
+  for (int t = 0; t < KP / 32; ++t) {
     v[t] = view_load(X, ld, r, c0 + lane + 32 * t, tri, rows, cols);
     mx = fmax(mx, fabs(v[t]));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int e = chunk_exponent(mx);
-  if (lane == 0) exps[(long long)(c0 / KAPPA) * rows_pad + r] = e;
+  if (lane == 0) exps[(long long)(c0 / KP) * rows_pad + r] = e;
 #pragma unroll
-  for (int t = 0; t < KAPPA / 32; ++t) write_digits(v[t], e, s, dig + (long long)r * k_pad + c0 + lane + 32 * t, plane);
+  for (int t = 0; t < KP / 32; ++t) write_digits(v[t], e, s, dig + (long long)r * k_pad + c0 + lane + 32 * t, plane);
   (void)status;
 }
 
 // Role B (the operand is K x N row-major; digits are wanted K-major per column): a block of 256
-// threads owns 16 columns of one chunk, stages the KAPPA x 16 block through shared memory, and
+// threads owns 16 columns of one chunk, stages the KP x 16 block through shared memory, and
 // each warp slices 2 columns.  digits[p][col][k], exps[chunk][col].
+template <int KP>
 __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ X, long long ld, int tri,
                                                          int krows, int cols, int cols_pad, int k_pad, int s,
                                                          __nv_bfloat16* __restrict__ dig, int* __restrict__ exps,
                                                          int* status) {
-  __shared__ double tile[KAPPA][17];
+  __shared__ double tile[KP][17];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n0 = blockIdx.x * 16;
-  const int c0 = blockIdx.y * KAPPA;
+  const int c0 = blockIdx.y * KP;
   const long long plane = (long long)cols_pad * k_pad;
-  for (int e = threadIdx.x; e < KAPPA * 16; e += 256) {
+  for (int e = threadIdx.x; e < KP * 16; e += 256) {
     const int rr = e / 16, cc = e % 16;
     tile[rr][cc] = view_load(X, ld, c0 + rr, n0 + cc, tri, krows, cols);
   }
@@ -299,10 +274,10 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
 #pragma unroll
   for (int cc = 0; cc < 2; ++cc) {
     const int col = warp * 2 + cc;
-    double v[KAPPA / 32];
+    double v[KP / 32];
     double mx = 0.0;
 #pragma unroll
-    for (int t = 0; t < KAPPA / 32; ++t) {
+    for (int t = 0; t < KP / 32; ++t) {
       v[t] = tile[lane + 32 * t][col];
       mx = fmax(mx, fabs(v[t]));
     }
@@ -310,9 +285,9 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = chunk_exponent(mx);
     const int n = n0 + col;
-    if (lane == 0) exps[(long long)(c0 / KAPPA) * cols_pad + n] = e;
+    if (lane == 0) exps[(long long)(c0 / KP) * cols_pad + n] = e;
 #pragma unroll
-    for (int t = 0; t < KAPPA / 32; ++t) write_digits(v[t], e, s, dig + (long long)n * k_pad + c0 + lane + 32 * t, plane);
+    for (int t = 0; t < KP / 32; ++t) write_digits(v[t], e, s, dig + (long long)n * k_pad + c0 + lane + 32 * t, plane);
   }
   (void)status;
 }
@@ -320,8 +295,8 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
 // ---- the split GEMM --------------------------------------------------------------------------
 
 struct SplitArgs {
-  const int* eA;     // [K_pad / KAPPA][ma_pad]
-  const int* eB;     // [K_pad / KAPPA][nb_pad]
+  const int* eA;     // [K_pad / KP][ma_pad]
+  const int* eB;     // [K_pad / KP][nb_pad]
   int ma_pad, nb_pad;
   int M, N, K;       // M, N, K multiples of 64
   int s;
@@ -336,22 +311,16 @@ struct SplitArgs {
   int d_rows, d_cols;
   double log_gamma, tau;
   int* status;       // [0] first error, [1] detail, [2] precision flags (RD_FLAG_RANGE)
+  // stores of C, D (and Y) go to row row_map[row] and column col_map[col] (nullptr: the identity):
+  // the products of a graph in the locality order write back in the caller's node order
+  const int32_t* row_map;
+  const int32_t* col_map;
 };
 
-// CM x CN clusters (launched as 1-D clusters of CM * CN CTAs, rank = ri * CN + rj) own a block of
-// CM x CN output tiles.  The A tile of a tile row is needed by the CN CTAs of that cluster row:
-// each of them loads one 128/CN-row slice and multicasts it to the row; likewise each CTA of a
-// cluster column loads one 128/CM-row slice of the column's B tile.  The L2 reads per CTA fall from
-// two tiles to 1/CN + 1/CM tiles per stage.  A stage of CTA X is written by the CTAs of X's row and
-// column, so X's `empty` barrier counts CM + CN - 1 releases, and every MMA warp releases a stage in
-// all of them (multicast commit).  All CTAs of a cluster walk the union of their K-ranges, which
-// keeps their stage sequences in step (the digits outside a tile's triangle are zero).
-template <int CM, int CN>
+template <int KP>
 __global__ void __launch_bounds__(THREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const SplitArgs p) {
-  constexpr int CS = CM * CN;
-  constexpr int A_SLICE = TM / CN, B_SLICE = TN / CM;  // rows of the slices this CTA loads
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -368,32 +337,23 @@ __global__ void __launch_bounds__(THREADS, 1)
   int8_t* fl_s = (int8_t*)(smem + FL_OFFSET);                    // [TN][TM], column-major
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int rank = CS > 1 ? (int)cluster_rank() : 0;
-  const int ri = rank / CN, rj = rank % CN;
-  const int clusters_n = p.nb_pad / (TN * CN);  // the padded extents are multiples of the cluster block
-  const int cm0 = (int)(blockIdx.x / CS / clusters_n) * (TM * CM);
-  const int cn0 = (int)(blockIdx.x / CS % clusters_n) * (TN * CN);
-  const int m0 = cm0 + ri * TM;
-  const int n0 = cn0 + rj * TN;
-  // the cluster's multicast groups: its row (same ri) and its column (same rj)
-  const uint16_t row_mask = (uint16_t)(((1u << CN) - 1u) << (ri * CN));
-  uint16_t col_mask = 0;
-#pragma unroll
-  for (int i = 0; i < CM; ++i) col_mask |= (uint16_t)(1u << (i * CN + rj));
+  const int tiles_n = (p.N + TN - 1) / TN;
+  const int m0 = (blockIdx.x / tiles_n) * TM;
+  const int n0 = (blockIdx.x % tiles_n) * TN;
   int kbeg = 0, kend = p.K;
-  if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, cm0 + CM * TM);
-  if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, cm0);
-  if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, cn0);
-  if (p.b_tri == RD_TRI_UPPER) kend = min(kend, cn0 + CN * TN);
-  // chunks are aligned to absolute multiples of KAPPA; the first and last may be partial
-  const int cbeg = kbeg / KAPPA;
-  const int nchunks = (kbeg < kend) ? (kend + KAPPA - 1) / KAPPA - cbeg : 0;
+  if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, m0 + TM);
+  if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, m0);
+  if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, n0);
+  if (p.b_tri == RD_TRI_UPPER) kend = min(kend, n0 + TN);
+  // chunks are aligned to absolute multiples of KP; the first and last may be partial
+  const int cbeg = kbeg / KP;
+  const int nchunks = (kbeg < kend) ? (kend + KP - 1) / KP - cbeg : 0;
   const int s = p.s;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], CM + CN - 1);
+      mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
@@ -410,7 +370,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CS > 1) cluster_sync();  // every CTA's barriers exist before a peer loads or commits into them
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const unsigned long long deadline = globaltimer() + WAIT_NS;
@@ -421,8 +380,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       int it = 0;
       bool ok = true;
       for (int c = 0; c < nloop && ok; ++c) {
-        const int kc0 = max(kbeg, (cbeg + c) * KAPPA);
-        const int ksteps = (min(kend, (cbeg + c + 1) * KAPPA) - kc0) / TK;
+        const int kc0 = max(kbeg, (cbeg + c) * KP);
+        const int ksteps = (min(kend, (cbeg + c + 1) * KP) - kc0) / TK;
         for (int g = 0; g < s && ok; ++g)
           for (int pa = 0; pa <= g && ok; ++pa)
             for (int ks = 0; ks < ksteps; ++ks, ++it) {
@@ -432,31 +391,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                 ok = false;
                 break;
               }
-              mbar_arrive_expect_tx(&full[st], 2 * TILE_BYTES);  // this CTA's stage: both whole tiles
-              if (CS == 1) {
-                tma_load_2d(sA + st * TILE_BYTES, &tmA, &full[st], kc0 + ks * TK, pa * p.ma_pad + m0);
-                tma_load_2d(sB + st * TILE_BYTES, &tmB, &full[st], kc0 + ks * TK, (g - pa) * p.nb_pad + n0);
-              } else {
-                tma_load_2d_mc(sA + st * TILE_BYTES + rj * A_SLICE * 128, &tmA, &full[st], kc0 + ks * TK,
-                               pa * p.ma_pad + m0 + rj * A_SLICE, row_mask);
-                tma_load_2d_mc(sB + st * TILE_BYTES + ri * B_SLICE * 128, &tmB, &full[st], kc0 + ks * TK,
-                               (g - pa) * p.nb_pad + n0 + ri * B_SLICE, col_mask);
-              }
+              mbar_arrive_expect_tx(&full[st], 2 * TILE_BYTES);
+              tma_load_2d(sA + st * TILE_BYTES, &tmA, &full[st], kc0 + ks * TK, pa * p.ma_pad + m0);
+              tma_load_2d(sB + st * TILE_BYTES, &tmB, &full[st], kc0 + ks * TK, (g - pa) * p.nb_pad + n0);
             }
       }
-      // producer tail: every stage released by every CTA this one writes into, so no peer commit
-      // or load into this CTA is still in flight when it exits
-      if (CS > 1)
-        for (int k = 0; k < STAGES && ok; ++k, ++it)
-          ok = mbar_wait(&empty[it % STAGES], ((uint32_t)(it / STAGES) + 1) & 1u, abort_flag, deadline);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       int it = 0, gi = 0;
       bool ok = true;
       for (int c = 0; c < nloop && ok; ++c) {
-        const int kc0 = max(kbeg, (cbeg + c) * KAPPA);
-        const int ksteps = (min(kend, (cbeg + c + 1) * KAPPA) - kc0) / TK;
+        const int kc0 = max(kbeg, (cbeg + c) * KP);
+        const int ksteps = (min(kend, (cbeg + c + 1) * KP) - kc0) / TK;
         for (int g = 0; g < s && ok; ++g, ++gi) {
           const int buf = gi & 1;
           const uint32_t use = (uint32_t)(gi >> 1);
@@ -483,10 +430,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 umma_bf16(dt, sdesc_sw128(a_addr + k16 * 32), sdesc_sw128(b_addr + k16 * 32), acc);
                 acc = 1;
               }
-              if (CS == 1)
-                umma_commit(&empty[st]);
-              else
-                umma_commit_mc(&empty[st], (uint16_t)(row_mask | col_mask));
+              umma_commit(&empty[st]);
             }
           if (ok) umma_commit(&acc_full[buf]);
         }
@@ -588,8 +532,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int ref = ra + rb_s[half * 64 + j];
         double v = ldexp((double)hi[j] + (double)lo[j * TM], ref);
         v = p.alpha * v;
+        const long long orow = p.row_map ? p.row_map[row] : row;
+        const long long ocol = p.col_map ? p.col_map[col] : col;
         if (p.C && row < p.c_rows && col < p.c_cols) {
-          double* cp = p.C + (long long)row * p.ldc + col;
+          double* cp = p.C + orow * p.ldc + ocol;
           if (p.beta != 0.0) v = fma(p.beta, *cp, v);
           if (p.store_c) *cp = v;
         }
@@ -601,12 +547,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (p.D && row < p.d_rows && col < p.d_cols) {
           int32_t d;
           if (!isfinite(v)) {
-            rd_set_status(p.status, RD_DEV_NONFINITE, row);
+            rd_set_status(p.status, RD_DEV_NONFINITE, (int)orow);
             d = RD_UNREACHABLE;
           } else {
             d = (row == col) ? 0 : rd_decode_entry(v, p.log_gamma, p.tau);
           }
-          p.D[(long long)row * p.ldd + col] = d;
+          p.D[orow * p.ldd + ocol] = d;
         }
       }
       if (lost && p.status) atomicOr(&p.status[2], RD_FLAG_RANGE);
@@ -614,14 +560,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) rd_set_status(p.status, RD_DEV_TIMEOUT, blockIdx.x);
-  if (CS > 1) {
-    if (*abort_flag) {  // loads a peer issued before giving up land within microseconds
-      const unsigned long long until = globaltimer() + 50000ull;
-      while (globaltimer() < until) {
-      }
-    }
-    cluster_sync();  // no CTA leaves while a peer may still address its shared memory
-  }
   // (the status word is only read at the start of a CTA: a stale value merely skips work)
   if (warp == 1) {
     tc_fence_after();
@@ -676,14 +614,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D map over digit planes: inner dim k_pad (contiguous), outer dim s * rows_pad; boxes of TK x
-// box_rows (a whole tile, or the slice of a tile one CTA of a cluster loads)
-cudaError_t make_map(CUtensorMap* m, const void* base, int k_pad, long long rows, int box_rows) {
+// 2D map over digit planes: inner dim k_pad (contiguous), outer dim s * rows_pad
+cudaError_t make_map(CUtensorMap* m, const void* base, int k_pad, long long rows) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
-  cuuint32_t box[2] = {TK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {TK, TM};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -713,119 +650,69 @@ struct rd_split_plan {
 
 namespace {
 
-// Slice the A operand (rows x k) into digA/eA/RA.
+// Slice the A operand (rows x k) into digA/eA (chunks of h->kappa along k).
 cudaError_t slice_a(rd_ctx* h, const View& v, int rows_pad, int k_pad, cudaStream_t st) {
   rd_split_plan* P = h->split;
   cudaError_t e = rd_prof_begin(h, st, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
-  const long long warps = (long long)rows_pad * (k_pad / KAPPA);
+  const long long warps = (long long)rows_pad * (k_pad / h->kappa);
   const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
-  slice_rows_kernel<<<blocks, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, rows_pad, k_pad, P->s, P->digA, P->eA,
-                                            h->dStatus);
+  if (h->kappa == KAPPA_NARROW)
+    slice_rows_kernel<KAPPA_NARROW><<<blocks, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, rows_pad, k_pad, P->s,
+                                                            P->digA, P->eA, h->dStatus);
+  else
+    slice_rows_kernel<KAPPA_WIDE><<<blocks, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, rows_pad, k_pad, P->s,
+                                                          P->digA, P->eA, h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, st, RD_PROF_NONE, 0.0);
 }
 
-// Slice the B operand (k x cols, row-major) into digB/eB/RB (K-major per column).
+// Slice the B operand (k x cols, row-major) into digB/eB (K-major per column).
 cudaError_t slice_b(rd_ctx* h, const View& v, int cols_pad, int k_pad, cudaStream_t st) {
   rd_split_plan* P = h->split;
   cudaError_t e = rd_prof_begin(h, st, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
-  slice_cols_kernel<<<dim3(cols_pad / 16, k_pad / KAPPA), 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, cols_pad,
-                                                                        k_pad, P->s, P->digB, P->eB, h->dStatus);
+  const dim3 grid(cols_pad / 16, k_pad / h->kappa);
+  if (h->kappa == KAPPA_NARROW)
+    slice_cols_kernel<KAPPA_NARROW><<<grid, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, cols_pad, k_pad, P->s,
+                                                          P->digB, P->eB, h->dStatus);
+  else
+    slice_cols_kernel<KAPPA_WIDE><<<grid, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, cols_pad, k_pad, P->s,
+                                                        P->digB, P->eB, h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, st, RD_PROF_NONE, 0.0);
 }
 
-// C (M x N) = alpha * A (M x K) * B (K x N) + beta * C, or the decode of the product into D.
-// C (c_rows x c_cols, ldc) = alpha * A (M x K) * B (K x N) + beta * C; with D != nullptr the product is
-// decoded into D (n x n) instead and Ystore (n x n, may be null) receives Y.  `flops` is the
-// algorithmic count of one product; the profile counts the issued digit products.
-// Cluster shapes of the split GEMM (see split_gemm_kernel).  With one CTA per SM, a cluster needs
-// CM * CN SMs of one GPC; the 2 x 2 shape is taken only when whole clusters still cover nearly every
-// SM, else 2 x 1.  Products with a single tile row run without clusters.
-struct Shape {
-  int cm, cn;
-};
-
-template <int CM, int CN>
-cudaError_t launch_split(const CUtensorMap& ta, const CUtensorMap& tb, const SplitArgs& a, int ctas, cudaStream_t st) {
+template <int KP>
+cudaError_t launch_split(const CUtensorMap& ta, const CUtensorMap& tb, const SplitArgs& a, int tiles, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<CM, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)ctas);
-  cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CM * CN;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, split_gemm_kernel<CM, CN>, ta, tb, a);
-}
-
-template <int CM, int CN>
-int active_cluster_sms() {
-  if (cudaFuncSetAttribute(split_gemm_kernel<CM, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SMEM_BYTES) != cudaSuccess)
-    return 0;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CM * CN * 1024);
-  cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CM * CN;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, split_gemm_kernel<CM, CN>, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n * CM * CN;
-}
-
-Shape cluster_shape(int device) {
-  static int cached_dev = -1;
-  static Shape cached{1, 1};
-  if (cached_dev == device) return cached;
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  const int s22 = active_cluster_sms<2, 2>(), s21 = active_cluster_sms<2, 1>();
-  cached = (s22 >= sms - sms / 32) ? Shape{2, 2} : (s21 > 0 ? Shape{2, 1} : Shape{1, 1});
-  cached_dev = device;
-  return cached;
+  split_gemm_kernel<KP><<<tiles, THREADS, SMEM_BYTES, st>>>(ta, tb, a);
+  return cudaGetLastError();
 }
 
 // C (c_rows x c_cols, ldc) = alpha * A (M x K) * B (K x N) + beta * C; with D != nullptr the product is
-// decoded into D (n x n) instead and Ystore (n x n, may be null) receives Y.  `flops` is the
-// algorithmic count of one product; the profile counts the issued digit products.
+// decoded into D (n x n) instead and Ystore (n x n, may be null) receives Y.  row_map / col_map send
+// the stores to the caller's node order (see SplitArgs).  `flops` is the algorithmic count of one
+// product; the profile counts the issued digit products.
 cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, int K, double alpha, double beta,
                        double* C, long long ldc, int c_rows, int c_cols, int32_t* D, double* Ystore, double flops,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int32_t* row_map = nullptr, const int32_t* col_map = nullptr) {
   rd_split_plan* P = h->split;
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   if (M % 64 || N % 64 || K % 64) return cudaErrorInvalidValue;
-  Shape sh = (M > TM && N > TN) ? cluster_shape(h->device) : Shape{1, 1};
-  // the padded extents are whole cluster blocks (<= N + 128 each, within the digit buffers)
-  const int ma_pad = round_up(M, TM * sh.cm), nb_pad = round_up(N, TN * sh.cn), k_pad = round_up(K, KAPPA);
+  const int ma_pad = round_up(M, TM), nb_pad = round_up(N, TN), k_pad = round_up(K, h->kappa);  // k_pad <= N + 128
   cudaError_t e;
   if ((e = slice_a(h, A, ma_pad, k_pad, st)) != cudaSuccess) return e;
   if ((e = slice_b(h, B, nb_pad, k_pad, st)) != cudaSuccess) return e;
   CUtensorMap ta, tb;
-  if ((e = make_map(&ta, P->digA, k_pad, (long long)P->s * ma_pad, TM / sh.cn)) != cudaSuccess) return e;
-  if ((e = make_map(&tb, P->digB, k_pad, (long long)P->s * nb_pad, TN / sh.cm)) != cudaSuccess) return e;
+  if ((e = make_map(&ta, P->digA, k_pad, (long long)P->s * ma_pad)) != cudaSuccess) return e;
+  if ((e = make_map(&tb, P->digB, k_pad, (long long)P->s * nb_pad)) != cudaSuccess) return e;
   SplitArgs a{};
   a.eA = P->eA;
   a.eB = P->eB;
@@ -851,16 +738,13 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   a.log_gamma = log(h->gamma);
   a.tau = h->tau;
   a.status = h->dStatus;
-  const int ctas = (ma_pad / TM) * (nb_pad / TN);
+  a.row_map = row_map;
+  a.col_map = col_map;
+  const int tiles = (ma_pad / TM) * (nb_pad / TN);
   if ((e = rd_prof_begin(h, st, RD_PROF_SPLIT)) != cudaSuccess) return e;
-  if (sh.cm == 2 && sh.cn == 2)
-    e = launch_split<2, 2>(ta, tb, a, ctas, st);
-  else if (sh.cm == 2)
-    e = launch_split<2, 1>(ta, tb, a, ctas, st);
-  else
-    e = launch_split<1, 1>(ta, tb, a, ctas, st);
+  e = (h->kappa == KAPPA_NARROW) ? launch_split<KAPPA_NARROW>(ta, tb, a, tiles, st)
+                                 : launch_split<KAPPA_WIDE>(ta, tb, a, tiles, st);
   if (e != cudaSuccess) return e;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, st, RD_PROF_SPLIT, flops * (double)P->s * (P->s + 1) / 2.0);
 }
 
@@ -955,16 +839,17 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
                  T + (long long)lo * N + mid, N, 2.0 * t1 * m2, st);
 }
 
-// rows goals[c] of U^-1 (upper part of T, zero left of the diagonal) into R (64 x N)
+// rows goals[c] of U^-1 (upper part of T, zero left of the diagonal) into R (64 x N); with the
+// locality order, goal g sits at position pos[g]
 __global__ void gather_uinv_rows_kernel(const double* __restrict__ T, long long N, const int32_t* __restrict__ goals,
-                                        int k, double* __restrict__ R) {
+                                        const int32_t* __restrict__ pos, int k, double* __restrict__ R) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)RD_MAX_GOALS * N) return;
   const int c = (int)(t / N);
   const long long j = t % N;
   double v = 0.0;
   if (c < k) {
-    const long long g = goals[c];
+    const long long g = pos ? pos[goals[c]] : goals[c];
     if (j >= g) v = T[g * N + j];
   }
   R[t] = v;
@@ -986,10 +871,9 @@ rd_status rd_split_prepare(rd_ctx* h, int s) {
     rd_split_plan* P = new rd_split_plan();
     h->split = P;
     P->N = h->N;
-    // rows and K padded to whole cluster blocks and chunks: each at most N + 128
-    const size_t NK = ((size_t)h->N + KAPPA) * ((size_t)h->N + KAPPA);
+    const size_t NK = (size_t)h->N * ((size_t)h->N + KAPPA_WIDE);  // rows x K padded to whole chunks
     const size_t dig = (size_t)MAX_SLICES * NK * sizeof(__nv_bfloat16);
-    const size_t ex = (NK / KAPPA + 64) * sizeof(int);
+    const size_t ex = (NK / KAPPA_NARROW + 64) * sizeof(int);  // exponents of the narrowest chunks
     cudaError_t e = cudaSuccess;
     auto get = [&](void** ptr, size_t bytes) {
       if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
@@ -1030,8 +914,9 @@ cudaError_t rd_trtri_split(rd_ctx*, cudaStream_t) { return cudaSuccess; }
 cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s) {
   const int N = h->N;
   const double Nd = (double)N;
+  const int32_t* map = h->ordered ? h->dOrd : nullptr;  // D and Y back in the caller's node order
   return split_gemm(h, tri(h->dT, N, N, RD_TRI_UPPER), tri(h->dT, N, N, RD_TRI_LOWER_UNIT), N, N, N, 1.0, 0.0,
-                    nullptr, 0, 0, 0, D, Y, 2.0 * Nd * (Nd + 1) * (2 * Nd + 1) / 6.0, s);
+                    nullptr, 0, 0, 0, D, Y, 2.0 * Nd * (Nd + 1) * (2 * Nd + 1) / 6.0, s, map, map);
 }
 
 // Self-check of the split result: 64 rows of Y spread over the graph, computed like the goal
@@ -1074,11 +959,12 @@ cudaError_t rd_goal_split(rd_ctx* h, const int32_t* dgoals, int k, double* out, 
   cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   const long long total = RD_MAX_GOALS * N;
-  gather_uinv_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->dT, N, dgoals, k, h->dR);
+  gather_uinv_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->dT, N, dgoals,
+                                                                           h->ordered ? h->dPos : nullptr, k, h->dR);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   const double Nd = (double)N;
   return split_gemm(h, full(h->dR, N, RD_MAX_GOALS, (int)N), tri(h->dT, N, (int)N, RD_TRI_LOWER_UNIT), RD_MAX_GOALS,
                     (int)N, (int)N, 1.0, 0.0, out, h->n, k, h->n, nullptr, nullptr, RD_MAX_GOALS * Nd * (Nd + 1),
-                    s);
+                    s, nullptr, h->ordered ? h->dOrd : nullptr);
 }

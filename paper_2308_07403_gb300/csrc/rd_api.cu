@@ -77,7 +77,7 @@ void free_all(rd_ctx* h) {
     h->prof_ev = nullptr;
   }
   void* ptrs[] = {h->dA, h->dW, h->dLU, h->dT, h->dS, h->dR, h->dStatus, h->dRed, h->dDeg, h->dColsum,
-                  h->dSucc, h->dGoals, h->dNext, h->dYrows, h->dDout, h->dYout};
+                  h->dSucc, h->dGoals, h->dNext, h->dYrows, h->dDout, h->dYout, h->dOrd, h->dPos};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : h->ev)
@@ -122,6 +122,8 @@ rd_status load_impl(rd_ctx* h, const uint8_t* A, const float* W, double gamma) {
   h->split_floor = 0;
   h->screened = 0;
   h->screen_bits = -1.0;
+  h->ordered = 0;
+  h->kappa = RD_SCREEN_CHUNK;
   h->succ_ready = 0;
   RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 4 * sizeof(int), h->stream));
   RD_CK(h, rd_build_m(h, h->stream));
@@ -192,6 +194,8 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
   RD_ALLOC(h->dDeg, 2 * (size_t)n + 2);
   RD_ALLOC(h->dColsum, (size_t)n);
   RD_ALLOC(h->dGoals, RD_MAX_GOALS);
+  RD_ALLOC(h->dOrd, (size_t)n);
+  RD_ALLOC(h->dPos, (size_t)n);
 #undef RD_ALLOC
   for (auto& ev : h->ev)
     if (st == RD_OK) {
@@ -247,29 +251,59 @@ rd_status escalate(rd_ctx* h, bool range) {
 // chunk's largest entry, and the entries of Y fall by log2(1/gamma) bits per hop (Y_ij ~ gamma^d
 // for distance d), so a chunk whose nodes lie S hops apart as seen from one node costs about
 // S log2(1/gamma) of the 7 s bits the digits carry.  The largest S over the chunks, seen from 8
-// sampled sources, picks where the attempt starts: RD_SPLIT_START digits when they cover the
-// spread plus RD_SCREEN_RESULT_BITS bits of result, RD_SPLIT_MAX digits when those do, FP64
-// otherwise.  It only steers: the residual self-check still judges every split result.
+// sampled sources, decides where the attempt starts; a configuration fits when its digits cover
+// the spread plus RD_SCREEN_RESULT_BITS bits of result.  In order of preference:
+//   natural node order, 256-wide chunks, RD_SPLIT_START digits;
+//   the locality order (compact 64-node parts, see bisect_kernel), 64-wide chunks, RD_SPLIT_START;
+//   natural order, RD_SPLIT_MAX digits;  the locality order, RD_SPLIT_MAX digits;  FP64.
+// Large-diameter graphs (grids, meshes) are the ones that need the locality order: a 256-node run
+// of their natural order spans a whole row of the mesh.  The screen only steers: the residual
+// self-check still judges every split result.
+double spread_bits(rd_ctx* h, const int32_t* ord, int chunk, rd_status* st) {
+  *st = RD_OK;
+  cudaError_t e = cudaMemsetAsync(h->dRed, 0, sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess)
+    e = rd_chunk_spread(h, RD_SCREEN_SOURCES, chunk, ord, reinterpret_cast<int32_t*>(h->dS), h->dRed, h->stream);
+  unsigned long long spread = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&spread, h->dRed, sizeof(spread), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    *st = fail_cuda(h, e, "range screen");
+    return 0.0;
+  }
+  return (double)spread * std::log2(1.0 / h->gamma);
+}
+
 rd_status screen_split(rd_ctx* h) {
   h->screened = 1;
   h->screen_bits = -1.0;
+  h->ordered = 0;
+  h->kappa = RD_SCREEN_CHUNK;
   if (h->weighted || !h->dSucc) return RD_OK;
   if (!h->succ_ready) {
     RD_CK(h, rd_build_succ(h, h->stream));
     h->succ_ready = 1;
   }
-  RD_CK(h, cudaMemsetAsync(h->dRed, 0, sizeof(unsigned long long), h->stream));
-  RD_CK(h, rd_chunk_spread(h, RD_SCREEN_SOURCES, RD_SCREEN_CHUNK, reinterpret_cast<int32_t*>(h->dS), h->dRed,
-                           h->stream));
-  unsigned long long spread = 0;
-  RD_CK(h, cudaMemcpyAsync(&spread, h->dRed, sizeof(spread), cudaMemcpyDeviceToHost, h->stream));
-  RD_CK(h, cudaStreamSynchronize(h->stream));
-  const double bits = (double)spread * std::log2(1.0 / h->gamma);
-  h->screen_bits = bits;
-  if (bits + RD_SCREEN_RESULT_BITS > (double)RD_SPLIT_DIGIT_BITS * RD_SPLIT_MAX)
-    h->split_floor = -1;
-  else if (bits + RD_SCREEN_RESULT_BITS > (double)RD_SPLIT_DIGIT_BITS * RD_SPLIT_START)
+  const double r = RD_SCREEN_RESULT_BITS, start = (double)RD_SPLIT_DIGIT_BITS * RD_SPLIT_START,
+               most = (double)RD_SPLIT_DIGIT_BITS * RD_SPLIT_MAX;
+  rd_status st;
+  const double nat = spread_bits(h, nullptr, RD_SCREEN_CHUNK, &st);
+  if (st != RD_OK) return st;
+  h->screen_bits = nat;
+  if (nat + r <= start) return RD_OK;
+  RD_CK(h, rd_locality_order(h, h->stream));
+  const double ord = spread_bits(h, h->dOrd, RD_SCREEN_CHUNK_ORDERED, &st);
+  if (st != RD_OK) return st;
+  if (ord + r <= start || (nat + r > most && ord + r <= most)) {
+    h->ordered = 1;
+    h->kappa = RD_SCREEN_CHUNK_ORDERED;
+    h->screen_bits = ord;
+    if (ord + r > start) h->split_floor = RD_SPLIT_MAX;
+  } else if (nat + r <= most) {
     h->split_floor = RD_SPLIT_MAX;
+  } else {
+    h->split_floor = -1;
+  }
   return RD_OK;
 }
 
@@ -283,6 +317,8 @@ rd_status ensure_factored(rd_ctx* h) {
   for (;;) {
     const bool split = h->precision == RD_PREC_SPLIT_BF16 && h->split_floor >= 0;
     if (!split) {
+      h->ordered = 0;  // the FP64 path works in the caller's node order
+      h->kappa = RD_SCREEN_CHUNK;
       RD_CK(h, rd_lu_f64(h, h->stream));
       h->used_precision = RD_PREC_FP64;
       h->factored = 1;
@@ -293,6 +329,7 @@ rd_status ensure_factored(rd_ctx* h) {
     if (h->split_floor > s) s = h->split_floor;
     rd_status st = rd_split_prepare(h, s);
     if (st != RD_OK) return st;
+    if (h->ordered) RD_CK(h, rd_permute_m(h, h->stream));  // factor P M P^T
     RD_CK(h, rd_lu_split(h, h->stream));  // LU and both triangular inverses
     h->used_precision = RD_PREC_SPLIT_BF16;
     h->factored = 1;
@@ -420,6 +457,8 @@ rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices) {
     h->split_floor = 0;
     h->screened = 0;
     h->screen_bits = -1.0;
+    h->ordered = 0;
+    h->kappa = RD_SCREEN_CHUNK;
     if (h->factored) {
       // the factors in dLU belong to the old mode: rebuild M from the resident graph
       RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 2 * sizeof(int), h->stream));
@@ -560,6 +599,7 @@ rd_status rd_get_stats(rd_handle h, rd_stats* s) {
   s->split_residual = h->last_residual;
   s->split_flags = h->last_flags;
   s->split_screen_bits = h->screen_bits;
+  s->split_order = h->ordered;
   s->gamma = h->gamma;
   s->max_column_sum = h->max_colsum;
   s->tau = h->tau;

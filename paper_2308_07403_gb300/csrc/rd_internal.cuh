@@ -34,6 +34,7 @@
 #define RD_SPLIT_DIGIT_BITS 7  // bits per digit of the split operands
 #define RD_SCREEN_SOURCES 8  // BFS sources of the split path's range screen
 #define RD_SCREEN_CHUNK 256  // operand chunk along K that shares one scale (the split path's KAPPA)
+#define RD_SCREEN_CHUNK_ORDERED 64  // the same with the locality order
 #define RD_SCREEN_RESULT_BITS 34  // bits the digits must keep below a chunk's spread (2^-34 ~ 6e-11)
 
 struct rd_split_plan;       // defined by the split path
@@ -61,6 +62,8 @@ struct rd_ctx {
   int64_t succ_cap = 0;
   int succ_ready = 0;
   int32_t* dGoals = nullptr;   // RD_MAX_GOALS
+  int32_t* dOrd = nullptr;     // n: locality order of the split path, node at each position
+  int32_t* dPos = nullptr;     // n: its inverse, position of each node
   int32_t* dNext = nullptr;    // staging for host next-hop output (k x n)
   double* dYrows = nullptr;    // staging for host goal rows (k x n)
   int32_t* dDout = nullptr;    // staging for host D output (n x n), lazy
@@ -72,6 +75,8 @@ struct rd_ctx {
   int split_floor = 0;         // per graph: least digit count to use, -1 = FP64 (self-check history)
   int screened = 0;            // the range screen ran for the current graph and mode
   double screen_bits = -1.0;   // its estimate of the bits a chunk's spread costs (-1: not screened)
+  int ordered = 0;             // the split path runs on P M P^T with the locality order (dOrd)
+  int kappa = 256;             // chunk width of the split digits: 256, or 64 with the locality order
   int fallbacks = 0;           // split results redone (more digits or FP64) after the self-check
   double last_residual = 0.0;  // largest sampled-row residual of the last split result
   int last_flags = 0;          // precision flags raised while computing it
@@ -144,10 +149,15 @@ cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cud
 // ---- kernels in k_build.cu ----------------------------------------------------------------
 cudaError_t rd_build_m(rd_ctx* h, cudaStream_t s);       // M into dLU, degrees, column sums
 cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s);    // successor CSR from dA
-// largest hop spread within chunks of `chunk` consecutive nodes, BFS from nsrc sampled sources
-// (needs the successor lists; dist: nsrc * n ints of scratch) -> atomicMax into *out
-cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, int32_t* dist, unsigned long long* out,
-                            cudaStream_t s);
+// largest hop spread within chunks of `chunk` consecutive positions (node at position q: ord[q],
+// or q when ord is null), BFS from nsrc sampled sources (needs the successor lists; dist: nsrc * n
+// ints of scratch) -> atomicMax into *out
+cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, const int32_t* ord, int32_t* dist,
+                            unsigned long long* out, cudaStream_t s);
+// locality order for the split path (dOrd, dPos; uses dS as scratch; synchronises once)
+cudaError_t rd_locality_order(rd_ctx* h, cudaStream_t s);
+// dLU <- P M P^T (the permuted M; dT is used as the staging buffer and swapped in)
+cudaError_t rd_permute_m(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows, int cols,
                              double* out, long long ldo, cudaStream_t s);
 

@@ -66,6 +66,7 @@ class rd_stats(ctypes.Structure):
         ("split_screen_bits", ctypes.c_double),
         ("prof_split_launches", ctypes.c_int64), ("prof_split_ms", ctypes.c_double),
         ("prof_split_flops", ctypes.c_double),
+        ("split_order", ctypes.c_int32),
     ]
 
 

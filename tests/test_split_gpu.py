@@ -182,20 +182,52 @@ def test_range_screen_matches_bfs(rd, name):
     spread = screen_spread(A)
     bits = spread * np.log2(1.0 / g)
     Dg, _, st = run(rd, A, g, want_y=False)
-    assert st["split_screen_bits"] == pytest.approx(bits, rel=1e-12, abs=0.0)
-    if bits + 34 > 7 * 15:
+    if bits + 34 <= 7 * 12 or st["split_order"] == 0:
+        # natural order: the screen's estimate is the BFS spread of 256-node runs, exactly
+        assert st["split_order"] == 0
+        assert st["split_screen_bits"] == pytest.approx(bits, rel=1e-12, abs=0.0)
+        used = bits
+    else:
+        # the locality order was taken: it must have screened better than the natural order
+        assert st["split_screen_bits"] < bits
+        used = st["split_screen_bits"]
+    if used + 34 > 7 * 15:
         assert st["precision_used"] == rd.RD_PREC_FP64 and st["fallbacks"] == 0
     elif st["fallbacks"] == 0:
         assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16
-        assert st["slices"] == (15 if bits + 34 > 7 * 12 else 12)
+        assert st["slices"] == (15 if used + 34 > 7 * 12 else 12)
     assert np.array_equal(Dg, oracle.rdistance(A, g)), name
+
+
+def test_locality_order_path(rd):
+    """A 40-column grid: 256-node runs of the natural order span ~45 hops (95 bits at 0.9/Delta), so
+    the library factors P M P^T with its locality order (compact 64-node parts, 64-wide chunks).
+    D, Y, the goal rows and the greedy next hops must come back in the caller's node order."""
+    A = graphs.grid4(1000, 40)
+    g = graphs.gamma_frac(A, 0.9)
+    Do, Yo = oracle.rdistance(A, g, want_y=True)
+    Dg, Yg, st = run(rd, A, g)
+    assert st["split_order"] == 1 and st["precision_used"] == rd.RD_PREC_SPLIT_BF16, st
+    assert 0 < st["split_residual"] < 1e-9
+    assert rel_err(Yg, Yo) < YTOL
+    assert np.array_equal(Dg, Do)
+    goals = np.array([0, 13, 500, 999], dtype=np.int32)
+    rows = np.empty((goals.size, 1000))
+    nxt = np.empty((goals.size, 1000), np.int32)
+    with rd.Handle(A, g) as h:
+        h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
+        h.goal_solve(goals, rows)
+        h.greedy_next(goals, rows, nxt)
+        assert h.stats()["split_order"] == 1
+    assert rel_err(rows, Yo[goals]) < YTOL
+    assert np.array_equal(nxt, oracle.greedy_next(A, goals, rows))
 
 
 @pytest.mark.parametrize("kind,frac", [(k, f) for k in graphs.LARGE_KINDS for f in graphs.LARGE_FRACS])
 def test_split_full_size_D_identical(rd, kind, frac):
     """n = 8192: the D of the split mode hashes to the oracle's D.  ER and WS stay on the split
-    path; the 90 x 91 grid (a 256-node chunk spans ~47 hops of Y) goes to FP64 at the range screen,
-    without a wasted split attempt."""
+    path in their own node order; the 90 x 91 grid (a 256-node run of its natural order spans ~84
+    hops of Y) runs on the split path in the locality order, whose 64-node parts span ~17 hops."""
     p = os.path.join(HERE, "golden", f"large_{kind}_{frac}.json")
     if not os.path.exists(p):
         pytest.skip("golden file missing")
@@ -203,11 +235,9 @@ def test_split_full_size_D_identical(rd, kind, frac):
         rec = json.load(f)
     A, g = graphs.workload_large(kind, frac)
     Dg, _, st = run(rd, A, g, want_y=False)
-    if kind != "grid":
-        assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16, st
-        assert 0 < st["split_residual"] < 1e-9, st
-    else:
-        assert st["precision_used"] == rd.RD_PREC_FP64 and st["fallbacks"] == 0, st
+    assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16, st
+    assert 0 < st["split_residual"] < 1e-9, st
+    assert st["split_order"] == (1 if kind == "grid" else 0), st
     digest = hashlib.sha256(np.ascontiguousarray(Dg, dtype="<i4").tobytes()).hexdigest()
     if digest != rec["sha256_D"]:
         B = rec["block_rows"]
