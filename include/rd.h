@@ -93,7 +93,6 @@ typedef struct {
   int32_t fallbacks;      /* split results this handle redid (more digits or FP64)           */
   double split_residual;  /* largest entrywise relative residual of the sampled rows of the  */
                           /* last split result against M (the self-check; 1e-9 accepted)     */
-  int32_t split_flags;    /* 1: some digit-product term fell below the FP32 accumulators    */
   double split_screen_bits; /* range screen of the split path (digit count left open,        */
                           /* unweighted graph): largest hop spread of Y within a 256-node   */
                           /* chunk, seen from 8 sampled sources, times log2(1/gamma): the   */
@@ -127,15 +126,16 @@ rd_status rd_load(rd_handle h, const uint8_t* A, const float* W, double gamma);
 rd_status rd_set_stream(rd_handle h, void* stream);
 
 /* Select RD_PREC_FP64 or RD_PREC_SPLIT_BF16.  slices in [2, 15] fixes the digit count (no
- * self-check: the caller owns the precision); 0 lets the library choose per graph.  It first
- * screens the graph (unweighted graphs; one synchronisation): the digits of each 256-wide chunk
- * share one scale, so a chunk spanning S hops costs about S log2(1/gamma) bits; when 12 digits
- * (84 bits) cannot keep 34 bits beyond that it starts from 15, and when 15 cannot it computes in
- * FP64 (rd_stats.split_screen_bits).  It then checks every split result: 64 sampled rows of Y
- * must satisfy y^T M = e_g^T to a relative 1e-9 per entry (rd_stats.split_residual).  When the
- * check fails it recomputes the graph's inverse with 15 digits, then in FP64 (directly in FP64
- * when the residual is far off or the products also lost terms below their FP32 accumulators,
- * rd_stats.split_flags).  Drops cached factors when the mode changes. */
+ * screen, no self-check, the caller's node order: the caller owns the precision); 0 lets the
+ * library choose per graph.  It first screens the graph (unweighted graphs; a few
+ * synchronisations): the digits of each 256-wide chunk of the node order share one scale, so a
+ * chunk spanning S hops costs about S log2(1/gamma) bits.  When 12 digits (84 bits) cannot keep
+ * 34 bits beyond that, it tries its locality order (compact 64-node parts, 64-wide chunks:
+ * rd_stats.split_order), then 15 digits, then FP64 (rd_stats.split_screen_bits).  It then checks
+ * every split result: 64 sampled rows of Y must satisfy y^T M = e_g^T to a relative 1e-9 per
+ * entry (rd_stats.split_residual).  When the check fails it recomputes the graph's inverse with
+ * 15 digits, then in FP64 (directly in FP64 when the residual is beyond 1e-3).  Drops cached
+ * factors when the mode changes. */
 rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices);
 
 /* Change the decode snap tau (>= 0, < 0.5). */

@@ -16,8 +16,9 @@
 //     an integer of magnitude <= 2^12 and a group holds at most s <= 15 of them per K entry,
 //     so a chunk sum stays below 256 * 15 * 2^12 < 2^24: exact.
 //   * The epilogue warps read each group sum, scale it by 2^(eA + eB - 7 (g + 2)) relative to a
-//     per-row and per-column reference exponent, and add it into a float-float (two FP32)
-//     accumulator; FP64 is touched once per output entry at the end.
+//     per-entry reference exponent (the largest chunk scale eA + eB met so far; the accumulator
+//     is rebased by an exact power of two when it grows), and add it into a float-float (two
+//     FP32) accumulator; FP64 is touched once per output entry at the end.
 // The operands of every product of the inverse are sign-definite, so the accumulated value is
 // accurate relative to itself; the digit count s sets the precision.
 //
@@ -68,11 +69,11 @@ constexpr uint32_t IDESC = (1u << 4)               // D: FP32
                            | ((uint32_t)(TN >> 3) << 17)  // N
                            | ((uint32_t)(TM >> 4) << 24); // M  (A and B K-major)
 
-constexpr int RB_OFFSET = 2 * STAGES * TILE_BYTES + 256 + 2 * TN * 4;    // column reference exponents
-constexpr int LO_OFFSET = RB_OFFSET + TN * 4;                            // low words of the accumulators
-constexpr int FL_OFFSET = LO_OFFSET + TM * TN * 4;                        // flushed-term exponents (int8)
-constexpr int FLUSH_MARGIN = 48;  // a flushed term within 2^-48 of its final entry raises RD_FLAG_RANGE
-constexpr size_t SMEM_BYTES = 1024 + FL_OFFSET + TM * TN;
+constexpr int LO_OFFSET = 2 * STAGES * TILE_BYTES + 256 + 2 * TN * 4;  // low words of the accumulators
+constexpr int REF_OFFSET = LO_OFFSET + TM * TN * 4;                     // per-entry reference exponents
+constexpr int16_t REF_NONE = -32768;                                    // no chunk with digits yet
+constexpr size_t SMEM_BYTES = 1024 + REF_OFFSET + TM * TN * 2;
+static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
 
 // ---- PTX wrappers -----------------------------------------------------------------------
 
@@ -310,7 +311,7 @@ struct SplitArgs {
   long long ldd;
   int d_rows, d_cols;
   double log_gamma, tau;
-  int* status;       // [0] first error, [1] detail, [2] precision flags (RD_FLAG_RANGE)
+  int* status;       // [0] first error, [1] detail
   // stores of C, D (and Y) go to row row_map[row] and column col_map[col] (nullptr: the identity):
   // the products of a graph in the locality order write back in the caller's node order
   const int32_t* row_map;
@@ -332,9 +333,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   int* ecol_s = (int*)(smem + 2 * STAGES * TILE_BYTES + 256);  // [2][TN]
-  int* rb_s = (int*)(smem + RB_OFFSET);                          // [TN]
   float* lo_s = (float*)(smem + LO_OFFSET);                      // [TN][TM], column-major
-  int8_t* fl_s = (int8_t*)(smem + FL_OFFSET);                    // [TN][TM], column-major
+  int16_t* ref_s = (int16_t*)(smem + REF_OFFSET);                // [TN][TM], column-major
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int tiles_n = (p.N + TN - 1) / TN;
@@ -442,27 +442,21 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int half = ew >> 2;          // column half of the tile
     const int lrow = quarter * 32 + lane;
     const int row = m0 + lrow;
-    // reference exponents of this tile: largest chunk exponent of the row (column) over the chunks
-    // the tile visits, so every scaled group term is at most 2^-14
-    int ra = EXP_ZERO;
-    for (int c = 0; c < nloop; ++c) ra = max(ra, p.eA[(long long)(cbeg + c) * p.ma_pad + row]);
-    if (ew < 4) {
-      const int t = ew * 32 + lane;
-      int rb = EXP_ZERO;
-      for (int c = 0; c < nloop; ++c) rb = max(rb, p.eB[(long long)(cbeg + c) * p.nb_pad + n0 + t]);
-      rb_s[t] = rb;
-    }
-    asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
-    // float-float accumulators: high words in registers, low words in shared memory; per entry,
-    // the largest exponent (relative to the tile reference) of a term flushed below FP32's range
+    // float-float accumulators: high words in registers, low words in shared memory, both relative
+    // to a per-entry reference exponent (shared memory, int16) that follows the largest chunk scale
+    // eA[c][row] + eB[c][col] met so far.  When a chunk's scale exceeds it, the accumulator is
+    // rebased by that exact power of two, so every group term is at most 2^-14 of the reference,
+    // and an entry far below the rest of its tile (a Y spanning hundreds of binades) keeps its own
+    // scale.  A term more than 2^-126 below its entry's reference is dropped: the entry is at least
+    // its largest chunk's real contribution, which the chunk spread bounds far above that.
     float hi[64];
-    float* lo = lo_s + (half * 64) * TM + lrow;   // lo[j * TM]
-    int8_t* fl = fl_s + (half * 64) * TM + lrow;  // fl[j * TM]; -128 = nothing flushed
+    float* lo = lo_s + (half * 64) * TM + lrow;    // lo[j * TM]
+    int16_t* rf = ref_s + (half * 64) * TM + lrow;  // rf[j * TM]
 #pragma unroll
     for (int j = 0; j < 64; ++j) {
       hi[j] = 0.f;
       lo[j * TM] = 0.f;
-      fl[j * TM] = -128;
+      rf[j * TM] = REF_NONE;
     }
     int gi = 0;
     bool ok = true;
@@ -471,11 +465,26 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int cb = c & 1;
       if (ew < 4) {
         const int t = ew * 32 + lane;  // 0..127: one column each
-        ecol_s[cb * TN + t] = p.eB[(long long)kc * p.nb_pad + n0 + t] - rb_s[t];
+        ecol_s[cb * TN + t] = p.eB[(long long)kc * p.nb_pad + n0 + t];
       }
       asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
       if (!ok) continue;
-      const int erow = p.eA[(long long)kc * p.ma_pad + row] - ra;
+      const int erow = p.eA[(long long)kc * p.ma_pad + row];
+      if (erow != EXP_ZERO) {  // rebase the entries whose reference this chunk's scale exceeds
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          const int ec = ecol_s[cb * TN + half * 64 + j];
+          const int sc = erow + ec;
+          const int r = rf[j * TM];
+          if (ec != EXP_ZERO && sc > r) {
+            const int d = r - sc;
+            const float f = (d >= -126) ? __int_as_float((d + 127) << 23) : 0.f;
+            hi[j] *= f;
+            lo[j * TM] *= f;
+            rf[j * TM] = (int16_t)sc;
+          }
+        }
+      }
       for (int g = 0; g < s; ++g, ++gi) {
         const int buf = gi & 1;
         const uint32_t use = (uint32_t)(gi >> 1);
@@ -498,14 +507,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int jj = 0; jj < 16; ++jj) {
             const int j = t * 16 + jj;
             const float G = __uint_as_float(r[jj]);
-            const int x = base + ecol_s[cb * TN + half * 64 + j];
-            float sc = 0.f;
-            if (x >= -126 && x <= 0) {
-              sc = __int_as_float((x + 127) << 23);
-            } else if (G != 0.f) {
-              const int fe = max(-127, x + ((__float_as_int(G) >> 23) & 0xFF) - 127);
-              if (fe > fl[j * TM]) fl[j * TM] = (int8_t)fe;
-            }
+            // <= -14 for a chunk with digits; a chunk without (EXP_ZERO) has G == 0
+            const int x = base + ecol_s[cb * TN + half * 64 + j] - rf[j * TM];
+            const float sc = (x >= -126 && x <= 0) ? __int_as_float((x + 127) << 23) : 0.f;
             const float term = G * sc;
             const float sum = hi[j] + term;
             const float bp = sum - hi[j];
@@ -524,13 +528,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
     if (ok && !*abort_flag) {
-      bool lost = false;
 #pragma unroll
       for (int j = 0; j < 64; ++j) {
         const int col = n0 + half * 64 + j;
         if (row >= p.M || col >= p.N) continue;
-        const int ref = ra + rb_s[half * 64 + j];
-        double v = ldexp((double)hi[j] + (double)lo[j * TM], ref);
+        double v = ldexp((double)hi[j] + (double)lo[j * TM], (int)rf[j * TM]);
         v = p.alpha * v;
         const long long orow = p.row_map ? p.row_map[row] : row;
         const long long ocol = p.col_map ? p.col_map[col] : col;
@@ -538,11 +540,6 @@ __global__ void __launch_bounds__(THREADS, 1)
           double* cp = p.C + orow * p.ldc + ocol;
           if (p.beta != 0.0) v = fma(p.beta, *cp, v);
           if (p.store_c) *cp = v;
-        }
-        const int f = fl[j * TM];
-        if (f > -128) {  // something was flushed: does it matter next to the entry written?
-          const int ve = (v != 0.0) ? (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1023 : -4096;
-          lost |= (f + ref) > ve - FLUSH_MARGIN;
         }
         if (p.D && row < p.d_rows && col < p.d_cols) {
           int32_t d;
@@ -555,7 +552,6 @@ __global__ void __launch_bounds__(THREADS, 1)
           p.D[orow * p.ldd + ocol] = d;
         }
       }
-      if (lost && p.status) atomicOr(&p.status[2], RD_FLAG_RANGE);
     }
   }
   __syncthreads();

@@ -214,33 +214,18 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
   return RD_OK;
 }
 
-// The split path's self-check (RD_FLAG_RANGE in status word 2, see k_split.cu): read it
-// (synchronises) and clear it.
-rd_status read_split_flags(rd_ctx* h, int* flags) {
-  int st[4];
-  RD_CK(h, cudaMemcpyAsync(st, h->dStatus, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
-  RD_CK(h, cudaStreamSynchronize(h->stream));
-  *flags = st[2];
-  if (st[2]) RD_CK(h, cudaMemsetAsync(h->dStatus + 2, 0, sizeof(int), h->stream));
-  return RD_OK;
-}
-
 // Split mode with the self-check: after the inverse product, 64 sampled rows of Y (computed with
 // the same digit products) must satisfy y^T M = e_g^T to RD_SPLIT_RESIDUAL per entry.  When the
-// caller leaves the digit count open, the library starts from RD_SPLIT_START digits; a failed
-// check raises the floor of the current graph to RD_SPLIT_MAX digits, or moves it to FP64 when
-// the products also reported terms lost below their FP32 accumulators' range (RD_FLAG_RANGE:
-// more digits cannot recover those) or when RD_SPLIT_MAX digits already failed.  The inverse is
-// then recomputed from M.  RD_FLAG_RANGE alone is not a failure: the LU's Schur updates lose
-// fill-in terms far below the entries they update without harming Y.
+// caller leaves the digit count open, the library starts where the range screen says; a failed
+// check raises the floor of the current graph to RD_SPLIT_MAX digits, or moves it to FP64 when the
+// residual is far beyond what three more digits (21 bits) could close or RD_SPLIT_MAX digits
+// already failed.  The inverse is then recomputed from M.
 bool split_auto(const rd_ctx* h) { return h->precision == RD_PREC_SPLIT_BF16 && h->slices_req == 0; }
 
-// range: a term left the FP32 accumulators' range -- more digits cannot help, go to FP64;
-// otherwise (the sampled rows' residual failed) try RD_SPLIT_MAX digits first.
-rd_status escalate(rd_ctx* h, bool range) {
+// hopeless: more digits cannot close the gap, go to FP64; otherwise try RD_SPLIT_MAX digits first.
+rd_status escalate(rd_ctx* h, bool hopeless) {
   h->fallbacks++;
-  h->split_floor = (!range && h->slices < RD_SPLIT_MAX) ? RD_SPLIT_MAX : -1;
-  RD_CK(h, cudaMemsetAsync(h->dStatus + 2, 0, sizeof(int), h->stream));
+  h->split_floor = (!hopeless && h->slices < RD_SPLIT_MAX) ? RD_SPLIT_MAX : -1;
   RD_CK(h, rd_build_m(h, h->stream));  // M again (the factorisation overwrote it)
   h->factored = h->inverted = 0;
   return RD_OK;
@@ -501,13 +486,10 @@ rd_status rd_apsp(rd_handle h, int32_t* D, double* Y) {
       double worst = 0.0;  // residual of sampled rows of Y against M
       RD_CK(h, rd_split_row_check(h, &worst, h->stream));
       h->last_residual = worst;
-      int flags = 0;
-      if ((st = read_split_flags(h, &flags)) != RD_OK) return st;
-      h->last_flags = flags;
       if (worst <= RD_SPLIT_RESIDUAL) break;
-      // the result failed: with terms lost below the accumulators' range, or a residual far
-      // beyond what three more digits (21 bits) could close, go straight to FP64
-      if ((st = escalate(h, (flags & RD_FLAG_RANGE) != 0 || worst > 1e-3)) != RD_OK) return st;
+      // the result failed: with a residual far beyond what three more digits (21 bits) could
+      // close, go straight to FP64
+      if ((st = escalate(h, worst > 1e-3)) != RD_OK) return st;
       if ((st = ensure_factored(h)) != RD_OK) return st;
       continue;
     }
@@ -597,7 +579,6 @@ rd_status rd_get_stats(rd_handle h, rd_stats* s) {
   s->precision_used = h->used_precision;
   s->fallbacks = h->fallbacks;
   s->split_residual = h->last_residual;
-  s->split_flags = h->last_flags;
   s->split_screen_bits = h->screen_bits;
   s->split_order = h->ordered;
   s->gamma = h->gamma;

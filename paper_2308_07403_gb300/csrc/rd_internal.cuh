@@ -27,8 +27,6 @@
 #define RD_DEV_PIVOT 1      // non-positive or non-finite pivot
 #define RD_DEV_NONFINITE 2  // non-finite entry of Y
 #define RD_DEV_TIMEOUT 3    // a bounded wait expired
-// precision flags, OR-ed into status word [2] (not errors: the split path's self-check)
-#define RD_FLAG_RANGE 1     // a digit-product term fell out of the FP32 accumulator range
 #define RD_SPLIT_START 12   // digit count the split mode starts from when the caller leaves it open
 #define RD_SPLIT_MAX 15     // largest digit count (exact group sums)
 #define RD_SPLIT_DIGIT_BITS 7  // bits per digit of the split operands
@@ -54,7 +52,7 @@ struct rd_ctx {
   double* dT = nullptr;
   double* dS = nullptr;
   double* dR = nullptr;
-  int* dStatus = nullptr;      // [0] code, [1] detail, [2] precision flags, [3] spare
+  int* dStatus = nullptr;      // [0] code, [1] detail, [2..3] spare
   unsigned long long* dRed = nullptr;  // reductions: [0] max degree, [1] max column sum bits
   int32_t* dDeg = nullptr;     // n+1: out-degree, then exclusive prefix (successor CSR ptr)
   double* dColsum = nullptr;   // n: column sums of X (gain check)
@@ -79,7 +77,6 @@ struct rd_ctx {
   int kappa = 256;             // chunk width of the split digits: 256, or 64 with the locality order
   int fallbacks = 0;           // split results redone (more digits or FP64) after the self-check
   double last_residual = 0.0;  // largest sampled-row residual of the last split result
-  int last_flags = 0;          // precision flags raised while computing it
 
   rd_split_plan* split = nullptr;
 

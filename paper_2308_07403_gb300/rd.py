@@ -62,7 +62,7 @@ class rd_stats(ctypes.Structure):
         ("ms_goal", ctypes.c_double), ("ms_greedy", ctypes.c_double), ("bytes_device", ctypes.c_int64),
         ("launches", ctypes.c_int64), ("prof_launches", ctypes.c_int64), ("prof_ms", ctypes.c_double),
         ("prof_flops", ctypes.c_double), ("precision_used", ctypes.c_int32), ("fallbacks", ctypes.c_int32),
-        ("split_residual", ctypes.c_double), ("split_flags", ctypes.c_int32),
+        ("split_residual", ctypes.c_double),
         ("split_screen_bits", ctypes.c_double),
         ("prof_split_launches", ctypes.c_int64), ("prof_split_ms", ctypes.c_double),
         ("prof_split_flops", ctypes.c_double),
