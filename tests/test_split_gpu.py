@@ -227,7 +227,8 @@ def test_locality_order_path(rd):
 def test_split_full_size_D_identical(rd, kind, frac):
     """n = 8192: the D of the split mode hashes to the oracle's D.  ER and WS stay on the split
     path in their own node order; the 90 x 91 grid (a 256-node run of its natural order spans ~84
-    hops of Y) runs on the split path in the locality order, whose 64-node parts span ~17 hops."""
+    hops of Y, and Y itself spans 2^-540) runs on the split path in the locality order, whose
+    64-node parts span ~17 hops, with per-entry reference exponents in the accumulators."""
     p = os.path.join(HERE, "golden", f"large_{kind}_{frac}.json")
     if not os.path.exists(p):
         pytest.skip("golden file missing")
