@@ -129,9 +129,11 @@ rd_status rd_set_stream(rd_handle h, void* stream);
  * screen, no self-check, the caller's node order: the caller owns the precision); 0 lets the
  * library choose per graph.  It first screens the graph (unweighted graphs; a few
  * synchronisations): the digits of each 256-wide chunk of the node order share one scale, so a
- * chunk spanning S hops costs about S log2(1/gamma) bits.  When 12 digits (84 bits) cannot keep
- * 34 bits beyond that, it tries its locality order (compact 64-node parts, 64-wide chunks:
- * rd_stats.split_order), then 15 digits, then FP64 (rd_stats.split_screen_bits).  It then checks
+ * chunk spanning S hops costs about S log2(1/gamma) bits, and the digit count is the fewest
+ * (at least 8) whose 7 bits each cover that plus 40 bits of result.  When the node order needs
+ * more than 12, it also screens its locality order (compact 64-node parts, 64-wide chunks:
+ * rd_stats.split_order) and takes it when it needs fewer; beyond 15 digits the graph runs in
+ * FP64 (rd_stats.split_screen_bits, rd_stats.slices).  Weighted graphs start at 12.  It then checks
  * every split result: 64 sampled rows of Y must satisfy y^T M = e_g^T to a relative 1e-9 per
  * entry (rd_stats.split_residual).  When the check fails it recomputes the graph's inverse with
  * 15 digits, then in FP64 (directly in FP64 when the residual is beyond 1e-3).  Drops cached

@@ -52,7 +52,7 @@ constexpr int SIGMA = 7;          // bits per digit (balanced base 2^SIGMA)
 constexpr int KAPPA_WIDE = 256;   // exponent / read-out chunk along K (natural order)
 constexpr int KAPPA_NARROW = 64;  // the same with the locality order (compact 64-node parts)
 constexpr int TM = 128, TN = 128, TK = 64;
-constexpr int STAGES = 2;          // ring stages; each holds ITEMS (A, B) tile pairs of one digit group
+constexpr int STAGES = 3;          // ring stages; each holds ITEMS (A, B) tile pairs of one digit group
 constexpr int ITEMS = 2;           // (pair, K step) items per stage: 8 MMAs per wait of the MMA thread
 constexpr int SLOTS = STAGES * ITEMS;  // 16 KiB tile slots per operand
 constexpr int EPI_WARPS = 8;
@@ -71,10 +71,14 @@ constexpr uint32_t IDESC = (1u << 4)               // D: FP32
                            | ((uint32_t)(TN >> 3) << 17)  // N
                            | ((uint32_t)(TM >> 4) << 24); // M  (A and B K-major)
 
-constexpr int LO_OFFSET = 2 * SLOTS * TILE_BYTES + 256 + 2 * TN * 4;  // low words of the accumulators
-constexpr int REF_OFFSET = LO_OFFSET + TM * TN * 4;                     // per-entry reference exponents
+constexpr int REF_OFFSET = 2 * SLOTS * TILE_BYTES + 256 + 2 * TN * 4;  // per-entry reference exponents
 constexpr int16_t REF_NONE = -32768;                                    // no chunk with digits yet
 constexpr size_t SMEM_BYTES = 1024 + REF_OFFSET + TM * TN * 2;
+// tensor memory: two accumulator buffers, the low words of the float-float accumulators, and the
+// per-entry scale of the current chunk (one 32-bit column per tile column each)
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TMEM_LO = 2 * TN;
+constexpr uint32_t TMEM_SCALE = 3 * TN;
 static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
 
 // ---- PTX wrappers -----------------------------------------------------------------------
@@ -176,14 +180,28 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// tcgen05.ld of 8 columns without the wait; tmem_wait_ld(r) then waits for every prior load of this
+// thread and ties r to the wait, so no use of r is scheduled before it
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
+}
+
+// store 8 columns of this warp's 32 lanes, then wait for it (registers and columns are free
+// to reuse after the call)
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // ---- slicing --------------------------------------------------------------------------------
@@ -325,6 +343,7 @@ struct SplitArgs {
   long long ldd;
   int d_rows, d_cols;
   double log_gamma, tau;
+  float inv_log2_gamma;  // 1 / log2(gamma) for the decode's FP32 fast path
   int* status;       // [0] first error, [1] detail
   // stores of C, D (and Y) go to row row_map[row] and column col_map[col] (nullptr: the identity):
   // the products of a graph in the locality order write back in the caller's node order
@@ -347,7 +366,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   int* ecol_s = (int*)(smem + 2 * SLOTS * TILE_BYTES + 256);   // [2][TN]
-  float* lo_s = (float*)(smem + LO_OFFSET);                      // [TN][TM], column-major
   int16_t* ref_s = (int16_t*)(smem + REF_OFFSET);                // [TN][TM], column-major
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -379,7 +397,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * TN));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -465,20 +483,28 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int half = ew >> 2;          // column half of the tile
     const int lrow = quarter * 32 + lane;
     const int row = m0 + lrow;
-    // float-float accumulators: high words in registers, low words in shared memory, both relative
+    // float-float accumulators: high words in registers, low words in tensor memory, both relative
     // to a per-entry reference exponent (shared memory, int16) that follows the largest chunk scale
     // eA[c][row] + eB[c][col] met so far.  When a chunk's scale exceeds it, the accumulator is
     // rebased by that exact power of two, so every group term is at most 2^-14 of the reference,
     // and an entry far below the rest of its tile (a Y spanning hundreds of binades) keeps its own
-    // scale.  A term more than 2^-126 below its entry's reference is dropped: the entry is at least
-    // its largest chunk's real contribution, which the chunk spread bounds far above that.
+    // scale.  A term more than 2^-126 below its entry's reference underflows: the entry is at least
+    // its largest chunk's real contribution, which the chunk spread bounds far above that.  Each
+    // chunk's scale relative to the reference, S = 2^(eA + eB - ref), is kept in tensor memory, so
+    // a group term is G 2^(-7 (g + 2)) S.
     float hi[64];
-    float* lo = lo_s + (half * 64) * TM + lrow;    // lo[j * TM]
     int16_t* rf = ref_s + (half * 64) * TM + lrow;  // rf[j * TM]
+    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);  // this warp's lanes
+    {
+      uint32_t z[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) z[q] = 0u;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) tmem_st8(tl + TMEM_LO + t * 8, z);
+    }
 #pragma unroll
     for (int j = 0; j < 64; ++j) {
       hi[j] = 0.f;
-      lo[j * TM] = 0.f;
       rf[j * TM] = REF_NONE;
     }
     int gi = 0;
@@ -493,69 +519,92 @@ __global__ void __launch_bounds__(THREADS, 1)
       asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
       if (!ok) continue;
       const int erow = p.eA[(long long)kc * p.ma_pad + row];
-      if (erow != EXP_ZERO) {  // rebase the entries whose reference this chunk's scale exceeds
+      // renormalise the previous chunk's sums, rebase where this chunk's scale exceeds the
+      // reference, and set this chunk's per-entry scale
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
+      for (int t = 0; t < 8; ++t) {
+        uint32_t lr[8], sr[8];
+        tmem_ld8_async(tl + TMEM_LO + t * 8, lr);
+        tmem_wait_ld(lr);
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = t * 8 + jj;
+          float l = __uint_as_float(lr[jj]);
+          const float sum = hi[j] + l;
+          l = l - (sum - hi[j]);
+          hi[j] = sum;
           const int ec = ecol_s[cb * TN + half * 64 + j];
+          const bool live = (erow != EXP_ZERO) && (ec != EXP_ZERO);
           const int sc = erow + ec;
-          const int r = rf[j * TM];
-          if (ec != EXP_ZERO && sc > r) {
+          int r = rf[j * TM];
+          if (live && sc > r) {
             const int d = r - sc;
             const float f = (d >= -126) ? __int_as_float((d + 127) << 23) : 0.f;
             hi[j] *= f;
-            lo[j * TM] *= f;
+            l *= f;
+            r = sc;
             rf[j * TM] = (int16_t)sc;
           }
+          const int d = sc - r;  // <= 0 for a live chunk
+          sr[jj] = (live && d >= -126) ? (uint32_t)((d + 127) << 23) : 0u;
+          lr[jj] = __float_as_uint(l);
         }
+        tmem_st8(tl + TMEM_LO + t * 8, lr);
+        tmem_st8(tl + TMEM_SCALE + t * 8, sr);
       }
       for (int g = 0; g < s; ++g, ++gi) {
         const int buf = gi & 1;
         const uint32_t use = (uint32_t)(gi >> 1);
-        if (!mbar_wait(&acc_full[buf], use & 1u, abort_flag, deadline)) {
+        // warp-uniform outcome: the tensor-memory loads below are warp-wide
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], use & 1u, abort_flag, deadline))) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const int base = erow - SIGMA * (g + 2);
+        const float cg = __int_as_float((127 - SIGMA * (g + 2)) << 23);  // 2^(-7 (g + 2))
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * TN + half * 64 + t * 16), r);
-          if (t == 3) {  // all four reads done: hand the buffer back to the MMA warp
+        for (int t = 0; t < 8; ++t) {  // 8 columns at a time
+          uint32_t gr[8], sr[8], lr[8];
+          tmem_ld8_async(tl + (uint32_t)(buf * TN) + t * 8, gr);
+          tmem_ld8_async(tl + TMEM_SCALE + t * 8, sr);
+          tmem_ld8_async(tl + TMEM_LO + t * 8, lr);
+          tmem_wait_ld(gr);
+          tmem_wait_ld(sr);
+          tmem_wait_ld(lr);
+          if (t == 7) {  // all reads of the accumulator done: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
           }
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int j = t * 16 + jj;
-            const float G = __uint_as_float(r[jj]);
-            // <= -14 for a chunk with digits; a chunk without (EXP_ZERO) has G == 0
-            const int x = base + ecol_s[cb * TN + half * 64 + j] - rf[j * TM];
-            const float sc = (x >= -126 && x <= 0) ? __int_as_float((x + 127) << 23) : 0.f;
-            const float term = G * sc;
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = t * 8 + jj;
+            const float term = (__uint_as_float(gr[jj]) * cg) * __uint_as_float(sr[jj]);
             const float sum = hi[j] + term;
             const float bp = sum - hi[j];
             const float err = (hi[j] - (sum - bp)) + (term - bp);
             hi[j] = sum;
-            lo[j * TM] += err;
+            lr[jj] = __float_as_uint(__uint_as_float(lr[jj]) + err);
           }
+          tmem_st8(tl + TMEM_LO + t * 8, lr);
         }
       }
-#pragma unroll
-      for (int j = 0; j < 64; ++j) {  // renormalise once per chunk
-        const float l = lo[j * TM];
-        const float sum = hi[j] + l;
-        lo[j * TM] = l - (sum - hi[j]);
-        hi[j] = sum;
-      }
     }
-    if (ok && !*abort_flag) {
+    // final values, 16 columns at a time (the tensor-memory loads are warp-wide: outside any
+    // per-lane condition)
+    const bool store = ok && !*abort_flag;
 #pragma unroll
-      for (int j = 0; j < 64; ++j) {
+    for (int t = 0; t < 8; ++t) {
+      uint32_t lr[8];
+      tmem_ld8_async(tl + TMEM_LO + t * 8, lr);
+      tmem_wait_ld(lr);
+      if (!store) continue;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = t * 8 + jj;
         const int col = n0 + half * 64 + j;
         if (row >= p.M || col >= p.N) continue;
-        double v = ldexp((double)hi[j] + (double)lo[j * TM], (int)rf[j * TM]);
+        double v = ldexp((double)hi[j] + (double)__uint_as_float(lr[jj]), (int)rf[j * TM]);
         v = p.alpha * v;
         const long long orow = p.row_map ? p.row_map[row] : row;
         const long long ocol = p.col_map ? p.col_map[col] : col;
@@ -570,7 +619,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             rd_set_status(p.status, RD_DEV_NONFINITE, (int)orow);
             d = RD_UNREACHABLE;
           } else {
-            d = (row == col) ? 0 : rd_decode_entry(v, p.log_gamma, p.tau);
+            d = (row == col) ? 0 : rd_decode_entry_fast(v, p.inv_log2_gamma, p.log_gamma, p.tau);
           }
           p.D[orow * p.ldd + ocol] = d;
         }
@@ -582,7 +631,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   // (the status word is only read at the start of a CTA: a stale value merely skips work)
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
 }
 
@@ -755,6 +804,7 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   a.d_rows = D ? h->n : 0;
   a.d_cols = D ? h->n : 0;
   a.log_gamma = log(h->gamma);
+  a.inv_log2_gamma = (float)(1.0 / log2(h->gamma));
   a.tau = h->tau;
   a.status = h->dStatus;
   a.row_map = row_map;

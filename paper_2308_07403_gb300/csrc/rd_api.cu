@@ -120,6 +120,7 @@ rd_status load_impl(rd_ctx* h, const uint8_t* A, const float* W, double gamma) {
   h->gamma = gamma;
   h->factored = h->inverted = 0;
   h->split_floor = 0;
+  h->split_start = 0;
   h->screened = 0;
   h->screen_bits = -1.0;
   h->ordered = 0;
@@ -236,14 +237,13 @@ rd_status escalate(rd_ctx* h, bool hopeless) {
 // chunk's largest entry, and the entries of Y fall by log2(1/gamma) bits per hop (Y_ij ~ gamma^d
 // for distance d), so a chunk whose nodes lie S hops apart as seen from one node costs about
 // S log2(1/gamma) of the 7 s bits the digits carry.  The largest S over the chunks, seen from 8
-// sampled sources, decides where the attempt starts; a configuration fits when its digits cover
-// the spread plus RD_SCREEN_RESULT_BITS bits of result.  In order of preference:
-//   natural node order, 256-wide chunks, RD_SPLIT_START digits;
-//   the locality order (compact 64-node parts, see bisect_kernel), 64-wide chunks, RD_SPLIT_START;
-//   natural order, RD_SPLIT_MAX digits;  the locality order, RD_SPLIT_MAX digits;  FP64.
-// Large-diameter graphs (grids, meshes) are the ones that need the locality order: a 256-node run
-// of their natural order spans a whole row of the mesh.  The screen only steers: the residual
-// self-check still judges every split result.
+// sampled sources, sets the digit count: the fewest (at least RD_SPLIT_MIN) whose 7 s bits cover
+// the spread plus RD_SCREEN_RESULT_BITS bits of result.  When the natural node order (256-wide
+// chunks) needs more than RD_SPLIT_START digits, the locality order (compact 64-node parts, see
+// rcb_kernel, 64-wide chunks) is screened too and taken when it needs fewer digits; beyond
+// RD_SPLIT_MAX digits the graph runs in FP64.  Large-diameter graphs (grids, meshes) are the ones
+// that need the locality order: a 256-node run of their natural order spans a whole row of the
+// mesh.  The screen only steers: the residual self-check still judges every split result.
 double spread_bits(rd_ctx* h, const int32_t* ord, int chunk, rd_status* st) {
   *st = RD_OK;
   cudaError_t e = cudaMemsetAsync(h->dRed, 0, sizeof(unsigned long long), h->stream);
@@ -269,23 +269,30 @@ rd_status screen_split(rd_ctx* h) {
     RD_CK(h, rd_build_succ(h, h->stream));
     h->succ_ready = 1;
   }
-  const double r = RD_SCREEN_RESULT_BITS, start = (double)RD_SPLIT_DIGIT_BITS * RD_SPLIT_START,
-               most = (double)RD_SPLIT_DIGIT_BITS * RD_SPLIT_MAX;
+  auto digits_for = [](double bits) {
+    const int s = (int)std::ceil((bits + RD_SCREEN_RESULT_BITS) / RD_SPLIT_DIGIT_BITS);
+    return s < RD_SPLIT_MIN ? RD_SPLIT_MIN : s;
+  };
   rd_status st;
   const double nat = spread_bits(h, nullptr, RD_SCREEN_CHUNK, &st);
   if (st != RD_OK) return st;
   h->screen_bits = nat;
-  if (nat + r <= start) return RD_OK;
+  const int s_nat = digits_for(nat);
+  if (s_nat <= RD_SPLIT_START) {
+    h->split_start = s_nat;
+    return RD_OK;
+  }
   RD_CK(h, rd_locality_order(h, h->stream));
   const double ord = spread_bits(h, h->dOrd, RD_SCREEN_CHUNK_ORDERED, &st);
   if (st != RD_OK) return st;
-  if (ord + r <= start || (nat + r > most && ord + r <= most)) {
+  const int s_ord = digits_for(ord);
+  if (s_ord < s_nat && s_ord <= RD_SPLIT_MAX) {
     h->ordered = 1;
     h->kappa = RD_SCREEN_CHUNK_ORDERED;
     h->screen_bits = ord;
-    if (ord + r > start) h->split_floor = RD_SPLIT_MAX;
-  } else if (nat + r <= most) {
-    h->split_floor = RD_SPLIT_MAX;
+    h->split_start = s_ord;
+  } else if (s_nat <= RD_SPLIT_MAX) {
+    h->split_start = s_nat;
   } else {
     h->split_floor = -1;
   }
@@ -310,7 +317,7 @@ rd_status ensure_factored(rd_ctx* h) {
       h->inverted = 0;
       break;
     }
-    int s = h->slices_req > 0 ? h->slices_req : RD_SPLIT_START;
+    int s = h->slices_req > 0 ? h->slices_req : (h->split_start > 0 ? h->split_start : RD_SPLIT_START);
     if (h->split_floor > s) s = h->split_floor;
     rd_status st = rd_split_prepare(h, s);
     if (st != RD_OK) return st;
@@ -440,6 +447,7 @@ rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices) {
   if (slices < 0 || slices > 15 || slices == 1) return fail(h, RD_ERR_ARG, "slices must be 0 or lie in [2, 15]");
   if (mode != h->precision || slices != h->slices_req) {
     h->split_floor = 0;
+    h->split_start = 0;
     h->screened = 0;
     h->screen_bits = -1.0;
     h->ordered = 0;

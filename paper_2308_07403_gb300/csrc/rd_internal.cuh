@@ -27,13 +27,14 @@
 #define RD_DEV_PIVOT 1      // non-positive or non-finite pivot
 #define RD_DEV_NONFINITE 2  // non-finite entry of Y
 #define RD_DEV_TIMEOUT 3    // a bounded wait expired
-#define RD_SPLIT_START 12   // digit count the split mode starts from when the caller leaves it open
+#define RD_SPLIT_START 12   // digit count of an unscreened graph (weighted) when the caller leaves it open
+#define RD_SPLIT_MIN 8      // fewest digits the range screen picks
 #define RD_SPLIT_MAX 15     // largest digit count (exact group sums)
 #define RD_SPLIT_DIGIT_BITS 7  // bits per digit of the split operands
 #define RD_SCREEN_SOURCES 8  // BFS sources of the split path's range screen
 #define RD_SCREEN_CHUNK 256  // operand chunk along K that shares one scale (the split path's KAPPA)
 #define RD_SCREEN_CHUNK_ORDERED 64  // the same with the locality order
-#define RD_SCREEN_RESULT_BITS 34  // bits the digits must keep below a chunk's spread (2^-34 ~ 6e-11)
+#define RD_SCREEN_RESULT_BITS 40  // bits the digits must keep below a chunk's spread (2^-40 ~ 1e-12)
 
 struct rd_split_plan;       // defined by the split path
 
@@ -71,6 +72,7 @@ struct rd_ctx {
   int inverted = 0;            // dT holds the triangular inverses
   int used_precision = RD_PREC_FP64;  // precision that produced the current factors
   int split_floor = 0;         // per graph: least digit count to use, -1 = FP64 (self-check history)
+  int split_start = 0;         // per graph: digit count picked by the range screen (0: none)
   int screened = 0;            // the range screen ran for the current graph and mode
   double screen_bits = -1.0;   // its estimate of the bits a chunk's spread costs (-1: not screened)
   int ordered = 0;             // the split path runs on P M P^T with the locality order (dOrd)
@@ -190,6 +192,28 @@ __device__ __forceinline__ int32_t rd_decode_entry(double y, double log_gamma, d
   if (c >= 2147483646.0) return RD_UNREACHABLE - 1;
   if (c <= -2147483647.0) return -2147483647;
   return (int32_t)c;
+}
+
+// The same decode with an FP32 fast path.  For a normal y = 2^e m (m in [1, 2)),
+// R = (e + log2 m) / log2(gamma) is formed in FP32; its error is at most 2e-4 |1/log2 gamma|
+// (the FP32 sum e + log2 m, |e| <= 1074, carries 2^-13; log2f and the 23-bit mantissa add
+// < 1e-6) plus 2e-6 |R| (the product and the rounded 1/log2 gamma).  When R lies farther than
+// that from every integer, its ceiling is the exact one (tau = 1e-9 is far inside the bound);
+// otherwise, and for R beyond 2^22 where FP32 holds no fraction, the FP64 formula decides.
+__device__ __forceinline__ int32_t rd_decode_entry_fast(double y, float inv_log2_gamma, double log_gamma,
+                                                        double tau) {
+  if (y > 0.0) {
+    const long long b = __double_as_longlong(y);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex != 0 && ex != 0x7FF) {
+      const float m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7FFFFF));
+      const float r = ((float)(ex - 1023) + log2f(m)) * inv_log2_gamma;
+      const float fr = r - floorf(r);
+      const float tol = 2e-4f * fabsf(inv_log2_gamma) + 2e-6f * fabsf(r) + 1e-6f;
+      if (fabsf(r) < 4194304.f && fr > tol && fr < 1.f - tol) return (int32_t)ceilf(r);
+    }
+  }
+  return rd_decode_entry(y, log_gamma, tau);
 }
 
 __device__ __forceinline__ void rd_set_status(int* status, int code, int detail) {

@@ -172,30 +172,39 @@ SCREEN_CASES = {  # (graph, gain): the branch follows from spread x log2(1/gamma
 }
 
 
+def screen_digits(bits):
+    """The screen's digit count: the fewest (at least 8) whose 7 bits each cover the spread's bits
+    plus 40 bits of result."""
+    return max(8, int(np.ceil((bits + 40) / 7)))
+
+
 @pytest.mark.parametrize("name", list(SCREEN_CASES))
 def test_range_screen_matches_bfs(rd, name):
     """The screen's hop spread equals the one computed from the oracle's BFS (integer work: exact),
-    the digit count or FP64 follows from it as documented, and D is exact on every branch."""
+    the digit count, the node order or FP64 follow from it as documented, and D is exact on every
+    branch."""
     A, g = SCREEN_CASES[name]()
     if g is None:
         g = graphs.gamma_frac(A, 0.9)
     spread = screen_spread(A)
     bits = spread * np.log2(1.0 / g)
     Dg, _, st = run(rd, A, g, want_y=False)
-    if bits + 34 <= 7 * 12 or st["split_order"] == 0:
-        # natural order: the screen's estimate is the BFS spread of 256-node runs, exactly
+    if screen_digits(bits) <= 12:
+        # the natural order suffices: the estimate is the BFS spread of 256-node runs, exactly
         assert st["split_order"] == 0
         assert st["split_screen_bits"] == pytest.approx(bits, rel=1e-12, abs=0.0)
-        used = bits
+        want = screen_digits(bits)
+    elif st["split_order"] == 1:
+        # the locality order was taken: it must need fewer digits than the natural order
+        assert screen_digits(st["split_screen_bits"]) < screen_digits(bits)
+        want = screen_digits(st["split_screen_bits"])
     else:
-        # the locality order was taken: it must have screened better than the natural order
-        assert st["split_screen_bits"] < bits
-        used = st["split_screen_bits"]
-    if used + 34 > 7 * 15:
+        assert st["split_screen_bits"] == pytest.approx(bits, rel=1e-12, abs=0.0)
+        want = screen_digits(bits)
+    if want > 15:
         assert st["precision_used"] == rd.RD_PREC_FP64 and st["fallbacks"] == 0
     elif st["fallbacks"] == 0:
-        assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16
-        assert st["slices"] == (15 if used + 34 > 7 * 12 else 12)
+        assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16 and st["slices"] == want
     assert np.array_equal(Dg, oracle.rdistance(A, g)), name
 
 
