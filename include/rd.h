@@ -210,6 +210,39 @@ void rd_destroy(rd_handle h);
  * caller.  Errors are readable with rd_last_error(NULL). */
 rd_status rd_apsp_noalloc(const uint8_t* A, int32_t n, double gamma, int32_t* D, void* stream);
 
+/* ---- Batched graphs (many small independent problems in one launch) -------------------------
+ * The whole method (M = I - gamma A, Y = M^-1, D = ceil(log_gamma Y - tau) with D_ii = 0, the
+ * sentinel for Y <= 0; Sec. 2 and Sec. 4.1) for G independent graphs of at most RD_BATCH_MAX_N
+ * nodes each, in FP64, in one persistent kernel launch: each CTA takes the next graph (largest
+ * first) from a queue and inverts its M by blocked Gauss-Jordan elimination without pivoting.  The
+ * paper treats one graph at a time; batching is a deployment variant of the same computation. */
+#define RD_BATCH_MAX_N 512
+
+typedef struct rd_batch* rd_batch_handle;
+
+/* Plan a batch: n (G node counts, each in [1, RD_BATCH_MAX_N]) and gamma (G gains) are host
+ * arrays; graph g's adjacency matrix (n_g x n_g bytes, A[i*n_g+j] != 0 iff edge j -> i) and its D
+ * (n_g x n_g int32, D[i*n_g+j] = distance j -> i) are packed at element offset off[g] of the
+ * caller's buffers, off[0] = 0, off[g+1] = off[g] + n_g^2 (rd_batch_offsets).  Allocates the FP64
+ * workspace (8 sum n_g^2 bytes) on the current device.  Synchronises. */
+rd_status rd_batch_create(const int32_t* n, const double* gamma, int32_t G, rd_batch_handle* out);
+
+/* The G + 1 packing offsets (host array). */
+rd_status rd_batch_offsets(rd_batch_handle b, int64_t* off);
+
+/* Run the batch: A (packed uint8) and D (packed int32) are device memory of the batch's device; the
+ * work is one memset and one kernel launch on `stream` (a cudaStream_t; NULL = default stream),
+ * asynchronous and capturable in a CUDA graph.  Per-graph outcomes: rd_batch_status. */
+rd_status rd_batch_apsp(rd_batch_handle b, const uint8_t* A, int32_t* D, void* stream);
+
+/* Per-graph status of the last run (host array of G): RD_OK, RD_ERR_GAMMA (gamma outside (0,1) or
+ * a column sum of gamma A >= 1: not computed, D untouched), RD_ERR_NUMERIC (non-positive pivot or
+ * non-finite Y).  Synchronises the device. */
+rd_status rd_batch_status(rd_batch_handle b, int32_t* status);
+
+/* Free a batch (NULL is ignored). */
+void rd_batch_destroy(rd_batch_handle b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -228,3 +228,32 @@ def workload_large(kind: str, frac: float, n: int = 8192, replica: int = 0):
     else:
         raise ValueError(kind)
     return A, gamma_frac(A, frac)
+
+
+BATCH_KINDS = ("er", "grid", "ws")
+
+
+def workload_batched(G: int = 4096, n_lo: int = 32, n_hi: int = 512, replica: int = 0):
+    """The batched workload: G independent graphs, n uniform in [n_lo, n_hi], the kind uniform over
+    ER (p = 4/n), a 4-neighbour grid with ceil(sqrt n) columns and Watts-Strogatz (k = min(10,
+    n - 1 rounded down to even), beta = 0.1); gain 0.5 / (Delta + 1) per graph.  Returns the lists
+    (kinds, n, A, gamma); graph g draws its own seed from the batch's generator."""
+    rng = np.random.default_rng(seed_for(2, replica))
+    kinds, ns, As, gs = [], [], [], []
+    for _ in range(G):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        kind = BATCH_KINDS[int(rng.integers(len(BATCH_KINDS)))]
+        s = int(rng.integers(2**31 - 1))
+        if kind == "er":
+            A = er(n, 4.0 / n, s)
+        elif kind == "grid":
+            A = grid4(n, int(np.ceil(np.sqrt(n))))
+        else:
+            k = min(10, n - 1)
+            k -= k % 2
+            A = ws(n, k, 0.1, s)
+        kinds.append(kind)
+        ns.append(n)
+        As.append(A)
+        gs.append(gamma_small(A))
+    return kinds, np.array(ns, dtype=np.int32), As, np.array(gs, dtype=np.float64)

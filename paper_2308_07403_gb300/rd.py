@@ -31,6 +31,7 @@ RD_PREC_SPLIT_BF16 = 1
 RD_UNREACHABLE = 2**31 - 1
 MAX_GOALS = 64
 NOALLOC_MAX_N = 512
+BATCH_MAX_N = 512
 
 # every symbol declared in include/rd.h, with its ctypes signature
 _P = ctypes.c_void_p
@@ -51,6 +52,11 @@ _SIGS = {
     "rd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rd_destroy": (None, [_P]),
     "rd_apsp_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, _P, _P]),
+    "rd_batch_create": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "rd_batch_offsets": (ctypes.c_int, [_P, _P]),
+    "rd_batch_apsp": (ctypes.c_int, [_P, _P, _P, _P]),
+    "rd_batch_status": (ctypes.c_int, [_P, _P]),
+    "rd_batch_destroy": (None, [_P]),
 }
 
 
@@ -257,6 +263,57 @@ class Handle:
     def close(self):
         if self.h:
             rd_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns one rd_batch_handle: G graphs of at most BATCH_MAX_N nodes, solved in one launch.
+
+    n and gamma are host sequences; offsets() gives the packing of A (uint8) and D (int32):
+    graph g occupies elements [off[g], off[g + 1]) = n_g * n_g entries, row-major."""
+
+    def __init__(self, n, gamma):
+        n = np.ascontiguousarray(n, dtype=np.int32)
+        gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+        if n.shape != gamma.shape:
+            raise ValueError("n and gamma must have the same length")
+        self.G = int(n.size)
+        h = ctypes.c_void_p()
+        _check(load().rd_batch_create(n.ctypes.data_as(_P), gamma.ctypes.data_as(_P), self.G, ctypes.byref(h)))
+        self.h = h
+
+    def offsets(self):
+        off = np.empty(self.G + 1, dtype=np.int64)
+        _check(load().rd_batch_offsets(self.h, off.ctypes.data_as(_P)))
+        return off
+
+    def apsp(self, A, D, stream=None):
+        """A, D: CUDA tensors (packed); the call is asynchronous on `stream` (cudaStream_t int)."""
+        pa, ka = _ptr(A)
+        pd, kd = _ptr(D)
+        _check(load().rd_batch_apsp(self.h, pa, pd, ctypes.c_void_p(stream or 0)))
+        return D
+
+    def status(self):
+        st = np.empty(self.G, dtype=np.int32)
+        _check(load().rd_batch_status(self.h, st.ctypes.data_as(_P)))
+        return st
+
+    def close(self):
+        if self.h:
+            load().rd_batch_destroy(self.h)
             self.h = None
 
     def __enter__(self):

@@ -1,0 +1,84 @@
+"""Batched graphs (rd_batch_*): every graph of a mixed batch in one launch, D bit-exact against the
+oracle graph by graph, per-graph gain rejection, determinism across runs, argument errors."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_07403_gb300 import graphs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_07403_gb300 import build
+    from paper_2308_07403_gb300 import rd as _rd
+
+    build.build()
+    _rd.load()
+    return _rd
+
+
+def mixed_batch():
+    """The batched recipe's mix plus edge sizes (1, 2, 63, 64, 65, 128, 130, 512), closed-form
+    families, and one graph whose gain breaks the column-sum bound."""
+    kinds, n, As, g = graphs.workload_batched(40, 32, 512, replica=5)
+    As, gs = list(As), list(g)
+    for m in (1, 2, 63, 64, 65, 128, 130, 512):
+        A = graphs.er(m, min(1.0, 4.0 / m), 77 + m)
+        As.append(A)
+        gs.append(graphs.gamma_small(A))
+    for A, gam in ((graphs.directed_path(100), 0.3), (graphs.binary_tree(200), None),
+                   (graphs.grid4(300, 17), None), (graphs.complete(40), 0.5 / 40)):
+        As.append(A)
+        gs.append(graphs.gamma_small(A) if gam is None else gam)
+    bad = len(As)
+    As.append(graphs.complete(20))
+    gs.append(0.9)  # 0.9 * 19 >= 1: rejected
+    ns = np.array([A.shape[0] for A in As], dtype=np.int32)
+    return ns, As, np.array(gs), bad
+
+
+def run(rd, ns, As, gs, fill=-7):
+    with rd.Batch(ns, gs) as b:
+        off = b.offsets()
+        packed = np.zeros(int(off[-1]), dtype=np.uint8)
+        for g, A in enumerate(As):
+            packed[off[g]:off[g + 1]] = np.ascontiguousarray(A).ravel()
+        A_dev = torch.from_numpy(packed).cuda()
+        D_dev = torch.full((int(off[-1]),), fill, dtype=torch.int32, device="cuda")
+        b.apsp(A_dev, D_dev, torch.cuda.current_stream().cuda_stream)
+        st = b.status()
+    return off, D_dev.cpu().numpy(), st
+
+
+def test_batch_matches_oracle(rd):
+    ns, As, gs, bad = mixed_batch()
+    off, D, st = run(rd, ns, As, gs)
+    for g, A in enumerate(As):
+        n = int(ns[g])
+        Dg = D[off[g]:off[g + 1]].reshape(n, n)
+        if g == bad:
+            assert st[g] == rd.RD_ERR_GAMMA
+            assert (Dg == -7).all()  # untouched
+            continue
+        assert st[g] == rd.RD_OK, (g, n, st[g])
+        assert np.array_equal(Dg, oracle.rdistance(A, float(gs[g]))), (g, n)
+
+
+def test_batch_deterministic(rd):
+    kinds, ns, As, gs = graphs.workload_batched(24, 32, 256, replica=6)
+    off1, D1, st1 = run(rd, ns, As, gs)
+    off2, D2, st2 = run(rd, ns, As, gs, fill=0)
+    assert (st1 == rd.RD_OK).all() and (st2 == rd.RD_OK).all()
+    assert np.array_equal(D1, D2)
+
+
+def test_batch_rejects_bad_sizes(rd):
+    for ns in ([0, 10], [10, rd.BATCH_MAX_N + 1]):
+        with pytest.raises(rd.RDError) as ei:
+            rd.Batch(np.array(ns), np.array([0.1, 0.1]))
+        assert ei.value.status == rd.RD_ERR_ARG
