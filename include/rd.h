@@ -243,6 +243,55 @@ rd_status rd_batch_status(rd_batch_handle b, int32_t* status);
 /* Free a batch (NULL is ignored). */
 void rd_batch_destroy(rd_batch_handle b);
 
+/* ---- Serving (continuous batching of requests over resident graphs) --------------------------
+ * A server runs requests -- the full R-distance of a graph, or goal rows (the local mode of
+ * Sec. 4.2) -- on `workers` threads, each with its own CUDA stream, one request per worker at a
+ * time, so requests that arrive while others run start as soon as a worker and device memory are
+ * free and their work overlaps on the device.  Each graph's handle (its LU factors and inverses)
+ * stays resident under the caller's graph id, so later goal solves on the same graph skip the
+ * factorisation; when a new handle does not fit the device-memory budget, the least recently used
+ * idle graphs are evicted.  Requests for one graph run one after another (a handle is not
+ * thread-safe).  Latency is measured from submit to completion.  The paper has no counterpart;
+ * this is a deployment layer over rd_create / rd_apsp / rd_goal_solve. */
+enum { RD_REQ_APSP = 0, RD_REQ_GOALS = 1 };
+
+typedef struct {
+  int32_t kind;          /* RD_REQ_APSP or RD_REQ_GOALS                                        */
+  int32_t graph_id;      /* caller's graph id: requests with one id share the resident factors */
+                         /* (and must carry the same graph); < 0: not kept                     */
+  const uint8_t* A;      /* host, n x n (copied at submit)                                      */
+  int32_t n;
+  double gamma;
+  const int32_t* goals;  /* RD_REQ_GOALS: host, k goals (copied at submit)                      */
+  int32_t k;             /* 1..64                                                               */
+  int32_t precision;     /* RD_PREC_FP64 or RD_PREC_SPLIT_BF16 (digits chosen by the library)  */
+  int32_t* D_out;        /* RD_REQ_APSP: host n x n, valid when the request completes           */
+  double* Y_out;         /* RD_REQ_GOALS: host k x n, valid when the request completes          */
+} rd_request;
+
+typedef struct {
+  int64_t completed, failed, queued;
+  int32_t resident_graphs, max_inflight;
+  int64_t bytes_used, evictions, reused;
+  double p50_ms, p99_ms;  /* submit-to-completion latency over all completed requests           */
+  double seconds;         /* since rd_serve_create                                              */
+} rd_serve_report;
+
+typedef struct rd_server* rd_server_handle;
+
+/* Start a server on the current device with a device-memory budget (bytes) and 1..64 workers. */
+rd_status rd_serve_create(int64_t hbm_budget_bytes, int32_t workers, rd_server_handle* out);
+/* Queue a request (its inputs are copied); *id identifies it for poll and wait. */
+rd_status rd_serve_submit(rd_server_handle s, const rd_request* r, int64_t* id);
+/* *done = 1 once the request completed (its outputs are valid). */
+rd_status rd_serve_poll(rd_server_handle s, int64_t id, int32_t* done);
+/* Block until the request completed; its status and latency (ms) are returned and the id is
+ * released. */
+rd_status rd_serve_wait(rd_server_handle s, int64_t id, rd_status* result, double* latency_ms);
+rd_status rd_serve_stats(rd_server_handle s, rd_serve_report* out);
+/* Finish the queued requests, then free every resident graph and the server. */
+void rd_serve_destroy(rd_server_handle s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,332 @@
+// rd_serve.cu -- the serving runtime: a request queue over handles, continuous batching on several
+// CUDA streams, admission by device-memory footprint, resident factors per graph for repeated goal
+// solves, latency accounting.  Host code only; every computation runs through rd_create / rd_apsp /
+// rd_goal_solve on the workers' streams.
+//
+// Each worker thread runs on one non-blocking stream of the server's and runs one request at a time.  A request is
+// runnable when its graph's handle is resident and idle (goal solves reuse the factors), or when a
+// new handle fits the budget, after evicting least-recently-used idle handles if needed.  Requests
+// that arrive while others are on the GPU start as soon as a worker and the memory are free, so
+// the work of several requests overlaps on the device.  Requests for one graph never run at the
+// same time (a handle is not thread-safe); a later request for a busy graph waits while the queue
+// behind it moves on.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "rd_internal.cuh"
+
+namespace {
+
+using clock_type = std::chrono::steady_clock;
+
+struct Job {
+  int64_t id = 0;
+  rd_request r{};
+  std::vector<uint8_t> A;       // copied at submit
+  std::vector<int32_t> goals;   // copied at submit
+  clock_type::time_point t_submit, t_start, t_done;
+  rd_status result = RD_OK;
+  bool done = false;
+  bool fresh = false;           // created a handle for this job
+};
+
+struct Resident {
+  rd_handle h = nullptr;
+  int32_t n = 0;
+  int64_t bytes = 0;            // reserved or measured device bytes
+  bool busy = false;
+  bool ready = false;           // the handle exists (a reservation precedes it)
+  uint64_t last_use = 0;
+  int32_t precision = -1;
+};
+
+// device bytes of a handle of n nodes (the workspace rd_create allocates, the split digit planes
+// when the precision asks for them, host-output staging), used to admit before creating
+int64_t estimate_bytes(int32_t n, int32_t precision) {
+  const int64_t N = ((int64_t)n + RD_PAD - 1) / RD_PAD * RD_PAD;
+  int64_t b = (int64_t)n * n + 8 * N * N * 5 / 2 + 8 * 64 * N + 16 * (int64_t)n;
+  b += 4 * (int64_t)n * n + 8 * (int64_t)n * n;  // staging of host D and Y outputs
+  if (precision == RD_PREC_SPLIT_BF16) b += 2 * 2 * 15 * N * (N + 256) + 8 * (N + 256) * (N + 256) / 64;
+  return b;
+}
+
+}  // namespace
+
+struct rd_server {
+  int device = 0;
+  int64_t budget = 0;
+  int64_t used = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job*> queue;
+  std::unordered_map<int64_t, Job*> jobs;
+  std::unordered_map<int32_t, Resident> cache;  // graph id -> resident handle
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;  // one per worker; destroyed after the resident handles
+  int64_t next_id = 1;
+  uint64_t tick = 0;
+  bool stop = false;
+  int inflight = 0, max_inflight = 0;
+  int64_t completed = 0, failed = 0, evictions = 0, reused = 0;
+  std::vector<double> lat_ms;
+  clock_type::time_point t0;
+};
+
+namespace {
+
+// pick a runnable job (caller holds the lock); reserves memory / marks the graph busy
+Job* take_runnable(rd_server* s) {
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    Job* j = *it;
+    const int32_t gid = j->r.graph_id;
+    auto c = (gid >= 0) ? s->cache.find(gid) : s->cache.end();
+    if (c != s->cache.end() && c->second.n == j->r.n && c->second.precision == j->r.precision) {
+      if (c->second.busy) continue;  // the graph is running: keep its order, let others pass
+      c->second.busy = true;
+      s->queue.erase(it);
+      return j;
+    }
+    const int64_t need = estimate_bytes(j->r.n, j->r.precision);
+    // evict least-recently-used idle handles until the job fits (other graphs only)
+    while (s->used + need > s->budget) {
+      auto victim = s->cache.end();
+      for (auto e = s->cache.begin(); e != s->cache.end(); ++e)
+        if (!e->second.busy && e->second.ready && (victim == s->cache.end() || e->second.last_use < victim->second.last_use))
+          victim = e;
+      if (victim == s->cache.end()) break;
+      rd_destroy(victim->second.h);
+      s->used -= victim->second.bytes;
+      s->cache.erase(victim);
+      s->evictions++;
+    }
+    if (s->used + need > s->budget && s->inflight > 0) continue;  // wait for memory (unless idle)
+    if (c != s->cache.end()) {  // same id but another size or precision: replace it
+      if (c->second.busy) continue;
+      rd_destroy(c->second.h);
+      s->used -= c->second.bytes;
+      s->cache.erase(c);
+    }
+    s->used += need;
+    j->fresh = true;
+    Resident rsd;
+    rsd.n = j->r.n;
+    rsd.bytes = need;
+    rsd.busy = true;
+    rsd.precision = j->r.precision;
+    if (gid >= 0) s->cache[gid] = rsd;
+    s->queue.erase(it);
+    return j;
+  }
+  return nullptr;
+}
+
+void run_job(rd_server* s, Job* j, cudaStream_t st) {
+  rd_handle h = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!j->fresh) h = s->cache[j->r.graph_id].h;
+  }
+  rd_status r = RD_OK;
+  if (!h) {
+    r = rd_create(j->A.data(), j->r.n, j->r.gamma, &h);
+    if (r == RD_OK) r = rd_set_precision(h, j->r.precision, 0);
+  }
+  if (r == RD_OK) r = rd_set_stream(h, (void*)st);  // this worker's stream, whoever ran it before
+  if (r == RD_OK) {
+    if (j->r.kind == RD_REQ_APSP)
+      r = rd_apsp(h, j->r.D_out, nullptr);
+    else
+      r = rd_goal_solve(h, j->goals.data(), j->r.k, j->r.Y_out);
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  j->result = r;
+  j->t_done = clock_type::now();
+  j->done = true;
+  const int32_t gid = j->r.graph_id;
+  const bool cached = gid >= 0 && s->cache.count(gid) != 0;
+  if (j->fresh) {
+    const int64_t reserved = estimate_bytes(j->r.n, j->r.precision);
+    if (r == RD_OK && h && cached) {
+      Resident& e = s->cache[gid];
+      rd_stats stt;
+      const int64_t real = (rd_get_stats(h, &stt) == RD_OK) ? stt.bytes_device : reserved;
+      s->used += real - reserved;
+      e.h = h;
+      e.bytes = real;
+      e.ready = true;
+      e.busy = false;
+      e.last_use = ++s->tick;
+    } else {  // failed, or a graph without an id: nothing stays resident
+      if (h) rd_destroy(h);
+      s->used -= reserved;
+      if (cached) s->cache.erase(gid);
+    }
+  } else {
+    s->reused++;
+    if (cached) {
+      Resident& e = s->cache[gid];
+      e.busy = false;
+      e.last_use = ++s->tick;
+    }
+  }
+  s->inflight--;
+  s->completed++;
+  if (r != RD_OK) s->failed++;
+  s->lat_ms.push_back(std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count());
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();
+}
+
+void worker_main(rd_server* s, cudaStream_t st) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    Job* j = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      for (;;) {
+        if (s->stop && s->queue.empty()) break;
+        j = take_runnable(s);
+        if (j) break;
+        s->cv_work.wait(lk);
+      }
+      if (!j) break;
+      j->t_start = clock_type::now();
+      s->inflight++;
+      s->max_inflight = std::max(s->max_inflight, s->inflight);
+    }
+    run_job(s, j, st);
+  }
+}
+
+double percentile(std::vector<double> v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const size_t i = std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5));
+  return v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+rd_status rd_serve_create(int64_t hbm_budget_bytes, int32_t workers, rd_server_handle* out) {
+  if (!out) return RD_ERR_ARG;
+  *out = nullptr;
+  if (hbm_budget_bytes <= 0 || workers < 1 || workers > 64) {
+    rd_record_error("rd_serve_create: budget must be > 0 and workers in [1, 64]");
+    return RD_ERR_ARG;
+  }
+  rd_server* s = new rd_server();
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    rd_record_error("rd_serve_create: no CUDA device");
+    return RD_ERR_CUDA;
+  }
+  s->budget = hbm_budget_bytes;
+  s->t0 = clock_type::now();
+  for (int w = 0; w < workers; ++w) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      for (cudaStream_t q : s->streams) cudaStreamDestroy(q);
+      delete s;
+      rd_record_error("rd_serve_create: cudaStreamCreate failed");
+      return RD_ERR_CUDA;
+    }
+    s->streams.push_back(st);
+  }
+  for (int w = 0; w < workers; ++w) s->workers.emplace_back(worker_main, s, s->streams[w]);
+  *out = s;
+  return RD_OK;
+}
+
+rd_status rd_serve_submit(rd_server_handle s, const rd_request* r, int64_t* id) {
+  if (!s || !r || !id || !r->A || r->n < 1 || !(r->gamma > 0.0 && r->gamma < 1.0)) return RD_ERR_ARG;
+  if (r->kind != RD_REQ_APSP && r->kind != RD_REQ_GOALS) return RD_ERR_ARG;
+  if (r->kind == RD_REQ_APSP && !r->D_out) return RD_ERR_ARG;
+  if (r->kind == RD_REQ_GOALS && (!r->goals || !r->Y_out || r->k < 1 || r->k > RD_MAX_GOALS)) return RD_ERR_ARG;
+  if (r->precision != RD_PREC_FP64 && r->precision != RD_PREC_SPLIT_BF16) return RD_ERR_ARG;
+  Job* j = new Job();
+  j->r = *r;
+  j->A.assign(r->A, r->A + (size_t)r->n * r->n);
+  if (r->kind == RD_REQ_GOALS) j->goals.assign(r->goals, r->goals + r->k);
+  j->t_submit = clock_type::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      delete j;
+      return RD_ERR_STATE;
+    }
+    j->id = s->next_id++;
+    s->jobs[j->id] = j;
+    s->queue.push_back(j);
+  }
+  s->cv_work.notify_one();
+  *id = j->id;
+  return RD_OK;
+}
+
+rd_status rd_serve_poll(rd_server_handle s, int64_t id, int32_t* done) {
+  if (!s || !done) return RD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return RD_ERR_ARG;
+  *done = it->second->done ? 1 : 0;
+  return RD_OK;
+}
+
+rd_status rd_serve_wait(rd_server_handle s, int64_t id, rd_status* result, double* latency_ms) {
+  if (!s) return RD_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return RD_ERR_ARG;
+  Job* j = it->second;
+  s->cv_done.wait(lk, [&] { return j->done; });
+  if (result) *result = j->result;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
+  s->jobs.erase(it);
+  delete j;
+  return RD_OK;
+}
+
+rd_status rd_serve_stats(rd_server_handle s, rd_serve_report* out) {
+  if (!s || !out) return RD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->queued = (int64_t)s->queue.size();
+  out->resident_graphs = (int32_t)s->cache.size();
+  out->max_inflight = s->max_inflight;
+  out->bytes_used = s->used;
+  out->evictions = s->evictions;
+  out->reused = s->reused;
+  out->p50_ms = percentile(s->lat_ms, 0.5);
+  out->p99_ms = percentile(s->lat_ms, 0.99);
+  out->seconds = std::chrono::duration<double>(clock_type::now() - s->t0).count();
+  return RD_OK;
+}
+
+void rd_serve_destroy(rd_server_handle s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  for (auto& e : s->cache)
+    if (e.second.h) rd_destroy(e.second.h);
+  for (auto& e : s->jobs) delete e.second;
+  for (cudaStream_t q : s->streams) cudaStreamDestroy(q);
+  delete s;
+}
+
+}  // extern "C"

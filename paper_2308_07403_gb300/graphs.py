@@ -257,3 +257,23 @@ def workload_batched(G: int = 4096, n_lo: int = 32, n_hi: int = 512, replica: in
         As.append(A)
         gs.append(gamma_small(A))
     return kinds, np.array(ns, dtype=np.int32), As, np.array(gs, dtype=np.float64)
+
+
+def serving_pool(count: int = 128, n_lo: int = 64, n_hi: int = 4096, replica: int = 0):
+    """The serving workload's graph pool: n log-uniform in [n_lo, n_hi], the kind uniform over ER
+    (p = 4/n), a 4-neighbour grid with ceil(sqrt n) columns and Watts-Strogatz (k = 10, beta =
+    0.1); gain 0.5 / (Delta + 1).  Returns a list of (A, gamma)."""
+    rng = np.random.default_rng(seed_for(3, replica))
+    out = []
+    for _ in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        kind = BATCH_KINDS[int(rng.integers(len(BATCH_KINDS)))]
+        s = int(rng.integers(2**31 - 1))
+        if kind == "er":
+            A = er(n, 4.0 / n, s)
+        elif kind == "grid":
+            A = grid4(n, int(np.ceil(np.sqrt(n))))
+        else:
+            A = ws(n, 10, 0.1, s)
+        out.append((A, gamma_small(A)))
+    return out

@@ -57,7 +57,16 @@ _SIGS = {
     "rd_batch_apsp": (ctypes.c_int, [_P, _P, _P, _P]),
     "rd_batch_status": (ctypes.c_int, [_P, _P]),
     "rd_batch_destroy": (None, [_P]),
+    "rd_serve_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "rd_serve_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "rd_serve_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
+    "rd_serve_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "rd_serve_stats": (ctypes.c_int, [_P, _P]),
+    "rd_serve_destroy": (None, [_P]),
 }
+RD_REQ_APSP = 0
+RD_REQ_GOALS = 1
 
 
 class rd_stats(ctypes.Structure):
@@ -315,6 +324,103 @@ class Batch:
         if self.h:
             load().rd_batch_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class rd_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("graph_id", ctypes.c_int32), ("A", _P), ("n", ctypes.c_int32),
+                ("gamma", ctypes.c_double), ("goals", _P), ("k", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("D_out", _P), ("Y_out", _P)]
+
+
+class rd_serve_report(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("resident_graphs", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("bytes_used", ctypes.c_int64), ("evictions", ctypes.c_int64), ("reused", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class Server:
+    """Owns one rd_server_handle.  submit_* return an id; the numpy output array of a request stays
+    referenced here until wait(id) returns (the library writes it when the request completes)."""
+
+    def __init__(self, budget_bytes: int, workers: int = 4):
+        h = ctypes.c_void_p()
+        _check(load().rd_serve_create(int(budget_bytes), int(workers), ctypes.byref(h)))
+        self.h = h
+        self._live = {}
+
+    def _submit(self, kind, graph_id, A, gamma, goals, out, precision):
+        A = np.ascontiguousarray(A, dtype=np.uint8)
+        r = rd_request()
+        r.kind = kind
+        r.graph_id = int(graph_id)
+        r.A = A.ctypes.data_as(_P)
+        r.n = int(A.shape[0])
+        r.gamma = float(gamma)
+        r.precision = int(precision)
+        keep = [A, out]
+        if goals is not None:
+            goals = np.ascontiguousarray(goals, dtype=np.int32)
+            r.goals = goals.ctypes.data_as(_P)
+            r.k = int(goals.size)
+            r.Y_out = out.ctypes.data_as(_P)
+            keep.append(goals)
+        else:
+            r.D_out = out.ctypes.data_as(_P)
+        rid = ctypes.c_int64()
+        _check(load().rd_serve_submit(self.h, ctypes.byref(r), ctypes.byref(rid)))
+        self._live[rid.value] = keep
+        return rid.value
+
+    @staticmethod
+    def _host_out(x, dtype):
+        if not (isinstance(x, np.ndarray) and x.dtype == dtype and x.flags.c_contiguous):
+            raise ValueError(f"outputs of a server request are C-contiguous numpy {np.dtype(dtype).name} arrays")
+        return x
+
+    def submit_apsp(self, graph_id, A, gamma, D_out, precision=RD_PREC_SPLIT_BF16):
+        """D_out: C-contiguous int32 numpy array (n, n)."""
+        return self._submit(RD_REQ_APSP, graph_id, A, gamma, None, self._host_out(D_out, np.int32), precision)
+
+    def submit_goals(self, graph_id, A, gamma, goals, Y_out, precision=RD_PREC_SPLIT_BF16):
+        """Y_out: C-contiguous float64 numpy array (k, n)."""
+        return self._submit(RD_REQ_GOALS, graph_id, A, gamma, goals, self._host_out(Y_out, np.float64), precision)
+
+    def poll(self, rid):
+        d = ctypes.c_int32()
+        _check(load().rd_serve_poll(self.h, int(rid), ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, rid):
+        """Returns (status, latency_ms)."""
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        _check(load().rd_serve_wait(self.h, int(rid), ctypes.byref(st), ctypes.byref(lat)))
+        self._live.pop(int(rid), None)
+        return st.value, lat.value
+
+    def stats(self):
+        r = rd_serve_report()
+        _check(load().rd_serve_stats(self.h, ctypes.byref(r)))
+        return {name: getattr(r, name) for name, _ in r._fields_}
+
+    def close(self):
+        if self.h:
+            load().rd_serve_destroy(self.h)
+            self.h = None
+            self._live.clear()
 
     def __enter__(self):
         return self
