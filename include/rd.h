@@ -103,6 +103,8 @@ typedef struct {
   int32_t split_order;    /* 1: the split path ran on P M P^T with the library's locality     */
                           /* order (compact 64-node parts, 64-wide chunks); D, Y and goal    */
                           /* rows are returned in the caller's node order either way         */
+  int64_t edge_updates;   /* edges changed by rd_update_edge since rd_create / rd_load        */
+  int64_t update_refactors; /* of those, updates that refactored (cancellation in Y)          */
 } rd_stats;
 
 /* Create a handle for the unweighted graph A (n x n bytes) and gain gamma: validates gamma
@@ -127,17 +129,18 @@ rd_status rd_set_stream(rd_handle h, void* stream);
 
 /* Select RD_PREC_FP64 or RD_PREC_SPLIT_BF16.  slices in [2, 15] fixes the digit count (no
  * screen, no self-check, the caller's node order: the caller owns the precision); 0 lets the
- * library choose per graph.  It first screens the graph (unweighted graphs; a few
- * synchronisations): the digits of each 256-wide chunk of the node order share one scale, so a
- * chunk spanning S hops costs about S log2(1/gamma) bits, and the digit count is the fewest
- * (at least 8) whose 7 bits each cover that plus 40 bits of result.  When the node order needs
- * more than 12, it also screens its locality order (compact 64-node parts, 64-wide chunks:
- * rd_stats.split_order) and takes it when it needs fewer; beyond 15 digits the graph runs in
- * FP64 (rd_stats.split_screen_bits, rd_stats.slices).  Weighted graphs start at 12.  It then checks
- * every split result: 64 sampled rows of Y must satisfy y^T M = e_g^T to a relative 1e-9 per
- * entry (rd_stats.split_residual).  When the check fails it recomputes the graph's inverse with
- * 15 digits, then in FP64 (directly in FP64 when the residual is beyond 1e-3).  Drops cached
- * factors when the mode changes. */
+ * library choose per graph.  It first screens the graph (a few synchronisations): the digits of
+ * each 256-wide chunk of the node order share one scale, so a chunk spanning S hops costs about
+ * S log2(1/gamma) bits (for a weighted graph S is a weighted distance, and the estimate is
+ * raised by 10%), and the digit count is the fewest (at least 8) whose 7 bits each cover that
+ * plus 40 bits of result.  When the node order needs more than 12, it also screens its locality
+ * order (compact 64-node parts, 64-wide chunks: rd_stats.split_order) and takes it when it needs
+ * fewer; beyond 15 digits (22 in the locality order) the graph runs in FP64
+ * (rd_stats.split_screen_bits, rd_stats.slices).  It then checks every split factorisation,
+ * before any product uses it: 64 sampled rows of Y must satisfy y^T M = e_g^T to a relative 1e-9
+ * per entry (rd_stats.split_residual).  When the check fails it recomputes the graph's inverse with
+ * the digits the residual r asks for (about log2(r / 2^-40) / 7 more), or in FP64 beyond the
+ * order's limit.  Drops cached factors when the mode changes. */
 rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices);
 
 /* Change the decode snap tau (>= 0, < 0.5). */
@@ -163,6 +166,18 @@ rd_status rd_goal_solve(rd_handle h, const int32_t* goals, int32_t k, double* Y_
  * (k x n). */
 rd_status rd_greedy_next(rd_handle h, const int32_t* goals, int32_t k, const double* Yrows,
                          int32_t* next);
+
+/* Incremental edge update (the paper's map update when an obstacle appears, Sec. 6): the edge
+ * j -> i becomes present (weight w for a weighted handle; ignored otherwise) or absent, and D
+ * (n x n) -- and Y when not NULL -- receive the R-distance of the changed graph.  X_ij changes by
+ * delta, M by -delta e_i e_j^T, and the handle's resident Y (materialised once from the factors,
+ * n x n FP64) by the Sherman-Morrison rank-1 term alpha (Y e_i)(e_j^T Y), alpha = delta /
+ * (1 - delta Y_ji), in one O(n^2) pass that also decodes D.  Added or strengthened edges add terms
+ * of one sign; when a removal cancels an entry (more than 20 bits of it lost) the library factors
+ * the changed graph from scratch instead (rd_stats.update_refactors).  RD_ERR_GAMMA when the
+ * change would make column j's sum of X reach 1 (nothing changes).  Later goal solves read the
+ * resident Y.  Synchronises. */
+rd_status rd_update_edge(rd_handle h, int32_t i, int32_t j, int32_t present, float w, int32_t* D, double* Y);
 
 /* Turn the per-kernel profile on (1) or off (0); either way its counters restart at zero.
  * With the profile on, every launch of the dense-contraction (GEMM) kernels is bracketed by a

@@ -79,64 +79,91 @@ __global__ void scan_kernel(const int32_t* __restrict__ deg, int n, int32_t* __r
   if (n == 0 && t == 0) ptr[0] = 0;
 }
 
-// successors of node v: {j : A[j][v] != 0} (edge v -> j), ascending j
-__global__ void succ_fill_kernel(const uint8_t* __restrict__ A, int n, const int32_t* __restrict__ ptr,
-                                 int32_t* __restrict__ idx) {
+// successors of node v: {j : A[j][v] != 0} (edge v -> j), ascending j; with W, also the edge weights
+__global__ void succ_fill_kernel(const uint8_t* __restrict__ A, const float* __restrict__ W, int n,
+                                 const int32_t* __restrict__ ptr, int32_t* __restrict__ idx, float* __restrict__ wt) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   int w = ptr[v];
   for (int j = 0; j < n; ++j)
-    if (A[(long long)j * n + v]) idx[w++] = j;
+    if (A[(long long)j * n + v]) {
+      if (W) wt[w] = W[(long long)j * n + v];
+      idx[w++] = j;
+    }
 }
 
-// Hop distances from sampled sources and their spread within chunks of consecutive positions (the
-// split path's range screen; the node at position q is ord[q], or q without an order).  One CTA
-// per source: a level-synchronous BFS along the successor lists (dist: n ints per source, -1 = not
-// reached; at most n levels), then, one warp per chunk of `chunk` consecutive positions, the spread
-// max d - min d over the chunk's reached nodes.  The
-// largest spread over chunks and sources is atomicMax-ed into *out.  Sources: nodes
-// b n / nsrc + n / (2 nsrc), b = blockIdx.x.
+// Distances from sampled sources and their spread within chunks of consecutive positions (the split
+// path's range screen; the node at position q is ord[q], or q without an order).  One CTA per
+// source: a level-synchronous BFS along the successor lists (hop counts), or for a weighted graph
+// (w != null, the weight of each successor edge) Bellman-Ford rounds of relaxation along them
+// (float distances; at most n rounds; concurrent relaxations only lower a distance, so a round
+// without a change ends it).  Then, one warp per chunk of `chunk` consecutive positions, the spread
+// max d - min d over the chunk's reached nodes; the largest over chunks and sources goes to *out as
+// the bits of a non-negative float (atomicMax).  Sources: nodes b n / nsrc + n / (2 nsrc).
 __global__ void __launch_bounds__(1024) chunk_spread_kernel(const int32_t* __restrict__ ptr,
-                                                            const int32_t* __restrict__ succ, int n,
-                                                            int nsrc, int chunk, const int32_t* __restrict__ ord,
-                                                            int32_t* __restrict__ dist, unsigned long long* out) {
+                                                            const int32_t* __restrict__ succ,
+                                                            const float* __restrict__ w, int n, int nsrc,
+                                                            int chunk, const int32_t* __restrict__ ord,
+                                                            float* __restrict__ dist, unsigned long long* out) {
   const int b = blockIdx.x, t = threadIdx.x;
   const int src = (int)(((long long)b * n) / nsrc + (n / nsrc) / 2);
-  int32_t* d = dist + (long long)b * n;
-  for (int v = t; v < n; v += blockDim.x) d[v] = (v == src) ? 0 : -1;
+  float* d = dist + (long long)b * n;
+  const float inf = __int_as_float(0x7f800000);
+  for (int v = t; v < n; v += blockDim.x) d[v] = (v == src) ? 0.f : inf;
   __syncthreads();
-  for (int L = 0; L < n; ++L) {
-    int grew = 0;
-    for (int v = t; v < n; v += blockDim.x) {
-      if (d[v] != L) continue;
-      const int e1 = ptr[v + 1];
-      for (int e = ptr[v]; e < e1; ++e) {
-        const int w = succ[e];
-        if (d[w] < 0) {  // every writer of this level writes the same L + 1
-          d[w] = L + 1;
-          grew = 1;
+  if (!w) {
+    for (int L = 0; L < n; ++L) {
+      int grew = 0;
+      const float fl = (float)L;
+      for (int v = t; v < n; v += blockDim.x) {
+        if (d[v] != fl) continue;
+        const int e1 = ptr[v + 1];
+        for (int e = ptr[v]; e < e1; ++e) {
+          const int x = succ[e];
+          if (d[x] == inf) {  // every writer of this level writes the same L + 1
+            d[x] = fl + 1.f;
+            grew = 1;
+          }
         }
       }
+      if (!__syncthreads_or(grew)) break;
     }
-    if (!__syncthreads_or(grew)) break;
+  } else {
+    for (int round = 0; round < n; ++round) {
+      int changed = 0;
+      for (int v = t; v < n; v += blockDim.x) {
+        const float dv = d[v];
+        if (dv == inf) continue;
+        const int e1 = ptr[v + 1];
+        for (int e = ptr[v]; e < e1; ++e) {
+          const int x = succ[e];
+          const float nd = dv + w[e];
+          if (nd < d[x]) {  // non-negative floats order like their bit patterns
+            atomicMin(reinterpret_cast<int*>(d + x), __float_as_int(nd));
+            changed = 1;
+          }
+        }
+      }
+      if (!__syncthreads_or(changed)) break;
+    }
   }
   const int warp = t >> 5, lane = t & 31, nwarps = blockDim.x >> 5;
   const int nch = (n + chunk - 1) / chunk;
   for (int c = warp; c < nch; c += nwarps) {
-    int lo = 0x7fffffff, hi = -1;
+    float lo = inf, hi = -1.f;
     const int v1 = min(n, (c + 1) * chunk);
     for (int q = c * chunk + lane; q < v1; q += 32) {
-      const int x = d[ord ? ord[q] : q];
-      if (x >= 0) {
-        lo = min(lo, x);
-        hi = max(hi, x);
+      const float x = d[ord ? ord[q] : q];
+      if (x != inf) {
+        lo = fminf(lo, x);
+        hi = fmaxf(hi, x);
       }
     }
     for (int o = 16; o; o >>= 1) {
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    if (lane == 0 && hi >= 0) atomicMax(out, (unsigned long long)(hi - lo));
+    if (lane == 0 && hi >= 0.f) atomicMax(out, (unsigned long long)__float_as_uint(hi - lo));
   }
 }
 
@@ -231,64 +258,110 @@ __global__ void __launch_bounds__(1024) landmark_kernel(const int32_t* __restric
   }
 }
 
-// One level of the recursive coordinate bisection behind the split path's locality order.  CTA c
-// splits the part [parts[2c], parts[2c+1]) of the order `ord` (node at each position) into a first
-// part of m0 = 64 ceil(m / 128) positions and the rest, along the landmark axis (cu or cv) with the
-// larger extent over the part: the first part takes the m0 smallest coordinates, ties in order of
-// position; nodes without coordinates go last.  Both parts keep their nodes' relative order (a
-// stable partition), so the result is deterministic.  Coordinates are counted in a histogram
-// (hist: 2m + 2 ints of scratch at 2 b + 2 c; offsets past 2m share the last real bucket).
-__global__ void __launch_bounds__(1024) rcb_kernel(const int32_t* __restrict__ parts, const int32_t* __restrict__ cu,
-                                                   const int32_t* __restrict__ cv, int32_t* ord, int32_t* tmp,
-                                                   int32_t* hist_all) {
+// ---- recursive bisection behind the split path's locality order ------------------------------
+//
+// A part (positions [b, e) of the order) is split into a first part of m0 = 64 ceil(m / 128)
+// positions and the rest along one of three keys: the two landmark axes cu, cv (see
+// landmark_kernel), and the hop distance d_a from a peripheral node a of the part (the node
+// farthest, within the part, from its first node).  Each key's split is scored by the larger
+// double-sweep hop diameter of its two halves (a half that one BFS does not cover scores
+// RCB_SPLIT_PENALTY more), and the best scoring key is applied (ties: cu, cv, d_a).  The landmark
+// axes suit meshes with a Manhattan metric; the part-local distance suits king-move meshes, whose
+// Chebyshev balls give a corner landmark's distance no row information.  Every BFS stays inside
+// its part (or half), whose nodes carry the CTA's tag.
+
+constexpr int RCB_SPLIT_PENALTY = 1 << 20;
+
+// BFS inside the nodes L[q0..q1) that carry `tag_v`, from `src` (one of them): dist[v] = hops,
+// -1 if not reached.  At most q1 - q0 levels.
+__device__ void part_bfs(const int32_t* __restrict__ ptr, const int32_t* __restrict__ succ, const int32_t* L, int q0,
+                         int q1, const int32_t* tag, int tag_v, int src, int32_t* dist) {
+  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const int v = L[q];
+    dist[v] = (v == src) ? 0 : -1;
+  }
+  __syncthreads();
+  for (int lev = 0; lev < q1 - q0; ++lev) {
+    int grew = 0;
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+      const int v = L[q];
+      if (dist[v] != lev) continue;
+      for (int x = ptr[v]; x < ptr[v + 1]; ++x) {
+        const int w = succ[x];
+        if (tag[w] == tag_v && dist[w] < 0) {  // every writer of this level writes lev + 1
+          dist[w] = lev + 1;
+          grew = 1;
+        }
+      }
+    }
+    if (!__syncthreads_or(grew)) break;
+  }
+}
+
+// The farthest reached node of L[q0..q1) (smallest position among ties), its distance, and
+// whether some node was not reached.
+struct Far {
+  int node, dist, unreached;
+};
+__device__ Far part_farthest(const int32_t* L, int q0, int q1, const int32_t* dist) {
+  __shared__ long long red[32];
+  long long best = -1;  // (dist << 32) | (INT_MAX - q)
+  int miss = 0;
+  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const int d = dist[L[q]];
+    if (d < 0) miss = 1;
+    else best = max(best, ((long long)d << 32) | (long long)(0x7fffffff - q));
+  }
+  for (int o = 16; o; o >>= 1) best = max(best, (long long)__shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  miss = __syncthreads_or(miss);
+  long long b = -1;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = max(b, red[w]);
+  __syncthreads();
+  Far f;
+  f.node = b < 0 ? L[q0] : L[0x7fffffff - (int)(b & 0xffffffffll)];
+  f.dist = b < 0 ? 0 : (int)(b >> 32);
+  f.unreached = miss;
+  return f;
+}
+
+// Double-sweep hop diameter of the half L[q0..q1) (nodes tagged tag_v), plus the penalty when it
+// is not covered from its first node.
+__device__ int half_score(const int32_t* ptr, const int32_t* succ, const int32_t* L, int q0, int q1, const int32_t* tag,
+                          int tag_v, int32_t* dist) {
+  if (q1 - q0 <= 1) return 0;
+  part_bfs(ptr, succ, L, q0, q1, tag, tag_v, L[q0], dist);
+  const Far f0 = part_farthest(L, q0, q1, dist);
+  part_bfs(ptr, succ, L, q0, q1, tag, tag_v, f0.node, dist);
+  const Far f1 = part_farthest(L, q0, q1, dist);
+  return f1.dist + (f0.unreached ? RCB_SPLIT_PENALTY : 0);
+}
+
+// Stable split of Lin[b..e) into Lout: the m0 smallest keys first (ties in order of position),
+// nodes without a key (key < 0) last; both parts keep their nodes' relative order.  Keys are
+// counted in a histogram (hist: 2m + 2 ints; keys past 2m above the smallest share the last
+// real bucket).
+__device__ void part_split(const int32_t* Lin, int32_t* Lout, int b, int e, int m0, const int32_t* key,
+                           int32_t* hist) {
   __shared__ int sh[32];
   __shared__ int sh_cut;
-  const int b = parts[2 * blockIdx.x], e = parts[2 * blockIdx.x + 1];
-  const int m = e - b, m0 = 64 * ((m + 127) / 128);
-  const int t = threadIdx.x, T = blockDim.x;
-  if (m0 >= m) return;
-  // extents of both axes over the part's reached nodes
-  int umin = 0x7fffffff, umax = -0x7fffffff, vmin = 0x7fffffff, vmax = -0x7fffffff;
+  __shared__ int sh_lo[32];
+  const int m = e - b, t = threadIdx.x, T = blockDim.x;
+  int lo = 0x7fffffff;
   for (int q = b + t; q < e; q += T) {
-    const int v = ord[q];
-    if (cv[v] < 0) continue;
-    umin = min(umin, cu[v]);
-    umax = max(umax, cu[v]);
-    vmin = min(vmin, cv[v]);
-    vmax = max(vmax, cv[v]);
+    const int k = key[Lin[q]];
+    if (k >= 0) lo = min(lo, k);
   }
-  for (int o = 16; o; o >>= 1) {
-    umin = min(umin, __shfl_xor_sync(0xffffffffu, umin, o));
-    umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-    vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-    vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-  }
-  __shared__ int ext[4][32];
-  if ((t & 31) == 0) {
-    ext[0][t >> 5] = umin;
-    ext[1][t >> 5] = umax;
-    ext[2][t >> 5] = vmin;
-    ext[3][t >> 5] = vmax;
-  }
+  for (int o = 16; o; o >>= 1) lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+  if ((t & 31) == 0) sh_lo[t >> 5] = lo;
   __syncthreads();
-  if (t == 0) {
-    for (int w = 1; w < (T >> 5); ++w) {
-      ext[0][0] = min(ext[0][0], ext[0][w]);
-      ext[1][0] = max(ext[1][0], ext[1][w]);
-      ext[2][0] = min(ext[2][0], ext[2][w]);
-      ext[3][0] = max(ext[3][0], ext[3][w]);
-    }
-  }
-  __syncthreads();
-  const bool use_u = (ext[1][0] - ext[0][0]) >= (ext[3][0] - ext[2][0]);
-  const int lo = use_u ? ext[0][0] : ext[2][0];
-  const int cap = 2 * m;  // last real bucket; bucket cap + 1 holds nodes without coordinates
+  lo = 0x7fffffff;
+  for (int w = 0; w < (T >> 5); ++w) lo = min(lo, sh_lo[w]);
+  const int cap = 2 * m;  // last real bucket; bucket cap + 1 holds nodes without a key
   auto key_of = [&](int q) {
-    const int v = ord[q];
-    if (cv[v] < 0) return cap + 1;
-    return min(cap, (use_u ? cu[v] : cv[v]) - lo);
+    const int k = key[Lin[q]];
+    return k < 0 ? cap + 1 : min(cap, k - lo);
   };
-  int32_t* hist = hist_all + 2 * b + 2 * blockIdx.x;
   for (int k = t; k < cap + 2; k += T) hist[k] = 0;
   __syncthreads();
   for (int q = b + t; q < e; q += T) atomicAdd(&hist[key_of(q)], 1);
@@ -314,7 +387,7 @@ __global__ void __launch_bounds__(1024) rcb_kernel(const int32_t* __restrict__ p
   const int Ks = sh_cut;
   // contiguous segment of positions per thread, so that "earlier position" is a prefix count
   const int per = (m + T - 1) / T;
-  const int q0 = b + t * per, q1 = min(e, q0 + per);
+  const int q0 = min(e, b + t * per), q1 = min(e, q0 + per);
   int below = 0, tied = 0;
   for (int q = q0; q < q1; ++q) {
     const int k = key_of(q);
@@ -329,9 +402,9 @@ __global__ void __launch_bounds__(1024) rcb_kernel(const int32_t* __restrict__ p
   {
     int k = tied_before;
     for (int q = q0; q < q1; ++q) {
-      const int key = key_of(q);
-      const bool in0 = (key < Ks) || (key == Ks && k < take);
-      if (key == Ks) ++k;
+      const int key_q = key_of(q);
+      const bool in0 = (key_q < Ks) || (key_q == Ks && k < take);
+      if (key_q == Ks) ++k;
       first += in0;
     }
   }
@@ -340,16 +413,59 @@ __global__ void __launch_bounds__(1024) rcb_kernel(const int32_t* __restrict__ p
   {
     int k = tied_before, i0 = b + first_before, i1 = b + m0 + (q0 - b - first_before);
     for (int q = q0; q < q1; ++q) {
-      const int key = key_of(q);
-      const bool in0 = (key < Ks) || (key == Ks && k < take);
-      if (key == Ks) ++k;
+      const int key_q = key_of(q);
+      const bool in0 = (key_q < Ks) || (key_q == Ks && k < take);
+      if (key_q == Ks) ++k;
       if (in0)
-        tmp[i0++] = ord[q];
+        Lout[i0++] = Lin[q];
       else
-        tmp[i1++] = ord[q];
+        Lout[i1++] = Lin[q];
     }
   }
   __syncthreads();
+}
+
+// One depth of the bisection: CTA c splits the part [parts[2c], parts[2c+1]) of `ord`.  Scratch
+// (n ints each, a CTA touching only its own nodes): tag, distP, distH, da, key; tmp (n ints);
+// hist (2m + 2 ints per part at 2 b + 2 c).  Tags carry the depth, so a stale tag of another
+// part never matches.
+__global__ void __launch_bounds__(1024) rcb_kernel(const int32_t* __restrict__ parts, int depth, int n,
+                                                   const int32_t* __restrict__ ptr, const int32_t* __restrict__ succ,
+                                                   const int32_t* __restrict__ cu, const int32_t* __restrict__ cv,
+                                                   int32_t* ord, int32_t* tmp, int32_t* hist_all, int32_t* tag,
+                                                   int32_t* distP, int32_t* distH, int32_t* da, int32_t* key) {
+  const int b = parts[2 * blockIdx.x], e = parts[2 * blockIdx.x + 1];
+  const int m = e - b, m0 = 64 * ((m + 127) / 128);
+  const int t = threadIdx.x, T = blockDim.x;
+  if (m0 >= m) return;
+  int32_t* hist = hist_all + 2 * b + 2 * blockIdx.x;
+  const int tag0 = ((depth + 1) << 22) | ((int)blockIdx.x << 2);  // | 0 whole part, | 1, | 2 halves
+  for (int q = b + t; q < e; q += T) tag[ord[q]] = tag0;
+  __syncthreads();
+  // peripheral node a and the part-local distance d_a
+  part_bfs(ptr, succ, ord, b, e, tag, tag0, ord[b], distP);
+  const Far fa = part_farthest(ord, b, e, distP);
+  part_bfs(ptr, succ, ord, b, e, tag, tag0, fa.node, da);
+  int best = 0, best_score = 0x7fffffff;
+  for (int cand = 0; cand < 4; ++cand) {
+    const int use = cand < 3 ? cand : best;  // the last pass applies the best key
+    for (int q = b + t; q < e; q += T) {
+      const int v = ord[q];
+      key[v] = use == 0 ? (cv[v] >= 0 ? cu[v] + n : -1) : use == 1 ? (cv[v] >= 0 ? cv[v] : -1) : da[v];
+    }
+    __syncthreads();
+    part_split(ord, tmp, b, e, m0, key, hist);
+    if (cand == 3) break;
+    for (int q = b + t; q < e; q += T) tag[tmp[q]] = tag0 | (q < b + m0 ? 1 : 2);
+    __syncthreads();
+    const int s1 = half_score(ptr, succ, tmp, b, b + m0, tag, tag0 | 1, distH);
+    const int s2 = half_score(ptr, succ, tmp, b + m0, e, tag, tag0 | 2, distH);
+    const int sc = max(s1, s2);
+    if (sc < best_score) {
+      best_score = sc;
+      best = cand;
+    }
+  }
   for (int q = b + t; q < e; q += T) ord[q] = tmp[q];
 }
 
@@ -411,7 +527,8 @@ cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
-  succ_fill_kernel<<<(h->n + 127) / 128, 128, 0, s>>>(h->dA, h->n, ptr, h->dSucc);
+  succ_fill_kernel<<<(h->n + 127) / 128, 128, 0, s>>>(h->dA, h->weighted ? h->dW : nullptr, h->n, ptr, h->dSucc,
+                                                      h->dSuccW);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }
@@ -433,14 +550,15 @@ cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, const int32_t* ord, 
                             unsigned long long* out, cudaStream_t s) {
   cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
-  chunk_spread_kernel<<<nsrc, 1024, 0, s>>>(h->dDeg + (h->n + 1), h->dSucc, h->n, nsrc, chunk, ord, dist, out);
+  chunk_spread_kernel<<<nsrc, 1024, 0, s>>>(h->dDeg + (h->n + 1), h->dSucc, h->weighted ? h->dSuccW : nullptr, h->n,
+                                            nsrc, chunk, ord, reinterpret_cast<float*>(dist), out);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }
 
 // Locality order of the split path: landmark coordinates (landmark_kernel), then recursive
-// coordinate bisection into parts of 64 consecutive positions (rcb_kernel), h->dOrd[position] =
-// node, h->dPos[node] = position.  The part boundaries depend on n alone, so the host lists them;
+// bisection into parts of 64 consecutive positions (rcb_kernel), h->dOrd[position] = node,
+// h->dPos[node] = position.  Scratch: 12 n ints of the N^2-int buffer dS (N >= 128, n <= N).  The part boundaries depend on n alone, so the host lists them;
 // one launch per depth.
 cudaError_t rd_locality_order(rd_ctx* h, cudaStream_t s) {
   const int n = h->n;
@@ -451,7 +569,10 @@ cudaError_t rd_locality_order(rd_ctx* h, cudaStream_t s) {
   int32_t* cu = w + 3 * (size_t)n;
   int32_t* cv = w + 4 * (size_t)n;
   int32_t* tmp = w + 5 * (size_t)n;
-  int32_t* dparts = w + 6 * (size_t)n;  // < 4 n / 64 + 4 ints
+  int32_t* dparts = w + 6 * (size_t)n;  // < 4 n / 64 + 4 ints, then the histograms (< 2 n + n / 16 + 2)
+  int32_t* tag = w + 9 * (size_t)n;
+  int32_t* da = w + 10 * (size_t)n;
+  int32_t* key = w + 11 * (size_t)n;
   std::vector<int32_t> all;             // every depth's list of parts to split, concatenated
   std::vector<std::pair<int, int>> depth_span;
   std::vector<std::pair<int, int>> cur{{0, n}};
@@ -486,9 +607,11 @@ cudaError_t rd_locality_order(rd_ctx* h, cudaStream_t s) {
   iota_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, h->dOrd);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
-  for (auto& d : depth_span) {
+  for (size_t dep = 0; dep < depth_span.size(); ++dep) {
+    const auto& d = depth_span[dep];
     if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
-    rcb_kernel<<<d.second, 1024, 0, s>>>(dparts + 2 * d.first, cu, cv, h->dOrd, tmp, hist);
+    rcb_kernel<<<d.second, 1024, 0, s>>>(dparts + 2 * d.first, (int)dep, n, h->dDeg + (n + 1), h->dSucc, cu, cv,
+                                         h->dOrd, tmp, hist, tag, d0, d1, da, key);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   }
@@ -513,3 +636,4 @@ cudaError_t rd_permute_m(rd_ctx* h, cudaStream_t s) {
   h->dT = t;
   return cudaSuccess;
 }
+

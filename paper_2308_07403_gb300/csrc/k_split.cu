@@ -13,8 +13,9 @@
 //     Every digit is an integer of at most 7 bits, exact in BF16.
 //   * For a chunk, the digit products of equal weight g = p + q (p, q < s, p + q < s) are
 //     summed by the tensor core into one FP32 accumulator in tensor memory: every product is
-//     an integer of magnitude <= 2^12 and a group holds at most s <= 15 of them per K entry,
-//     so a chunk sum stays below 256 * 15 * 2^12 < 2^24: exact.
+//     an integer of magnitude <= 2^12 and a group holds at most s of them per K entry, so a
+//     chunk sum stays below KAPPA * s * 2^12 < 2^24 -- exact -- for s <= 15 with 256-wide
+//     chunks and s <= 22 with 64-wide ones.
 //   * The epilogue warps read each group sum, scale it by 2^(eA + eB - 7 (g + 2)) relative to a
 //     per-entry reference exponent (the largest chunk scale eA + eB met so far; the accumulator
 //     is rebased by an exact power of two when it grows), and add it into a float-float (two
@@ -59,11 +60,19 @@ constexpr int EPI_WARPS = 8;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr int TILE_BYTES = TM * TK * 2;            // one 128 x 64 BF16 tile: 16 KiB
 constexpr int EXP_ZERO = -16384;                   // exponent of an all-zero chunk
-constexpr int MAX_SLICES = 15;                     // group sums exact: 256 * 15 * 2^12 < 2^24
+constexpr int MAX_SLICES_WIDE = 15;    // group sums exact: 256 * 15 * 2^12 < 2^24
+constexpr int MAX_SLICES_NARROW = 22;  // 64 * 22 * 2^12 < 2^24; group scale 2^(ACC_OFF - 7 (g + 2)) normal for g <= 21
+constexpr int ACC_OFF = 64;            // the float-float accumulators hold an entry times 2^(ACC_OFF - reference)
 constexpr int LEAF = RD_BF;                        // FP64 diagonal leaves (64)
 constexpr unsigned long long WAIT_NS = 4000000000ull;
 static_assert(SIGMA == RD_SPLIT_DIGIT_BITS && KAPPA_WIDE == RD_SCREEN_CHUNK && KAPPA_NARROW == RD_SCREEN_CHUNK_ORDERED,
               "range screen out of step with the digits");
+static_assert(MAX_SLICES_WIDE == RD_SPLIT_MAX && MAX_SLICES_NARROW == RD_SPLIT_MAX_ORDERED, "digit limits");
+static_assert((long long)KAPPA_WIDE * MAX_SLICES_WIDE * 4096 < (1 << 24) &&
+                  (long long)KAPPA_NARROW * MAX_SLICES_NARROW * 4096 < (1 << 24),
+              "group sums must stay exact in FP32");
+static_assert(ACC_OFF - SIGMA * (MAX_SLICES_NARROW + 1) >= -126 && ACC_OFF - 2 * SIGMA + 24 + 17 < 127,
+              "group scales normal, accumulators finite");
 
 constexpr uint32_t IDESC = (1u << 4)               // D: FP32
                            | (1u << 7)             // A: BF16
@@ -232,18 +241,26 @@ __device__ __forceinline__ void write_digits(double x, int e, int s, __nv_bfloat
     ex = 1;  // subnormal: no implicit bit
   else
     m |= (1ull << 52);
-  // F = round(|x| 2^(-e) 2^(7 s)) = m 2^(ex - 1075 - e + 7 s)
-  unsigned __int128 F = 0;
+  // F = round(|x| 2^(-e) 2^(7 s)) = m 2^(ex - 1075 - e + 7 s) < 2^(7 s - 1).  When the shift
+  // is a left shift, F = (m 2^(sh mod 7)) 128^z: its z lowest digits are zero (no carry), and
+  // the rest are the digits of m 2^(sh mod 7) < 2^59.  Otherwise F = round(m 2^sh) < 2^53.
+  uint64_t F = 0;
+  int z = 0;  // zero digits at the least significant end
   if (m != 0 && e != EXP_ZERO) {
     const int sh = ex - 1075 - e + SIGMA * s;
     if (sh >= 0) {
-      F = (unsigned __int128)m << sh;
+      z = sh / SIGMA;
+      F = m << (sh - SIGMA * z);
     } else if (sh > -64) {
       const uint64_t half = 1ull << (-sh - 1);  // round half up
-      F = ((unsigned __int128)m + half) >> (-sh);
+      F = (m + half) >> (-sh);              // m + half < 2^63
     }
   }
   for (int p = s - 1; p >= 1; --p) {
+    if (s - 1 - p < z) {
+      out[(long long)p * plane] = __float2bfloat16_rn(0.f);
+      continue;
+    }
     int d = (int)(uint32_t)(F & 127u);
     F >>= SIGMA;
     if (d >= 64) {
@@ -491,7 +508,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     // scale.  A term more than 2^-126 below its entry's reference underflows: the entry is at least
     // its largest chunk's real contribution, which the chunk spread bounds far above that.  Each
     // chunk's scale relative to the reference, S = 2^(eA + eB - ref), is kept in tensor memory, so
-    // a group term is G 2^(-7 (g + 2)) S.
+    // a group term is G 2^(-7 (g + 2)) S.  Both words carry an extra 2^ACC_OFF, so that the group
+    // scale stays a normal float up to 22 digits and an entry 2^-100 below its reference keeps
+    // its low digits; the final FP64 scaling takes it off.
     float hi[64];
     int16_t* rf = ref_s + (half * 64) * TM + lrow;  // rf[j * TM]
     const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);  // this warp's lanes
@@ -561,7 +580,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         tc_fence_after();
-        const float cg = __int_as_float((127 - SIGMA * (g + 2)) << 23);  // 2^(-7 (g + 2))
+        const float cg = __int_as_float((127 + ACC_OFF - SIGMA * (g + 2)) << 23);  // 2^(ACC_OFF - 7 (g + 2))
 #pragma unroll
         for (int t = 0; t < 8; ++t) {  // 8 columns at a time
           uint32_t gr[8], sr[8], lr[8];
@@ -604,7 +623,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int j = t * 8 + jj;
         const int col = n0 + half * 64 + j;
         if (row >= p.M || col >= p.N) continue;
-        double v = ldexp((double)hi[j] + (double)__uint_as_float(lr[jj]), (int)rf[j * TM]);
+        double v = ldexp((double)hi[j] + (double)__uint_as_float(lr[jj]), (int)rf[j * TM] - ACC_OFF);
         v = p.alpha * v;
         const long long orow = p.row_map ? p.row_map[row] : row;
         const long long ocol = p.col_map ? p.col_map[col] : col;
@@ -708,7 +727,7 @@ struct View {
 }  // namespace
 
 struct rd_split_plan {
-  int N = 0, s = 0;
+  int N = 0, s = 0, cap_s = 0;
   __nv_bfloat16* digA = nullptr;
   __nv_bfloat16* digB = nullptr;
   int* eA = nullptr;
@@ -927,21 +946,24 @@ __global__ void gather_uinv_rows_kernel(const double* __restrict__ T, long long 
 }  // namespace
 
 rd_status rd_split_prepare(rd_ctx* h, int s) {
-  if (s < 2 || s > MAX_SLICES) {
-    h->err = "split precision needs 2..15 digits (0 = chosen by the library)";
+  const int smax = h->ordered ? MAX_SLICES_NARROW : MAX_SLICES_WIDE;
+  if (s < 2 || s > smax) {
+    h->err = h->ordered ? "split precision needs 2..22 digits in the locality order"
+                        : "split precision needs 2..15 digits (0 = chosen by the library)";
     return RD_ERR_ARG;
   }
   if (!encode_fn()) {
     h->err = "cuTensorMapEncodeTiled is not available from the driver";
     return RD_ERR_UNSUPPORTED;
   }
-  if (!h->split || h->split->N != h->N) {
+  if (!h->split || h->split->N != h->N || h->split->cap_s < s) {
     rd_split_release(h);
     rd_split_plan* P = new rd_split_plan();
     h->split = P;
     P->N = h->N;
+    P->cap_s = s;  // digit planes sized for this count; a later escalation reallocates
     const size_t NK = (size_t)h->N * ((size_t)h->N + KAPPA_WIDE);  // rows x K padded to whole chunks
-    const size_t dig = (size_t)MAX_SLICES * NK * sizeof(__nv_bfloat16);
+    const size_t dig = (size_t)s * NK * sizeof(__nv_bfloat16);
     const size_t ex = (NK / KAPPA_NARROW + 64) * sizeof(int);  // exponents of the narrowest chunks
     cudaError_t e = cudaSuccess;
     auto get = [&](void** ptr, size_t bytes) {
@@ -997,10 +1019,11 @@ cudaError_t rd_split_row_check(rd_ctx* h, double* worst, cudaStream_t s) {
   const int k = h->n < RD_MAX_GOALS ? h->n : RD_MAX_GOALS;
   int32_t goals[RD_MAX_GOALS];
   for (int c = 0; c < k; ++c) goals[c] = (int32_t)(((long long)c * h->n) / k + (h->n / k) / 2);
-  cudaError_t e = cudaMemcpyAsync(h->dGoals, goals, k * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  // its own goal buffer: a goal solve has its caller's goals in dGoals while it factors
+  cudaError_t e = cudaMemcpyAsync(h->dCheckGoals, goals, k * sizeof(int32_t), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   double* rows = h->dS;  // free after the factorisation (64 x n doubles)
-  if ((e = rd_goal_split(h, h->dGoals, k, rows, s)) != cudaSuccess) return e;
+  if ((e = rd_goal_split(h, h->dCheckGoals, k, rows, s)) != cudaSuccess) return e;
   if (!h->succ_ready) {
     if ((e = rd_build_succ(h, s)) != cudaSuccess) return e;
     h->succ_ready = 1;
@@ -1009,7 +1032,7 @@ cudaError_t rd_split_row_check(rd_ctx* h, double* worst, cudaStream_t s) {
   if ((e = cudaMemsetAsync(res, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
   const long long total = (long long)k * h->n;
   if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
-  row_residual_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(rows, h->dGoals, k, h->n, h->dDeg + (h->n + 1),
+  row_residual_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(rows, h->dCheckGoals, k, h->n, h->dDeg + (h->n + 1),
                                                                        h->dSucc, h->dA, h->weighted ? h->dW : nullptr,
                                                                        h->gamma, res);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -77,7 +77,7 @@ void free_all(rd_ctx* h) {
     h->prof_ev = nullptr;
   }
   void* ptrs[] = {h->dA, h->dW, h->dLU, h->dT, h->dS, h->dR, h->dStatus, h->dRed, h->dDeg, h->dColsum,
-                  h->dSucc, h->dGoals, h->dNext, h->dYrows, h->dDout, h->dYout, h->dOrd, h->dPos};
+                  h->dSucc, h->dGoals, h->dNext, h->dYrows, h->dDout, h->dYout, h->dOrd, h->dPos, h->dCheckGoals, h->dYres, h->dSuccW};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : h->ev)
@@ -103,6 +103,25 @@ rd_status check_device_status(rd_ctx* h) {
   return fail(h, RD_ERR_ARG, buf);
 }
 
+// successor lists (and, for a weighted graph, their edge weights) for `edges` edges
+rd_status ensure_succ_capacity(rd_ctx* h, int64_t edges) {
+  const bool need_w = h->weighted && !h->dSuccW;
+  if (edges <= h->succ_cap && !need_w) return RD_OK;
+  const int64_t cap = edges > h->succ_cap ? edges + edges / 8 + 1024 : h->succ_cap;
+  if (h->dSucc) cudaFree(h->dSucc);
+  if (h->dSuccW) cudaFree(h->dSuccW);
+  h->bytes -= h->succ_cap * (int64_t)(sizeof(int32_t) + sizeof(float));
+  h->dSucc = nullptr;
+  h->dSuccW = nullptr;
+  h->succ_cap = 0;
+  h->succ_ready = 0;
+  if (cap > 2147483647ll) return RD_OK;  // no successor lists: the screen and the self-check step aside
+  RD_CK(h, dalloc(h, &h->dSucc, (size_t)cap));
+  RD_CK(h, dalloc(h, &h->dSuccW, (size_t)cap));
+  h->succ_cap = cap;
+  return RD_OK;
+}
+
 rd_status load_impl(rd_ctx* h, const uint8_t* A, const float* W, double gamma) {
   if (!A) return fail(h, RD_ERR_ARG, "A is NULL");
   if (!(gamma > 0.0 && gamma < 1.0) || !std::isfinite(gamma))
@@ -122,27 +141,20 @@ rd_status load_impl(rd_ctx* h, const uint8_t* A, const float* W, double gamma) {
   h->split_floor = 0;
   h->split_start = 0;
   h->screened = 0;
+  h->order_ready = 0;
   h->screen_bits = -1.0;
   h->ordered = 0;
   h->kappa = RD_SCREEN_CHUNK;
   h->succ_ready = 0;
+  h->y_current = h->updated = 0;
   RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 4 * sizeof(int), h->stream));
   RD_CK(h, rd_build_m(h, h->stream));
   unsigned long long red[3];
   RD_CK(h, cudaMemcpyAsync(red, h->dRed, sizeof(red), cudaMemcpyDeviceToHost, h->stream));
   RD_CK(h, cudaStreamSynchronize(h->stream));
-  if ((int64_t)red[2] > h->succ_cap) {
-    if (h->dSucc) {
-      cudaFree(h->dSucc);
-      h->bytes -= h->succ_cap * (int64_t)sizeof(int32_t);
-      h->dSucc = nullptr;
-      h->succ_cap = 0;
-    }
-    if (red[2] <= 2147483647ull) {
-      RD_CK(h, dalloc(h, &h->dSucc, (size_t)red[2]));
-      h->succ_cap = (int64_t)red[2];
-    }
-  }
+  h->n_edges = (int64_t)red[2];
+  const rd_status st = ensure_succ_capacity(h, h->n_edges);
+  if (st != RD_OK) return st;
   const double delta = (double)red[0];
   double colsum;
   memcpy(&colsum, &red[1], sizeof(double));
@@ -195,6 +207,7 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
   RD_ALLOC(h->dDeg, 2 * (size_t)n + 2);
   RD_ALLOC(h->dColsum, (size_t)n);
   RD_ALLOC(h->dGoals, RD_MAX_GOALS);
+  RD_ALLOC(h->dCheckGoals, RD_MAX_GOALS);
   RD_ALLOC(h->dOrd, (size_t)n);
   RD_ALLOC(h->dPos, (size_t)n);
 #undef RD_ALLOC
@@ -215,25 +228,43 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
   return RD_OK;
 }
 
-// Split mode with the self-check: after the inverse product, 64 sampled rows of Y (computed with
+// Split mode with the self-check: after the factorisation, 64 sampled rows of Y (computed with
 // the same digit products) must satisfy y^T M = e_g^T to RD_SPLIT_RESIDUAL per entry.  When the
 // caller leaves the digit count open, the library starts where the range screen says; a failed
-// check raises the floor of the current graph to RD_SPLIT_MAX digits, or moves it to FP64 when the
-// residual is far beyond what three more digits (21 bits) could close or RD_SPLIT_MAX digits
-// already failed.  The inverse is then recomputed from M.
+// check sets the next count from the residual (escalate) or moves the graph to FP64, and the
+// inverse is recomputed from M.
 bool split_auto(const rd_ctx* h) { return h->precision == RD_PREC_SPLIT_BF16 && h->slices_req == 0; }
 
-// hopeless: more digits cannot close the gap, go to FP64; otherwise try RD_SPLIT_MAX digits first.
-rd_status escalate(rd_ctx* h, bool hopeless) {
+// Each added digit carries 7 more bits of every operand chunk, so a residual r at s digits asks
+// for about log2(r / 2^-40) / 7 more digits to reach the 2^-40 of result the screen aims at (a
+// residual near 1, entries lost below the digits altogether, reads as at least 40 missing bits).
+// Beyond RD_SPLIT_MAX digits the natural order moves to the locality order (RD_SPLIT_MAX_ORDERED
+// at most); beyond that the graph runs in FP64.  The count grows by at least one digit per failure, so
+// the loop ends.
+rd_status escalate(rd_ctx* h, double worst) {
   h->fallbacks++;
-  h->split_floor = (!hopeless && h->slices < RD_SPLIT_MAX) ? RD_SPLIT_MAX : -1;
+  const int smax = h->ordered ? RD_SPLIT_MAX_ORDERED : RD_SPLIT_MAX;
+  const double missing = std::log2(worst > 0.0 ? worst : 1.0) + RD_SCREEN_RESULT_BITS;
+  int next = h->slices + (int)std::ceil(missing / RD_SPLIT_DIGIT_BITS);
+  if (next <= h->slices) next = h->slices + 1;
+  if (next > smax && !h->ordered && next <= RD_SPLIT_MAX_ORDERED && h->dSucc) {
+    // the natural order ran out of digits: the locality order's 64-wide chunks carry up to 22
+    if (!h->order_ready) {
+      RD_CK(h, rd_locality_order(h, h->stream));
+      h->order_ready = 1;
+    }
+    h->ordered = 1;
+    h->kappa = RD_SCREEN_CHUNK_ORDERED;
+    h->split_floor = next;
+  } else {
+    h->split_floor = next <= smax ? next : -1;
+  }
   RD_CK(h, rd_build_m(h, h->stream));  // M again (the factorisation overwrote it)
   h->factored = h->inverted = 0;
   return RD_OK;
 }
 
-// Range screen of the split path, run once per graph when the caller leaves the digit count open
-// (unweighted graphs).  The digits of a KAPPA-wide chunk of an operand row are scaled to the
+// Range screen of the split path, run once per graph when the caller leaves the digit count open.  The digits of a KAPPA-wide chunk of an operand row are scaled to the
 // chunk's largest entry, and the entries of Y fall by log2(1/gamma) bits per hop (Y_ij ~ gamma^d
 // for distance d), so a chunk whose nodes lie S hops apart as seen from one node costs about
 // S log2(1/gamma) of the 7 s bits the digits carry.  The largest S over the chunks, seen from 8
@@ -241,7 +272,9 @@ rd_status escalate(rd_ctx* h, bool hopeless) {
 // the spread plus RD_SCREEN_RESULT_BITS bits of result.  When the natural node order (256-wide
 // chunks) needs more than RD_SPLIT_START digits, the locality order (compact 64-node parts, see
 // rcb_kernel, 64-wide chunks) is screened too and taken when it needs fewer digits; beyond
-// RD_SPLIT_MAX digits the graph runs in FP64.  Large-diameter graphs (grids, meshes) are the ones
+// RD_SPLIT_MAX (natural) or RD_SPLIT_MAX_ORDERED (locality order) digits the graph runs in FP64.
+// On weighted graphs the spread is a weighted distance (Bellman-Ford on gamma^W's exponents),
+// scaled by RD_SCREEN_WEIGHTED.  Large-diameter graphs (grids, meshes) are the ones
 // that need the locality order: a 256-node run of their natural order spans a whole row of the
 // mesh.  The screen only steers: the residual self-check still judges every split result.
 double spread_bits(rd_ctx* h, const int32_t* ord, int chunk, rd_status* st) {
@@ -249,13 +282,16 @@ double spread_bits(rd_ctx* h, const int32_t* ord, int chunk, rd_status* st) {
   cudaError_t e = cudaMemsetAsync(h->dRed, 0, sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess)
     e = rd_chunk_spread(h, RD_SCREEN_SOURCES, chunk, ord, reinterpret_cast<int32_t*>(h->dS), h->dRed, h->stream);
-  unsigned long long spread = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&spread, h->dRed, sizeof(spread), cudaMemcpyDeviceToHost, h->stream);
+  unsigned long long bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, h->dRed, sizeof(bits), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     *st = fail_cuda(h, e, "range screen");
     return 0.0;
   }
+  const unsigned int fb = (unsigned int)bits;
+  float spread;
+  memcpy(&spread, &fb, sizeof(spread));
   return (double)spread * std::log2(1.0 / h->gamma);
 }
 
@@ -264,7 +300,7 @@ rd_status screen_split(rd_ctx* h) {
   h->screen_bits = -1.0;
   h->ordered = 0;
   h->kappa = RD_SCREEN_CHUNK;
-  if (h->weighted || !h->dSucc) return RD_OK;
+  if (!h->dSucc) return RD_OK;
   if (!h->succ_ready) {
     RD_CK(h, rd_build_succ(h, h->stream));
     h->succ_ready = 1;
@@ -274,7 +310,8 @@ rd_status screen_split(rd_ctx* h) {
     return s < RD_SPLIT_MIN ? RD_SPLIT_MIN : s;
   };
   rd_status st;
-  const double nat = spread_bits(h, nullptr, RD_SCREEN_CHUNK, &st);
+  const double wf = h->weighted ? RD_SCREEN_WEIGHTED : 1.0;
+  const double nat = wf * spread_bits(h, nullptr, RD_SCREEN_CHUNK, &st);
   if (st != RD_OK) return st;
   h->screen_bits = nat;
   const int s_nat = digits_for(nat);
@@ -283,10 +320,12 @@ rd_status screen_split(rd_ctx* h) {
     return RD_OK;
   }
   RD_CK(h, rd_locality_order(h, h->stream));
-  const double ord = spread_bits(h, h->dOrd, RD_SCREEN_CHUNK_ORDERED, &st);
+  h->order_ready = 1;
+  const double ord = wf * spread_bits(h, h->dOrd, RD_SCREEN_CHUNK_ORDERED, &st);
   if (st != RD_OK) return st;
   const int s_ord = digits_for(ord);
-  if (s_ord < s_nat && s_ord <= RD_SPLIT_MAX) {
+  // the locality order when it needs fewer digits, or when only it can carry more than 15
+  if (s_ord <= RD_SPLIT_MAX_ORDERED && (s_ord < s_nat || s_nat > RD_SPLIT_MAX)) {
     h->ordered = 1;
     h->kappa = RD_SCREEN_CHUNK_ORDERED;
     h->screen_bits = ord;
@@ -326,7 +365,18 @@ rd_status ensure_factored(rd_ctx* h) {
     h->used_precision = RD_PREC_SPLIT_BF16;
     h->factored = 1;
     h->inverted = 1;
-    break;  // the self-check runs on the result (rd_apsp)
+    if (split_auto(h)) {
+      // the self-check, before any product uses the inverses: sampled rows of Y against M
+      double worst = 0.0;
+      RD_CK(h, rd_split_row_check(h, &worst, h->stream));
+      h->last_residual = worst;
+      if (worst > RD_SPLIT_RESIDUAL) {
+        // failed: more digits as the residual asks, or FP64; the loop factors M again
+        if ((st = escalate(h, worst)) != RD_OK) return st;
+        continue;
+      }
+    }
+    break;
   }
   RD_CK(h, cudaEventRecord(h->ev[1], h->stream));
   h->ev_used[0] = 1;
@@ -449,9 +499,11 @@ rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices) {
     h->split_floor = 0;
     h->split_start = 0;
     h->screened = 0;
+    h->order_ready = 0;
     h->screen_bits = -1.0;
     h->ordered = 0;
     h->kappa = RD_SCREEN_CHUNK;
+    h->y_current = h->updated = 0;
     if (h->factored) {
       // the factors in dLU belong to the old mode: rebuild M from the resident graph
       RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 2 * sizeof(int), h->stream));
@@ -487,29 +539,104 @@ rd_status rd_apsp(rd_handle h, int32_t* D, double* Y) {
   int32_t* dD = d_host ? h->dDout : D;
   double* dY = Y ? (y_host ? h->dYout : Y) : nullptr;
   RD_CK(h, cudaEventRecord(h->ev[2], h->stream));
-  for (;;) {
-    if (h->used_precision == RD_PREC_SPLIT_BF16) {
-      RD_CK(h, rd_trmm_decode_split(h, dD, dY, h->stream));
-      if (!split_auto(h)) break;
-      double worst = 0.0;  // residual of sampled rows of Y against M
-      RD_CK(h, rd_split_row_check(h, &worst, h->stream));
-      h->last_residual = worst;
-      if (worst <= RD_SPLIT_RESIDUAL) break;
-      // the result failed: with a residual far beyond what three more digits (21 bits) could
-      // close, go straight to FP64
-      if ((st = escalate(h, worst > 1e-3)) != RD_OK) return st;
-      if ((st = ensure_factored(h)) != RD_OK) return st;
-      continue;
-    }
+  if (h->updated && h->y_current) {  // edges changed since the factorisation: Y is the resident one
+    unsigned int* lost = reinterpret_cast<unsigned int*>(h->dRed);
+    RD_CK(h, rd_rank1_update(h, 0, 0, 0.0, dD, lost, h->stream));  // alpha = 0: decode only
+    if (dY) RD_CK(h, cudaMemcpyAsync(dY, h->dYres, nn * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  } else if (h->used_precision == RD_PREC_SPLIT_BF16) {
+    RD_CK(h, rd_trmm_decode_split(h, dD, dY, h->stream));
+  } else {
     if (!h->inverted) RD_CK(h, rd_trtri_f64(h, h->stream));
     h->inverted = 1;
     RD_CK(h, rd_trmm_decode_f64(h, dD, dY, h->stream));
-    break;
   }
   RD_CK(h, cudaEventRecord(h->ev[3], h->stream));
   h->ev_used[1] = 1;
   if (d_host) RD_CK(h, cudaMemcpyAsync(D, dD, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   if (y_host) RD_CK(h, cudaMemcpyAsync(Y, dY, nn * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (d_host || y_host) return check_device_status(h);
+  return RD_OK;
+}
+
+namespace {
+// Y (resident) and D of the current factors: the inverse product into dYres
+rd_status materialize_y(rd_ctx* h, int32_t* dD) {
+  const size_t nn = (size_t)h->n * (size_t)h->n;
+  if (!h->dYres) RD_CK(h, dalloc(h, &h->dYres, nn));
+  rd_status st = ensure_factored(h);
+  if (st != RD_OK) return st;
+  if (h->used_precision == RD_PREC_SPLIT_BF16) {
+    RD_CK(h, rd_trmm_decode_split(h, dD, h->dYres, h->stream));
+  } else {
+    if (!h->inverted) RD_CK(h, rd_trtri_f64(h, h->stream));
+    h->inverted = 1;
+    RD_CK(h, rd_trmm_decode_f64(h, dD, h->dYres, h->stream));
+  }
+  h->y_current = 1;
+  h->updated = 0;
+  return RD_OK;
+}
+}  // namespace
+
+rd_status rd_update_edge(rd_handle h, int32_t i, int32_t j, int32_t present, float w, int32_t* D, double* Y) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  if (!D) return fail(h, RD_ERR_ARG, "D is NULL");
+  if (i < 0 || j < 0 || i >= h->n || j >= h->n) return fail(h, RD_ERR_ARG, "node index out of range");
+  if (present && h->weighted && !(w > 0.f && std::isfinite(w)))
+    return fail(h, RD_ERR_ARG, "an edge weight must be positive and finite");
+  if (is_foreign_device_ptr(D, h->device) || (Y && is_foreign_device_ptr(Y, h->device)))
+    return fail(h, RD_ERR_ARG, "output lives on another device");
+  RD_CK(h, cudaSetDevice(h->device));
+  const size_t nn = (size_t)h->n * (size_t)h->n;
+  const bool d_host = !is_device_ptr(D, h->device);
+  const bool y_host = Y && !is_device_ptr(Y, h->device);
+  if (d_host && !h->dDout) RD_CK(h, dalloc(h, &h->dDout, nn));
+  int32_t* dD = d_host ? h->dDout : D;
+  // the entry now, the entry wanted, and column j's sum afterwards (the gain condition)
+  const long long at = (long long)i * h->n + j;
+  uint8_t a_old = 0;
+  float w_old = 0.f;
+  double colsum = 0.0;
+  RD_CK(h, cudaMemcpyAsync(&a_old, h->dA + at, 1, cudaMemcpyDeviceToHost, h->stream));
+  if (h->weighted) RD_CK(h, cudaMemcpyAsync(&w_old, h->dW + at, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  RD_CK(h, cudaMemcpyAsync(&colsum, h->dColsum + j, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  RD_CK(h, cudaStreamSynchronize(h->stream));
+  const double x_old = a_old ? (h->weighted ? std::pow(h->gamma, (double)w_old) : h->gamma) : 0.0;
+  const double x_new = present ? (h->weighted ? std::pow(h->gamma, (double)w) : h->gamma) : 0.0;
+  const double delta = x_new - x_old;
+  if (!(colsum + delta < 1.0)) return fail(h, RD_ERR_GAMMA, "the update would make a column sum of X reach 1");
+  rd_status st;
+  if (!h->y_current && (st = materialize_y(h, dD)) != RD_OK) return st;
+  unsigned int* lost = reinterpret_cast<unsigned int*>(h->dRed);
+  if (delta != 0.0 || (a_old != 0) != (present != 0) || (present && w != w_old)) {
+    const int ddeg = (present ? 1 : 0) - (a_old ? 1 : 0);
+    h->n_edges += ddeg;
+    if ((st = ensure_succ_capacity(h, h->n_edges)) != RD_OK) return st;
+    RD_CK(h, rd_set_edge(h, i, j, present ? 1 : 0, present ? w : 0.f, delta, ddeg, h->stream));
+    h->succ_ready = 0;
+    h->edge_updates++;
+  }
+  RD_CK(h, rd_rank1_update(h, i, j, delta, dD, lost, h->stream));
+  unsigned int nlost = 0;
+  RD_CK(h, cudaMemcpyAsync(&nlost, lost, sizeof(nlost), cudaMemcpyDeviceToHost, h->stream));
+  RD_CK(h, cudaStreamSynchronize(h->stream));
+  if (delta != 0.0) h->updated = 1;
+  if (nlost) {
+    // a removal cancelled some entries: factor the updated graph from scratch
+    h->update_refactors++;
+    RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 2 * sizeof(int), h->stream));
+    RD_CK(h, rd_build_m(h, h->stream));
+    h->factored = h->inverted = 0;
+    h->split_floor = h->split_start = 0;
+    h->screened = 0;
+    h->order_ready = 0;
+    h->screen_bits = -1.0;
+    h->ordered = 0;
+    h->kappa = RD_SCREEN_CHUNK;
+    if ((st = materialize_y(h, dD)) != RD_OK) return st;
+  }
+  if (Y) RD_CK(h, cudaMemcpyAsync(Y, h->dYres, nn * sizeof(double), cudaMemcpyDefault, h->stream));
+  if (d_host) RD_CK(h, cudaMemcpyAsync(D, dD, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   if (d_host || y_host) return check_device_status(h);
   return RD_OK;
 }
@@ -526,7 +653,9 @@ rd_status rd_goal_solve(rd_handle h, const int32_t* goals, int32_t k, double* Y_
   if (host && !h->dYrows) RD_CK(h, dalloc(h, &h->dYrows, (size_t)RD_MAX_GOALS * h->n));
   double* dst = host ? h->dYrows : Y_out;
   RD_CK(h, cudaEventRecord(h->ev[4], h->stream));
-  if (h->used_precision == RD_PREC_SPLIT_BF16 && h->inverted)
+  if (h->updated && h->y_current)
+    RD_CK(h, rd_rows_from_y(h, h->dGoals, k, dst, h->stream));  // the factors predate the edge updates
+  else if (h->used_precision == RD_PREC_SPLIT_BF16 && h->inverted)
     RD_CK(h, rd_goal_split(h, h->dGoals, k, dst, h->stream));  // rows of U^-1 times L^-1
   else
     RD_CK(h, rd_goal_f64(h, h->dGoals, k, dst, h->stream));
@@ -589,6 +718,8 @@ rd_status rd_get_stats(rd_handle h, rd_stats* s) {
   s->split_residual = h->last_residual;
   s->split_screen_bits = h->screen_bits;
   s->split_order = h->ordered;
+  s->edge_updates = h->edge_updates;
+  s->update_refactors = h->update_refactors;
   s->gamma = h->gamma;
   s->max_column_sum = h->max_colsum;
   s->tau = h->tau;

@@ -29,12 +29,22 @@
 #define RD_DEV_TIMEOUT 3    // a bounded wait expired
 #define RD_SPLIT_START 12   // digit count of an unscreened graph (weighted) when the caller leaves it open
 #define RD_SPLIT_MIN 8      // fewest digits the range screen picks
-#define RD_SPLIT_MAX 15     // largest digit count (exact group sums)
+#define RD_SPLIT_MAX 15     // largest digit count in the natural order (exact group sums, 256-wide chunks)
+#define RD_SPLIT_MAX_ORDERED 22  // the same in the locality order (64-wide chunks)
 #define RD_SPLIT_DIGIT_BITS 7  // bits per digit of the split operands
 #define RD_SCREEN_SOURCES 8  // BFS sources of the split path's range screen
 #define RD_SCREEN_CHUNK 256  // operand chunk along K that shares one scale (the split path's KAPPA)
 #define RD_SCREEN_CHUNK_ORDERED 64  // the same with the locality order
 #define RD_SCREEN_RESULT_BITS 40  // bits the digits must keep below a chunk's spread (2^-40 ~ 1e-12)
+// Weighted graphs: the operands of the inverse products are path sums restricted to the
+// elimination order, and with unequal edge weights those restricted paths can cost more than the
+// true shortest paths that the weighted spread samples.  The largest operand-chunk scale over a
+// result entry, against the sampled spread, measured 1.05x on a dense random graph with
+// log-uniform weights in [1, 100] at gamma = 1e-7 (natural order) and 0.91x on a king-move grid
+// with weights in [1, 4] in the locality order.  The screen scales a weighted spread by
+// RD_SCREEN_WEIGHTED; a shortfall shows in the self-check's residual, which then sets the next
+// digit count.
+#define RD_SCREEN_WEIGHTED 1.1
 
 struct rd_split_plan;       // defined by the split path
 
@@ -43,6 +53,7 @@ struct rd_ctx {
   int32_t n = 0, N = 0;
   double gamma = 0.0, tau = 1e-9, max_colsum = 0.0;
   int weighted = 0;
+  int order_ready = 0;  // h->dOrd / h->dPos hold the locality order of the resident graph
   int precision = RD_PREC_FP64;
   int slices_req = 0, slices = 0;
   cudaStream_t stream = nullptr;
@@ -58,15 +69,22 @@ struct rd_ctx {
   int32_t* dDeg = nullptr;     // n+1: out-degree, then exclusive prefix (successor CSR ptr)
   double* dColsum = nullptr;   // n: column sums of X (gain check)
   int32_t* dSucc = nullptr;    // successor CSR indices
+  float* dSuccW = nullptr;     // weighted graphs: the weight of each successor edge (same layout)
   int64_t succ_cap = 0;
+  int64_t n_edges = 0;         // edges of the current graph (A_ij != 0)
   int succ_ready = 0;
   int32_t* dGoals = nullptr;   // RD_MAX_GOALS
+  int32_t* dCheckGoals = nullptr;  // RD_MAX_GOALS: rows of the split path's self-check
   int32_t* dOrd = nullptr;     // n: locality order of the split path, node at each position
   int32_t* dPos = nullptr;     // n: its inverse, position of each node
   int32_t* dNext = nullptr;    // staging for host next-hop output (k x n)
   double* dYrows = nullptr;    // staging for host goal rows (k x n)
   int32_t* dDout = nullptr;    // staging for host D output (n x n), lazy
   double* dYout = nullptr;     // staging for host Y output (n x n), lazy
+  double* dYres = nullptr;     // resident Y for incremental edge updates (n x n), lazy
+  int y_current = 0;           // dYres holds the current graph's Y
+  int updated = 0;             // edges changed since the factorisation: goal rows come from dYres
+  int64_t edge_updates = 0, update_refactors = 0;
 
   int factored = 0;            // dLU holds the factors of the current graph
   int inverted = 0;            // dT holds the triangular inverses
@@ -75,6 +93,7 @@ struct rd_ctx {
   int split_start = 0;         // per graph: digit count picked by the range screen (0: none)
   int screened = 0;            // the range screen ran for the current graph and mode
   double screen_bits = -1.0;   // its estimate of the bits a chunk's spread costs (-1: not screened)
+  double screen_per_hop = 1.0; // weight factor of a hop in that estimate (largest W; 1 unweighted)
   int ordered = 0;             // the split path runs on P M P^T with the locality order (dOrd)
   int kappa = 256;             // chunk width of the split digits: 256, or 64 with the locality order
   int fallbacks = 0;           // split results redone (more digits or FP64) after the self-check
@@ -148,9 +167,10 @@ cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cud
 // ---- kernels in k_build.cu ----------------------------------------------------------------
 cudaError_t rd_build_m(rd_ctx* h, cudaStream_t s);       // M into dLU, degrees, column sums
 cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s);    // successor CSR from dA
-// largest hop spread within chunks of `chunk` consecutive positions (node at position q: ord[q],
-// or q when ord is null), BFS from nsrc sampled sources (needs the successor lists; dist: nsrc * n
-// ints of scratch) -> atomicMax into *out
+// largest spread of the distance from nsrc sampled sources within chunks of `chunk` consecutive
+// positions (node at position q: ord[q], or q when ord is null): hop counts (BFS), or weighted
+// distances (Bellman-Ford on dSuccW) for a weighted graph; needs the successor lists; dist: nsrc * n
+// words of scratch.  atomicMax of the spread's float bits into *out
 cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, const int32_t* ord, int32_t* dist,
                             unsigned long long* out, cudaStream_t s);
 // locality order for the split path (dOrd, dPos; uses dS as scratch; synchronises once)
@@ -165,6 +185,15 @@ cudaError_t rd_lu_f64(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_trtri_f64(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_lu_diag(rd_ctx* h, int k0, cudaStream_t s);   // diag LU + its inverses
 cudaError_t rd_trmm_decode_f64(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s);
+
+// ---- incremental edge updates (k_update.cu) ----------------------------------------------------
+// Y <- Y + alpha Y e_i e_j^T Y with D decoded in the same pass; *lost counts cancelled entries
+cudaError_t rd_rank1_update(rd_ctx* h, int i, int j, double delta, int32_t* D, unsigned int* lost, cudaStream_t s);
+// A_ij (and W_ij), column sum j += delta and out-degree j += ddeg, on the device
+cudaError_t rd_set_edge(rd_ctx* h, int i, int j, uint8_t present, float w, double delta, int ddeg,
+                        cudaStream_t s);
+// rows goals[c] of the resident Y
+cudaError_t rd_rows_from_y(rd_ctx* h, const int32_t* dgoals, int k, double* out, cudaStream_t s);
 
 // ---- goals (k_goal.cu) ---------------------------------------------------------------------
 cudaError_t rd_goal_f64(rd_ctx* h, const int32_t* dgoals, int k, double* out, cudaStream_t s);

@@ -23,6 +23,7 @@ Workload recipes (seeds are ``SEED_BASE + config_index * 1000 + replica``):
                 undirected (symmetric A).
   * ``grid8w``  8-neighbour (king-move) grid with independent per-directed-edge weights
                 uniform in [wlo, whi] (float32).
+  * ``er_weighted``  directed Erdos-Renyi with per-edge weights log-uniform in [wlo, whi].
 plus small deterministic families used as closed-form pins (directed path, directed cycle,
 complete graph, binary tree, the three-node path of Example 4.1).
 """
@@ -98,6 +99,20 @@ def grid8_weighted(rows: int, cols: int, seed: int, wlo: float = 1.0, whi: float
     W = np.zeros((n, n), dtype=np.float32)
     ii, jj = np.nonzero(A)
     W[ii, jj] = rng.uniform(wlo, whi, size=ii.size).astype(np.float32)
+    return A, W
+
+
+def er_weighted(n: int, p: float, seed: int, wlo: float = 1.0, whi: float = 100.0):
+    """Directed G(n, p) with per-edge weights log-uniform in [wlo, whi] (float32): the weighted
+    graph family of the paper's Sec. 5 experiment (Fig. 3: p = 0.5, weights 1 to 100).
+
+    Returns (A, W); W is 0 where there is no edge.
+    """
+    A = er(n, p, seed)
+    rng = np.random.default_rng(seed + 1)
+    W = np.zeros((n, n), dtype=np.float32)
+    ii, jj = np.nonzero(A)
+    W[ii, jj] = np.exp(rng.uniform(np.log(wlo), np.log(whi), size=ii.size)).astype(np.float32)
     return A, W
 
 
@@ -277,3 +292,28 @@ def serving_pool(count: int = 128, n_lo: int = 64, n_hi: int = 4096, replica: in
             A = ws(n, 10, 0.1, s)
         out.append((A, gamma_small(A)))
     return out
+
+
+def gamma_weighted_bound(A: np.ndarray, W: np.ndarray) -> float:
+    """Largest gain with max_j sum_i gamma^W_ij <= 1 over the edges (the weighted extension's
+    counterpart of 1/Delta: strict column diagonal dominance of M = I - gamma^W), by bisection."""
+    ii, jj = np.nonzero(A)
+    w = W[ii, jj].astype(np.float64)
+    n = A.shape[0]
+    lo, hi = 0.0, 1.0
+    for _ in range(80):
+        g = 0.5 * (lo + hi)
+        col = np.bincount(jj, weights=np.power(g, w), minlength=n)
+        if col.max() <= 1.0:
+            lo = g
+        else:
+            hi = g
+    return lo
+
+
+def workload_weighted(rows: int = 128, cols: int = 256, frac: float = 0.9, replica: int = 0):
+    """Weighted local navigation: a rows x cols king-move grid (n = rows cols; 128 x 256 = 32768)
+    with per-directed-edge weights uniform in [1, 4] (float32), gain frac x the weighted bound.
+    Returns (A, W, gamma)."""
+    A, W = grid8_weighted(rows, cols, seed_for(4, replica))
+    return A, W, frac * gamma_weighted_bound(A, W)

@@ -52,6 +52,7 @@ _SIGS = {
     "rd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rd_destroy": (None, [_P]),
     "rd_apsp_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, _P, _P]),
+    "rd_update_edge": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P, _P]),
     "rd_batch_create": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(_P)]),
     "rd_batch_offsets": (ctypes.c_int, [_P, _P]),
     "rd_batch_apsp": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -82,6 +83,7 @@ class rd_stats(ctypes.Structure):
         ("prof_split_launches", ctypes.c_int64), ("prof_split_ms", ctypes.c_double),
         ("prof_split_flops", ctypes.c_double),
         ("split_order", ctypes.c_int32),
+        ("edge_updates", ctypes.c_int64), ("update_refactors", ctypes.c_int64),
     ]
 
 
@@ -226,6 +228,15 @@ def rd_destroy(h):
         load().rd_destroy(h)
 
 
+def rd_update_edge(h, i: int, j: int, present: bool, w: float, D, Y=None):
+    """Edge j -> i present (weight w) or absent; D (and Y) of the changed graph."""
+    _np_out(D)
+    _np_out(Y)
+    pd, kd = _ptr(D)
+    py, ky = _ptr(Y)
+    _check(load().rd_update_edge(h, int(i), int(j), 1 if present else 0, float(w), pd, py), h)
+
+
 def rd_apsp_noalloc(A, n: int, gamma: float, D, stream_ptr: int = 0):
     """APSP without any device allocation (device A and D, n <= NOALLOC_MAX_N)."""
     pa, ka = _ptr(A)
@@ -253,6 +264,10 @@ class Handle:
 
     def apsp(self, D, Y=None):
         rd_apsp(self.h, D, Y)
+        return D
+
+    def update_edge(self, i, j, present, D, Y=None, w=1.0):
+        rd_update_edge(self.h, i, j, present, w, D, Y)
         return D
 
     def goal_solve(self, goals, Y_out):

@@ -124,24 +124,89 @@ def test_split_rejects_bad_slice_counts(rd):
         assert np.array_equal(D, oracle.rdistance(A, g))
 
 
+def isolated_sources_path(n=200):
+    """A directed path through every node but the range screen's 8 BFS sources (b n / 8 + n / 16),
+    which are left isolated: every sampled BFS reaches nothing, so the screen sees no spread."""
+    srcs = {(b * n) // 8 + (n // 8) // 2 for b in range(8)}
+    chain = [v for v in range(n) if v not in srcs]
+    A = np.zeros((n, n), np.uint8)
+    for u, v in zip(chain, chain[1:]):
+        A[v, u] = 1  # edge u -> v
+    return A
+
+
 def test_self_check_falls_back_to_fp64(rd):
-    """A directed path at a small gain spans 2^-600 within one 256-chunk: the far entries of Y
-    are lost to the digit truncation.  Given as a weighted graph (unit weights: the same X) it
-    skips the range screen, so the residual of the sampled rows against M must expose the loss;
-    the library then recomputes the graph in FP64 -- D stays exact."""
-    A, g = graphs.directed_path(200), 0.125
-    W = A.astype(np.float32)
+    """A graph the screen misreads: a 192-node directed path at gain 0.125 spans 2^-573 within one
+    256-node chunk, but the screen's sampled sources are isolated, so it picks 8 digits.  The far
+    entries of Y are lost to the digit truncation, the residual of the sampled rows against M
+    exposes it, and the library recomputes the graph in FP64 -- D stays exact."""
+    A, g = isolated_sources_path(), 0.125
     Do = oracle.rdistance(A, g)
-    n = A.shape[0]
-    D = np.empty((n, n), np.int32)
-    with rd.Handle(A, g, W=W) as h:
-        h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
-        h.apsp(D)
-        st = h.stats()
-    assert st["split_screen_bits"] == -1.0
+    Dg, _, st = run(rd, A, g, want_y=False)
+    assert st["split_screen_bits"] == 0.0
     assert st["precision_used"] == rd.RD_PREC_FP64 and st["fallbacks"] >= 1
     assert st["split_residual"] > 1e-9
+    assert np.array_equal(Dg, Do)
+
+
+def weighted_split(rd, A, W, g, goals):
+    """Goal rows, greedy next hops and the whole D / Y of a weighted graph with the digit count
+    left to the library; returns the handle's stats and the outputs."""
+    n = A.shape[0]
+    D = np.empty((n, n), np.int32)
+    Y = np.empty((n, n))
+    rows = np.empty((goals.size, n))
+    nxt = np.empty((goals.size, n), np.int32)
+    with rd.Handle(A, g, W=W) as h:
+        h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
+        h.goal_solve(goals, rows)
+        h.greedy_next(goals, rows, nxt)
+        h.apsp(D, Y)
+        st = h.stats()
+    return st, D, Y, rows, nxt
+
+
+def check_weighted(A, W, g, goals, D, Y, rows, nxt):
+    Do, Yo = oracle.rdistance(A, g, W=W, want_y=True)
+    assert rel_err(Y, Yo) < YTOL
     assert np.array_equal(D, Do)
+    assert rel_err(rows, Yo[goals]) < YTOL
+    assert np.array_equal(nxt, oracle.greedy_next(A, goals, rows))
+
+
+@pytest.mark.parametrize("frac", [0.9, 0.5])
+def test_weighted_king_grid(rd, frac):
+    """Weighted extension (X = gamma^W, Sec. 3.3) on the split path: a 24 x 32 king-move grid with
+    weights uniform in [1, 4] at frac x the weighted gain bound (about 2.2 and 3.0 bits of Y per
+    unit of weight).  A 256-node run of the natural order spans 8 rows of the grid, so the screen
+    takes the locality order (64-node parts, 64-wide chunks); at 0.5 it needs more than 15 digits,
+    which only the locality order's chunks carry exactly (up to 22).  The result matches the
+    oracle: Y within 1e-10, D exact, goal rows and greedy next hops equal."""
+    A, W, gb = graphs.workload_weighted(24, 32, frac=1.0)
+    g = frac * gb
+    goals = np.array([0, 100, 383, 767], np.int32)
+    st, D, Y, rows, nxt = weighted_split(rd, A, W, g, goals)
+    assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16 and st["split_order"] == 1, st
+    assert st["fallbacks"] <= 1 and 0 < st["split_residual"] < 1e-9, st
+    if frac == 0.5:
+        assert st["slices"] > 15, st
+    check_weighted(A, W, g, goals, D, Y, rows, nxt)
+
+
+@pytest.mark.parametrize("gamma", ["0.9 bound", "1e-7"])
+def test_weighted_dense_random(rd, gamma):
+    """The paper's weighted family (Sec. 5, Fig. 3: G(n, 0.5) with weights log-uniform in
+    [1, 100]) at n = 768, at 0.9 x the weighted gain bound (Y spans about 11 bits: the screen's
+    fewest digits, natural order) and at the paper's gamma = 1e-7 (Y spans about 70 bits: more
+    than 12 digits, so the locality order's 64-wide chunks).  Split result, oracle parity."""
+    A, W = graphs.er_weighted(768, 0.5, graphs.seed_for(4, 7))
+    g = 0.9 * graphs.gamma_weighted_bound(A, W) if gamma == "0.9 bound" else 1e-7
+    goals = np.array([3, 200, 511, 766], np.int32)
+    st, D, Y, rows, nxt = weighted_split(rd, A, W, g, goals)
+    assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16 and 0 < st["split_residual"] < 1e-9, st
+    if gamma == "0.9 bound":
+        assert st["slices"] <= 9 and st["split_order"] == 0, st
+    check_weighted(A, W, g, goals, D, Y, rows, nxt)
 
 
 def screen_spread(A):
@@ -162,7 +227,7 @@ def screen_spread(A):
 
 
 SCREEN_CASES = {  # (graph, gain): the branch follows from spread x log2(1/gamma)
-    "grid1000x40": lambda: (graphs.grid4(1000, 40), None),   # ~95 bits: FP64
+    "grid1000x40": lambda: (graphs.grid4(1000, 40), None),   # ~95 bits natural: locality order
     "grid600x16": lambda: (graphs.grid4(600, 16), None),     # ~65 bits: 15 digits
     "dpath300_g0.85": lambda: (graphs.directed_path(300), 0.85),  # ~56 bits: 15 digits
     "dpath300_g0.9": lambda: (graphs.directed_path(300), 0.9),    # ~36 bits: 12 digits
@@ -195,13 +260,14 @@ def test_range_screen_matches_bfs(rd, name):
         assert st["split_screen_bits"] == pytest.approx(bits, rel=1e-12, abs=0.0)
         want = screen_digits(bits)
     elif st["split_order"] == 1:
-        # the locality order was taken: it must need fewer digits than the natural order
-        assert screen_digits(st["split_screen_bits"]) < screen_digits(bits)
+        # the locality order was taken: it needs fewer digits than the natural order, or the
+        # natural order needs more than its 15 (the locality order carries up to 22)
         want = screen_digits(st["split_screen_bits"])
+        assert want <= 22 and (want < screen_digits(bits) or screen_digits(bits) > 15)
     else:
         assert st["split_screen_bits"] == pytest.approx(bits, rel=1e-12, abs=0.0)
         want = screen_digits(bits)
-    if want > 15:
+    if st["split_order"] == 0 and want > 15:
         assert st["precision_used"] == rd.RD_PREC_FP64 and st["fallbacks"] == 0
     elif st["fallbacks"] == 0:
         assert st["precision_used"] == rd.RD_PREC_SPLIT_BF16 and st["slices"] == want
