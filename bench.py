@@ -53,10 +53,12 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--verify", type=int, default=1, help="hash D of every graph against the oracle's")
     p.add_argument("--cpu-sample", type=int, default=1536, help="oracle sample size (leading block)")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "serving", "weighted"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "serving", "weighted", "update"],
                    help="single: the n=8192 graphs (default); batched: 4096 graphs n~U[32,512] in one launch; "
                         "serving: a Poisson stream of requests over a pool of graphs; "
-                        "weighted: n=32768 king grid, split inverse + 1024 goal rows + greedy")
+                        "weighted: n=32768 king grid, split inverse + 1024 goal rows + greedy; "
+                        "update: edge removals and restores on the n=8192 grid (Sherman-Morrison)")
+    p.add_argument("--obstacles", type=int, default=64, help="update: edge pairs removed, then restored")
     p.add_argument("--weighted-rows", type=int, default=128)
     p.add_argument("--weighted-cols", type=int, default=256)
     p.add_argument("--batch-graphs", type=int, default=4096)
@@ -297,7 +299,7 @@ def verify_graphs(rd, h, wl, A_dev, modes, args, other, D, dev):
                 rec["split"] = {"precision_used": "split" if sg["precision_used"] else "fp64",
                                 "digits": sg["slices"] if sg["precision_used"] else None,
                                 "screen_bits": round(sg["split_screen_bits"], 1),
-                                "locality_order": bool(sg["split_order"]),
+                                "locality_order": ["none", "landmark", "scored"][sg["split_order"]],
                                 "sampled_row_residual": sg["split_residual"] if sg["precision_used"] else None,
                                 "redone_by_self_check": bool(redone)}
             if nm == args.precision:
@@ -654,7 +656,7 @@ def run_weighted(args):
                    "n": n, "gamma": g, "goals": G},
         "factor_and_first_goals_ms": t_first, "ms_factor": st["ms_factor"],
         "precision_used": "split" if st["precision_used"] else "fp64", "digits": st["slices"],
-        "locality_order": bool(st["split_order"]), "screen_bits": st["split_screen_bits"],
+        "locality_order": ["none", "landmark", "scored"][st["split_order"]], "screen_bits": st["split_screen_bits"],
         "sampled_row_residual": st["split_residual"], "fallbacks": st["fallbacks"],
         "greedy_on_shortest_path_fraction": ok / max(1, checked), "greedy_moves_checked": checked,
         "goal_row_entries_underflowed": underflow, "dijkstra_cpu_s": t_dij,
@@ -666,8 +668,139 @@ def run_weighted(args):
     print(json.dumps(line), flush=True)
 
 
+UPDATE_METRIC = ("incremental edge update, n=8192 grid 90x91 at 0.9/Delta: wall ms per update "
+                 "(rank-1 update of the resident Y + decode of D)")
+
+
+def run_update(args):
+    """Incremental edge updates (the map changing under a robot, Sec. 6): on the 90 x 91 grid at
+    0.9/Delta with Y resident, `--obstacles` edge pairs (both directions of a grid edge) are removed
+    one direction per update, then restored.  Each update is one rd_update_edge call into a device
+    D.  Checks: after the removals D equals a fresh FP64 factorisation of the changed graph, after
+    the restores D equals the original D."""
+    import torch
+
+    from paper_2308_07403_gb300 import build, graphs, rd
+
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
+        return
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    rd.load()
+    A, g = graphs.workload_large("grid", 0.9)
+    n = A.shape[0]
+    rng = np.random.default_rng(graphs.seed_for(5))
+    ii, jj = np.nonzero(np.triu(A, 1))  # undirected grid edges {i, j}, i < j
+    pick = rng.choice(ii.size, size=args.obstacles, replace=False)
+    pairs = [(int(ii[p]), int(jj[p])) for p in pick]
+    stream = torch.cuda.current_stream(dev)
+    A_dev = torch.from_numpy(A).to(dev)
+    D = torch.empty((n, n), dtype=torch.int32, device=dev)
+    D0 = torch.empty((n, n), dtype=torch.int32, device=dev)
+    h = rd.rd_create(A_dev, n, g)
+    rd.rd_set_stream(h, stream.cuda_stream)
+    rd.rd_set_precision(h, rd.RD_PREC_SPLIT_BF16, 0)
+    rd.rd_apsp(h, D0, None)
+    # warm-up: one removal and its restore (materialises the resident Y), untimed
+    i0, j0 = pairs[0]
+    rd.rd_update_edge(h, i0, j0, False, 1.0, D)
+    rd.rd_update_edge(h, i0, j0, True, 1.0, D)
+    torch.cuda.synchronize()
+    rd.rd_set_profiling(h, True)
+    st0 = rd.rd_get_stats(h)
+    clocks = ClockSampler(local)
+    clocks.start()
+    dev_ms, wall_ms = [], []
+    B = A.copy()
+
+    def one(i, j, present):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        rd.rd_update_edge(h, i, j, present, 1.0, D)
+        e1.record(stream)
+        e1.synchronize()
+        wall_ms.append((time.perf_counter() - t0) * 1e3)
+        dev_ms.append(e0.elapsed_time(e1))
+
+    for (i, j) in pairs:  # obstacles: both directions of the edge disappear
+        one(i, j, False)
+        one(j, i, False)
+        B[i, j] = B[j, i] = 0
+    torch.cuda.synchronize()
+    # check the removal phase against a fresh FP64 factorisation of the changed graph
+    Bd = torch.from_numpy(B).to(dev)
+    Df = torch.empty((n, n), dtype=torch.int32, device=dev)
+    hf = rd.rd_create(Bd, n, g)
+    rd.rd_set_precision(hf, rd.RD_PREC_FP64, 0)
+    rd.rd_apsp(hf, Df, None)
+    torch.cuda.synchronize()
+    rd.rd_destroy(hf)
+    removed_mismatch = int((D != Df).sum().item())
+    del Bd, Df
+    for (i, j) in pairs:
+        one(i, j, True)
+        one(j, i, True)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    restored_mismatch = int((D != D0).sum().item())
+    st = rd.rd_get_stats(h)
+    # end to end: the same update with D read back to pinned host memory
+    D_host = torch.empty((n, n), dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for (i, j) in pairs[:4]:
+        for present in (False, True):
+            t0 = time.perf_counter()
+            rd.rd_update_edge(h, i, j, present, 1.0, D_host.numpy())
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    rd.rd_destroy(h)
+    count = len(wall_ms)
+    pk, pk_kind = peaks()
+    ums, ubytes, ulaunch = st["prof_update_ms"], st["prof_update_bytes"], st["prof_update_launches"]
+    achieved = ubytes / (ums * 1e-3) / 1e9 if ums > 0 else None
+    roof = {"kernel": "rank1_decode_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": None,
+            "peak_source": f"{pk_kind} HBM copy bandwidth",
+            "work": "20 n^2 bytes per pass: read and write Y (FP64), write D (int32)",
+            "launches": ulaunch, "kernel_ms_per_update": ums / max(1, ulaunch)}
+    # CPU oracle: a full R-distance of a small grid of the same recipe, scaled to n by n^3
+    import oracle
+
+    oracle.build()
+    As = graphs.grid4(1024, 32)
+    t0 = time.perf_counter()
+    oracle.rdistance(As, graphs.gamma_frac(As, 0.9))
+    tcpu = (time.perf_counter() - t0) * (n / As.shape[0]) ** 3 * 1e3
+    line = {
+        "metric": UPDATE_METRIC, "value": float(np.mean(wall_ms)), "unit": "ms", "n_gpus": 1, "steps": count,
+        "warmup": 2, "ms_per_step": float(np.mean(wall_ms)), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"grid 90 x 91 (n={n}) at 0.9/Delta, split-precision factors; {args.obstacles} "
+                               f"edge pairs removed one direction per update, then restored", "n": n, "gamma": g,
+                   "updates": count, "l2": "no flush: Y (512 MiB) and D (256 MiB) exceed the 129 MB L2"},
+        "device_ms_per_update_p50": pct(dev_ms, 0.5), "wall_ms_per_update_p50": pct(wall_ms, 0.5),
+        "wall_ms_per_update_p99": pct(wall_ms, 0.99),
+        "updates_per_s": count / (sum(wall_ms) * 1e-3),
+        "refactors": st["update_refactors"] - st0["update_refactors"],
+        "D_mismatch_after_removals_vs_fresh_fp64": removed_mismatch,
+        "D_mismatch_after_restores_vs_original": restored_mismatch,
+        "e2e": {"value": float(np.mean(e2e_ms)), "unit": "ms", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4 * n * n, "note": "the update with D read back to pinned host memory"},
+        "clocks": clk, "gpu_launches": st["launches"] - st0["launches"], "roofline": roof,
+        "cpu_baseline": {"value": tcpu, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": "CPU oracle (1 thread, FP64): full R-distance of the 32 x 32 grid at 0.9/Delta, "
+                                   f"scaled to n={n} by n^3 (what a CPU recompute of the changed map costs)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "update":
+        run_update(args)
+        return
     if args.workload == "weighted":
         run_weighted(args)
         return

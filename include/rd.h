@@ -100,11 +100,16 @@ typedef struct {
   int64_t prof_split_launches; /* the split GEMM's share of the profile: its launches,     */
   double prof_split_ms;   /* device time and issued digit-product flops (the rest of prof_*  */
   double prof_split_flops;/* is the FP64 GEMM)                                               */
-  int32_t split_order;    /* 1: the split path ran on P M P^T with the library's locality     */
-                          /* order (compact 64-node parts, 64-wide chunks); D, Y and goal    */
+  int32_t split_order;    /* 0: the caller's node order; 1 / 2: the split path ran on P M P^T */
+                          /* with the library's locality order (compact 64-node parts,      */
+                          /* 64-wide chunks) from the landmark bisection (1) or from the     */
+                          /* bisection that scores four keys per part (2); D, Y and goal     */
                           /* rows are returned in the caller's node order either way         */
   int64_t edge_updates;   /* edges changed by rd_update_edge since rd_create / rd_load        */
   int64_t update_refactors; /* of those, updates that refactored (cancellation in Y)          */
+  int64_t prof_update_launches; /* profiled rank-1 update passes of rd_update_edge, their      */
+  double prof_update_ms;  /* summed device time and algorithmic bytes (read and write Y,      */
+  double prof_update_bytes; /* write D: 20 n^2 per pass)                                      */
 } rd_stats;
 
 /* Create a handle for the unweighted graph A (n x n bytes) and gain gamma: validates gamma

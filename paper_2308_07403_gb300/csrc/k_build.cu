@@ -261,13 +261,15 @@ __global__ void __launch_bounds__(1024) landmark_kernel(const int32_t* __restric
 // ---- recursive bisection behind the split path's locality order ------------------------------
 //
 // A part (positions [b, e) of the order) is split into a first part of m0 = 64 ceil(m / 128)
-// positions and the rest along one of three keys: the two landmark axes cu, cv (see
-// landmark_kernel), and the hop distance d_a from a peripheral node a of the part (the node
-// farthest, within the part, from its first node).  Each key's split is scored by the larger
-// double-sweep hop diameter of its two halves (a half that one BFS does not cover scores
-// RCB_SPLIT_PENALTY more), and the best scoring key is applied (ties: cu, cv, d_a).  The landmark
-// axes suit meshes with a Manhattan metric; the part-local distance suits king-move meshes, whose
-// Chebyshev balls give a corner landmark's distance no row information.  Every BFS stays inside
+// positions and the rest.  Unscored, along the landmark axis (cu or cv, see landmark_kernel) with
+// the larger extent over the part.  Scored, along the best of four keys: the two landmark axes cu, cv (see
+// landmark_kernel), and the hop distances d_a, d_b from the two ends of a double sweep inside the
+// part (a farthest from the part's first node, b farthest from a).  Each key's split is scored by
+// the larger double-sweep hop diameter of its two halves (a half that one BFS does not cover
+// scores RCB_SPLIT_PENALTY more), and the best scoring key is applied (ties: in that order).  The
+// landmark axes suit meshes with a Manhattan metric; the part-local distances suit king-move
+// meshes, whose Chebyshev balls give a corner landmark's distance no row information (a cut by
+// d_a alone leaves an L-shaped rest, which d_b then cuts from the other end).  Every BFS stays inside
 // its part (or half), whose nodes carry the CTA's tag.
 
 constexpr int RCB_SPLIT_PENALTY = 1 << 20;
@@ -426,36 +428,83 @@ __device__ void part_split(const int32_t* Lin, int32_t* Lout, int b, int e, int 
 }
 
 // One depth of the bisection: CTA c splits the part [parts[2c], parts[2c+1]) of `ord`.  Scratch
-// (n ints each, a CTA touching only its own nodes): tag, distP, distH, da, key; tmp (n ints);
+// (n ints each, a CTA touching only its own nodes): tag, distP, distH, da, db, key; tmp (n ints);
 // hist (2m + 2 ints per part at 2 b + 2 c).  Tags carry the depth, so a stale tag of another
 // part never matches.
 __global__ void __launch_bounds__(1024) rcb_kernel(const int32_t* __restrict__ parts, int depth, int n,
                                                    const int32_t* __restrict__ ptr, const int32_t* __restrict__ succ,
                                                    const int32_t* __restrict__ cu, const int32_t* __restrict__ cv,
                                                    int32_t* ord, int32_t* tmp, int32_t* hist_all, int32_t* tag,
-                                                   int32_t* distP, int32_t* distH, int32_t* da, int32_t* key) {
+                                                   int32_t* distP, int32_t* distH, int32_t* da, int32_t* db,
+                                                   int32_t* key, int scored) {
   const int b = parts[2 * blockIdx.x], e = parts[2 * blockIdx.x + 1];
   const int m = e - b, m0 = 64 * ((m + 127) / 128);
   const int t = threadIdx.x, T = blockDim.x;
   if (m0 >= m) return;
   int32_t* hist = hist_all + 2 * b + 2 * blockIdx.x;
-  const int tag0 = ((depth + 1) << 22) | ((int)blockIdx.x << 2);  // | 0 whole part, | 1, | 2 halves
-  for (int q = b + t; q < e; q += T) tag[ord[q]] = tag0;
-  __syncthreads();
-  // peripheral node a and the part-local distance d_a
-  part_bfs(ptr, succ, ord, b, e, tag, tag0, ord[b], distP);
-  const Far fa = part_farthest(ord, b, e, distP);
-  part_bfs(ptr, succ, ord, b, e, tag, tag0, fa.node, da);
-  int best = 0, best_score = 0x7fffffff;
-  for (int cand = 0; cand < 4; ++cand) {
-    const int use = cand < 3 ? cand : best;  // the last pass applies the best key
+  if (!scored) {  // the landmark axis with the larger extent over the part's reached nodes
+    __shared__ int ext[4][32];
+    int umin = 0x7fffffff, umax = -0x7fffffff, vmin = 0x7fffffff, vmax = -0x7fffffff;
     for (int q = b + t; q < e; q += T) {
       const int v = ord[q];
-      key[v] = use == 0 ? (cv[v] >= 0 ? cu[v] + n : -1) : use == 1 ? (cv[v] >= 0 ? cv[v] : -1) : da[v];
+      if (cv[v] < 0) continue;
+      umin = min(umin, cu[v]);
+      umax = max(umax, cu[v]);
+      vmin = min(vmin, cv[v]);
+      vmax = max(vmax, cv[v]);
+    }
+    for (int o = 16; o; o >>= 1) {
+      umin = min(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+      umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+      vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+      vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    if ((t & 31) == 0) {
+      ext[0][t >> 5] = umin;
+      ext[1][t >> 5] = umax;
+      ext[2][t >> 5] = vmin;
+      ext[3][t >> 5] = vmax;
+    }
+    __syncthreads();
+    for (int w = 0; w < (T >> 5); ++w) {
+      umin = min(umin, ext[0][w]);
+      umax = max(umax, ext[1][w]);
+      vmin = min(vmin, ext[2][w]);
+      vmax = max(vmax, ext[3][w]);
+    }
+    const bool use_u = (umax - umin) >= (vmax - vmin);
+    for (int q = b + t; q < e; q += T) {
+      const int v = ord[q];
+      key[v] = cv[v] < 0 ? -1 : (use_u ? cu[v] + n : cv[v]);
     }
     __syncthreads();
     part_split(ord, tmp, b, e, m0, key, hist);
-    if (cand == 3) break;
+    for (int q = b + t; q < e; q += T) ord[q] = tmp[q];
+    return;
+  }
+  const int tag0 = ((depth + 1) << 22) | ((int)blockIdx.x << 2);  // | 0 whole part, | 1, | 2 halves
+  for (int q = b + t; q < e; q += T) tag[ord[q]] = tag0;
+  __syncthreads();
+  // the ends a, b of a double sweep inside the part and the part-local distances d_a, d_b
+  part_bfs(ptr, succ, ord, b, e, tag, tag0, ord[b], distP);
+  const Far fa = part_farthest(ord, b, e, distP);
+  part_bfs(ptr, succ, ord, b, e, tag, tag0, fa.node, da);
+  const Far fb = part_farthest(ord, b, e, da);
+  part_bfs(ptr, succ, ord, b, e, tag, tag0, fb.node, db);
+  constexpr int KEYS = 4;
+  int best = 0, best_score = 0x7fffffff;
+  for (int cand = 0; cand <= KEYS; ++cand) {
+    const int use = cand < KEYS ? cand : best;  // the last pass applies the best key
+    for (int q = b + t; q < e; q += T) {
+      const int v = ord[q];
+      key[v] = use == 0   ? (cv[v] >= 0 ? cu[v] + n : -1)
+               : use == 1 ? (cv[v] >= 0 ? cv[v] : -1)
+               : use == 2 ? da[v]
+                          : db[v];
+    }
+    __syncthreads();
+    part_split(ord, tmp, b, e, m0, key, hist);
+    if (cand == KEYS) break;
     for (int q = b + t; q < e; q += T) tag[tmp[q]] = tag0 | (q < b + m0 ? 1 : 2);
     __syncthreads();
     const int s1 = half_score(ptr, succ, tmp, b, b + m0, tag, tag0 | 1, distH);
@@ -557,10 +606,11 @@ cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, const int32_t* ord, 
 }
 
 // Locality order of the split path: landmark coordinates (landmark_kernel), then recursive
-// bisection into parts of 64 consecutive positions (rcb_kernel), h->dOrd[position] = node,
-// h->dPos[node] = position.  Scratch: 12 n ints of the N^2-int buffer dS (N >= 128, n <= N).  The part boundaries depend on n alone, so the host lists them;
+// bisection into parts of 64 consecutive positions (rcb_kernel, unscored or scored: see there),
+// h->dOrd[position] = node,
+// h->dPos[node] = position.  Scratch: 13 n ints of the N^2-int buffer dS (N >= 128, n <= N).  The part boundaries depend on n alone, so the host lists them;
 // one launch per depth.
-cudaError_t rd_locality_order(rd_ctx* h, cudaStream_t s) {
+cudaError_t rd_locality_order(rd_ctx* h, int scored, cudaStream_t s) {
   const int n = h->n;
   int32_t* w = reinterpret_cast<int32_t*>(h->dS);  // free before the factorisation (>= N^2 ints)
   int32_t* d0 = w;
@@ -573,6 +623,7 @@ cudaError_t rd_locality_order(rd_ctx* h, cudaStream_t s) {
   int32_t* tag = w + 9 * (size_t)n;
   int32_t* da = w + 10 * (size_t)n;
   int32_t* key = w + 11 * (size_t)n;
+  int32_t* db = w + 12 * (size_t)n;
   std::vector<int32_t> all;             // every depth's list of parts to split, concatenated
   std::vector<std::pair<int, int>> depth_span;
   std::vector<std::pair<int, int>> cur{{0, n}};
@@ -611,7 +662,7 @@ cudaError_t rd_locality_order(rd_ctx* h, cudaStream_t s) {
     const auto& d = depth_span[dep];
     if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
     rcb_kernel<<<d.second, 1024, 0, s>>>(dparts + 2 * d.first, (int)dep, n, h->dDeg + (n + 1), h->dSucc, cu, cv,
-                                         h->dOrd, tmp, hist, tag, d0, d1, da, key);
+                                         h->dOrd, tmp, hist, tag, d0, d1, da, db, key, scored);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   }

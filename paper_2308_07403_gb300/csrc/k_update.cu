@@ -21,23 +21,56 @@ __global__ void gather_uv_kernel(const double* __restrict__ Y, int n, int i, int
   if (t == 0) uv[2 * n] = delta / (1.0 - delta * Y[(long long)j * n + i]);
 }
 
-__global__ void rank1_decode_kernel(double* __restrict__ Y, const double* __restrict__ uv, int n, int32_t* D,
-                                    float inv_log2_gamma, double log_gamma, double tau, unsigned int* lost) {
-  const double alpha = uv[2 * n];
-  unsigned int bad = 0;
-  const long long nn = (long long)n * n;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(e / n), c = (int)(e % n);
-    const double y0 = Y[e];
-    const double t = alpha * uv[r] * uv[n + c];
-    double y = y0 + t;
-    if (t < 0.0 && y < y0 * 0x1p-20) {  // cancellation: the entry kept fewer than ~33 bits
-      bad++;
-      if (y < 0.0) y = 0.0;
+// one entry: y = y0 + (alpha u_r) v_c as one FMA (the only FP64 instruction: GB300's FP64 pipe
+// retires 2 per clock per SM, which would otherwise bound the pass), the cancellation count and
+// the decode.  u, v >= 0, so the term's sign is the row's (neg); the tests on y compare the bit
+// patterns of non-negative doubles as integers: y < y0 2^-20 when the exponent fell by more than
+// 20 (y0 normal), y < 0 when the sign bit is set.
+__device__ __forceinline__ void rank1_entry(double y0, double ar, double vc, bool neg, bool diag,
+                                            float inv_log2_gamma, double log_gamma, double tau, double* y_out,
+                                            int32_t* d_out, unsigned int* bad) {
+  double y = fma(ar, vc, y0);
+  if (neg) {
+    const long long by = __double_as_longlong(y), b0 = __double_as_longlong(y0);
+    if (by < b0 - (20ll << 52)) {  // cancellation: the entry kept fewer than ~33 bits
+      ++*bad;
+      if (by < 0) y = 0.0;
     }
-    Y[e] = y;
-    D[e] = (r == c) ? 0 : rd_decode_entry_fast(y, inv_log2_gamma, log_gamma, tau);
+  }
+  *y_out = y;
+  *d_out = diag ? 0 : rd_decode_entry_fast(y, inv_log2_gamma, log_gamma, tau);
+}
+
+// Y += alpha u v^T with the decode of D, row by row (a CTA per row in turn); with vec (n even and
+// D 8-byte aligned; Y and u, v are the library's own, 256-byte aligned) two entries per access:
+// 16-byte loads and stores of Y, 8-byte stores of D (rows start at 8 n and 4 n bytes).  HBM bound: 20 bytes per entry (read Y, write Y, write D); v stays in L2.
+__global__ void __launch_bounds__(256) rank1_decode_kernel(double* __restrict__ Y, const double* __restrict__ uv,
+                                                           int n, int32_t* __restrict__ D, float inv_log2_gamma,
+                                                           double log_gamma, double tau, int vec,
+                                                           unsigned int* lost) {
+  const double alpha = uv[2 * n];
+  const double* __restrict__ v = uv + n;
+  unsigned int bad = 0;
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const double ar = alpha * uv[r];
+    const bool neg = __double_as_longlong(ar) < 0;
+    double* yr = Y + (long long)r * n;
+    int32_t* dr = D + (long long)r * n;
+    if (vec) {
+      for (int c = 2 * threadIdx.x; c < n; c += 2 * blockDim.x) {
+        const double2 y0 = *reinterpret_cast<const double2*>(yr + c);
+        const double2 vc = *reinterpret_cast<const double2*>(v + c);
+        double2 y;
+        int2 d;
+        rank1_entry(y0.x, ar, vc.x, neg, r == c, inv_log2_gamma, log_gamma, tau, &y.x, &d.x, &bad);
+        rank1_entry(y0.y, ar, vc.y, neg, r == c + 1, inv_log2_gamma, log_gamma, tau, &y.y, &d.y, &bad);
+        *reinterpret_cast<double2*>(yr + c) = y;
+        *reinterpret_cast<int2*>(dr + c) = d;
+      }
+    } else {
+      for (int c = threadIdx.x; c < n; c += blockDim.x)
+        rank1_entry(yr[c], ar, v[c], neg, r == c, inv_log2_gamma, log_gamma, tau, &yr[c], &dr[c], &bad);
+    }
   }
   for (int o = 16; o; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(lost, bad);
@@ -71,11 +104,13 @@ cudaError_t rd_rank1_update(rd_ctx* h, int i, int j, double delta, int32_t* D, u
   gather_uv_kernel<<<(n + 255) / 256, 256, 0, s>>>(h->dYres, n, i, j, delta, uv);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
-  if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
-  rank1_decode_kernel<<<1216, 256, 0, s>>>(h->dYres, uv, n, D, (float)(1.0 / log2(h->gamma)), log(h->gamma), h->tau,
-                                           lost);
+  if ((e = rd_prof_begin(h, s, RD_PROF_UPDATE)) != cudaSuccess) return e;
+  const int grid = n < 152 * 8 ? n : 152 * 8;  // 8 CTAs of 256 threads per SM, a row each in turn
+  const int vec = (n % 2 == 0) && ((uintptr_t)D % 8 == 0);
+  rank1_decode_kernel<<<grid, 256, 0, s>>>(h->dYres, uv, n, D, (float)(1.0 / log2(h->gamma)), log(h->gamma), h->tau,
+                                           vec, lost);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
+  return rd_prof_end(h, s, RD_PROF_UPDATE, 20.0 * (double)n * (double)n);
 }
 
 cudaError_t rd_set_edge(rd_ctx* h, int i, int j, uint8_t present, float w, double delta, int ddeg,

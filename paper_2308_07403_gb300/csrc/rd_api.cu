@@ -235,6 +235,8 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
 // inverse is recomputed from M.
 bool split_auto(const rd_ctx* h) { return h->precision == RD_PREC_SPLIT_BF16 && h->slices_req == 0; }
 
+double choose_locality_order(rd_ctx* h, double wf, rd_status* st);
+
 // Each added digit carries 7 more bits of every operand chunk, so a residual r at s digits asks
 // for about log2(r / 2^-40) / 7 more digits to reach the 2^-40 of result the screen aims at (a
 // residual near 1, entries lost below the digits altogether, reads as at least 40 missing bits).
@@ -250,8 +252,9 @@ rd_status escalate(rd_ctx* h, double worst) {
   if (next > smax && !h->ordered && next <= RD_SPLIT_MAX_ORDERED && h->dSucc) {
     // the natural order ran out of digits: the locality order's 64-wide chunks carry up to 22
     if (!h->order_ready) {
-      RD_CK(h, rd_locality_order(h, h->stream));
-      h->order_ready = 1;
+      rd_status st;
+      choose_locality_order(h, h->weighted ? RD_SCREEN_WEIGHTED : 1.0, &st);
+      if (st != RD_OK) return st;
     }
     h->ordered = 1;
     h->kappa = RD_SCREEN_CHUNK_ORDERED;
@@ -295,6 +298,36 @@ double spread_bits(rd_ctx* h, const int32_t* ord, int chunk, rd_status* st) {
   return (double)spread * std::log2(1.0 / h->gamma);
 }
 
+// the fewest digits (at least RD_SPLIT_MIN) whose 7 bits each cover `bits` plus the result bits
+int digits_for(double bits) {
+  const int s = (int)std::ceil((bits + RD_SCREEN_RESULT_BITS) / RD_SPLIT_DIGIT_BITS);
+  return s < RD_SPLIT_MIN ? RD_SPLIT_MIN : s;
+}
+
+// The locality order with the smaller screened spread: the landmark bisection, and, when its
+// 64-node parts still need more than RD_SPLIT_MAX digits (parts that are not compact: on a
+// king-move mesh the landmark axes cut strips), the scored bisection too.  Leaves the chosen
+// order in dOrd / dPos (h->order_ready = 1 or 2) and returns its spread bits times wf.
+double choose_locality_order(rd_ctx* h, double wf, rd_status* st) {
+  *st = RD_OK;
+  auto fail_order = [&](cudaError_t e) {
+    *st = fail_cuda(h, e, "locality order");
+    return 0.0;
+  };
+  cudaError_t e = rd_locality_order(h, 0, h->stream);
+  if (e != cudaSuccess) return fail_order(e);
+  h->order_ready = 1;
+  const double landmark = wf * spread_bits(h, h->dOrd, RD_SCREEN_CHUNK_ORDERED, st);
+  if (*st != RD_OK || digits_for(landmark) <= RD_SPLIT_MAX) return landmark;
+  if ((e = rd_locality_order(h, 1, h->stream)) != cudaSuccess) return fail_order(e);
+  h->order_ready = 2;
+  const double scored = wf * spread_bits(h, h->dOrd, RD_SCREEN_CHUNK_ORDERED, st);
+  if (*st != RD_OK || scored < landmark) return scored;
+  if ((e = rd_locality_order(h, 0, h->stream)) != cudaSuccess) return fail_order(e);  // back to the landmark order
+  h->order_ready = 1;
+  return landmark;
+}
+
 rd_status screen_split(rd_ctx* h) {
   h->screened = 1;
   h->screen_bits = -1.0;
@@ -305,10 +338,6 @@ rd_status screen_split(rd_ctx* h) {
     RD_CK(h, rd_build_succ(h, h->stream));
     h->succ_ready = 1;
   }
-  auto digits_for = [](double bits) {
-    const int s = (int)std::ceil((bits + RD_SCREEN_RESULT_BITS) / RD_SPLIT_DIGIT_BITS);
-    return s < RD_SPLIT_MIN ? RD_SPLIT_MIN : s;
-  };
   rd_status st;
   const double wf = h->weighted ? RD_SCREEN_WEIGHTED : 1.0;
   const double nat = wf * spread_bits(h, nullptr, RD_SCREEN_CHUNK, &st);
@@ -319,9 +348,7 @@ rd_status screen_split(rd_ctx* h) {
     h->split_start = s_nat;
     return RD_OK;
   }
-  RD_CK(h, rd_locality_order(h, h->stream));
-  h->order_ready = 1;
-  const double ord = wf * spread_bits(h, h->dOrd, RD_SCREEN_CHUNK_ORDERED, &st);
+  const double ord = choose_locality_order(h, wf, &st);
   if (st != RD_OK) return st;
   const int s_ord = digits_for(ord);
   // the locality order when it needs fewer digits, or when only it can carry more than 15
@@ -436,6 +463,12 @@ cudaError_t rd_prof_collect(rd_ctx* h) {
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]);
     if (e != cudaSuccess) return e;
+    if (h->prof_kind[i] == RD_PROF_UPDATE) {  // bytes, not flops: kept apart
+      h->prof_update_ms += ms;
+      h->prof_update_bytes += h->prof_pair_flops[i];
+      h->prof_update_launches++;
+      continue;
+    }
     h->prof_ms += ms;
     h->prof_flops += h->prof_pair_flops[i];
     h->prof_launches++;
@@ -465,6 +498,8 @@ rd_status rd_set_profiling(rd_handle h, int32_t on) {
   h->prof_launches = 0;
   h->prof_split_ms = h->prof_split_flops = 0.0;
   h->prof_split_launches = 0;
+  h->prof_update_ms = h->prof_update_bytes = 0.0;
+  h->prof_update_launches = 0;
   return RD_OK;
 }
 
@@ -717,7 +752,7 @@ rd_status rd_get_stats(rd_handle h, rd_stats* s) {
   s->fallbacks = h->fallbacks;
   s->split_residual = h->last_residual;
   s->split_screen_bits = h->screen_bits;
-  s->split_order = h->ordered;
+  s->split_order = h->ordered ? h->order_ready : 0;
   s->edge_updates = h->edge_updates;
   s->update_refactors = h->update_refactors;
   s->gamma = h->gamma;
@@ -737,6 +772,9 @@ rd_status rd_get_stats(rd_handle h, rd_stats* s) {
   s->prof_split_launches = h->prof_split_launches;
   s->prof_split_ms = h->prof_split_ms;
   s->prof_split_flops = h->prof_split_flops;
+  s->prof_update_launches = h->prof_update_launches;
+  s->prof_update_ms = h->prof_update_ms;
+  s->prof_update_bytes = h->prof_update_bytes;
   return st;
 }
 

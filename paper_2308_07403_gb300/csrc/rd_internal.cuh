@@ -53,7 +53,7 @@ struct rd_ctx {
   int32_t n = 0, N = 0;
   double gamma = 0.0, tau = 1e-9, max_colsum = 0.0;
   int weighted = 0;
-  int order_ready = 0;  // h->dOrd / h->dPos hold the locality order of the resident graph
+  int order_ready = 0;  // h->dOrd / h->dPos hold a locality order of the resident graph: 1 landmark, 2 scored
   int precision = RD_PREC_FP64;
   int slices_req = 0, slices = 0;
   cudaStream_t stream = nullptr;
@@ -119,13 +119,15 @@ struct rd_ctx {
   int64_t prof_launches = 0;
   double prof_split_ms = 0.0, prof_split_flops = 0.0;  // the split GEMM's share of the above
   int64_t prof_split_launches = 0;
+  double prof_update_ms = 0.0, prof_update_bytes = 0.0;  // the rank-1 update passes (HBM bound)
+  int64_t prof_update_launches = 0;
   int8_t prof_kind[kProfPairs] = {};           // RD_PROF_* of each pending event pair
   double prof_pair_flops[kProfPairs] = {};
 };
 
 // Launch accounting around one kernel launch (see rd_ctx).  `kind` marks the dense GEMM kernels
 // whose time and algorithmic flops are profiled (RD_PROF_NONE for every other kernel).
-enum { RD_PROF_NONE = 0, RD_PROF_F64 = 1, RD_PROF_SPLIT = 2 };
+enum { RD_PROF_NONE = 0, RD_PROF_F64 = 1, RD_PROF_SPLIT = 2, RD_PROF_UPDATE = 3 };
 cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, int kind);
 cudaError_t rd_prof_end(rd_ctx* h, cudaStream_t s, int kind, double flops);
 cudaError_t rd_prof_collect(rd_ctx* h);  // fold finished event pairs into prof_ms
@@ -173,8 +175,9 @@ cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s);    // successor CSR from d
 // words of scratch.  atomicMax of the spread's float bits into *out
 cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, const int32_t* ord, int32_t* dist,
                             unsigned long long* out, cudaStream_t s);
-// locality order for the split path (dOrd, dPos; uses dS as scratch; synchronises once)
-cudaError_t rd_locality_order(rd_ctx* h, cudaStream_t s);
+// locality order for the split path (dOrd, dPos; uses dS as scratch; synchronises once): the
+// landmark bisection (scored = 0) or the bisection that scores four keys per part (scored = 1)
+cudaError_t rd_locality_order(rd_ctx* h, int scored, cudaStream_t s);
 // dLU <- P M P^T (the permuted M; dT is used as the staging buffer and swapped in)
 cudaError_t rd_permute_m(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows, int cols,
@@ -231,8 +234,8 @@ __device__ __forceinline__ int32_t rd_decode_entry(double y, double log_gamma, d
 // otherwise, and for R beyond 2^22 where FP32 holds no fraction, the FP64 formula decides.
 __device__ __forceinline__ int32_t rd_decode_entry_fast(double y, float inv_log2_gamma, double log_gamma,
                                                         double tau) {
-  if (y > 0.0) {
-    const long long b = __double_as_longlong(y);
+  const long long b = __double_as_longlong(y);
+  if (b > 0) {  // y > 0 (NaN and infinity fail the exponent test below), without the FP64 pipe
     const int ex = (int)((b >> 52) & 0x7FF);
     if (ex != 0 && ex != 0x7FF) {
       const float m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7FFFFF));

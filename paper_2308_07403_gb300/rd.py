@@ -84,6 +84,8 @@ class rd_stats(ctypes.Structure):
         ("prof_split_flops", ctypes.c_double),
         ("split_order", ctypes.c_int32),
         ("edge_updates", ctypes.c_int64), ("update_refactors", ctypes.c_int64),
+        ("prof_update_launches", ctypes.c_int64), ("prof_update_ms", ctypes.c_double),
+        ("prof_update_bytes", ctypes.c_double),
     ]
 
 

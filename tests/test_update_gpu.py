@@ -124,3 +124,29 @@ def test_weighted_edge_reweight(rd):
         assert ok
         h.update_edge(int(i), int(j), True, D, w=float(W2[i, j]))
     assert np.array_equal(D, oracle.rdistance(A, g, W=W2))
+
+
+@pytest.mark.parametrize("n,offset", [(300, 0), (300, 1), (301, 0)])
+def test_update_into_device_views(rd, n, offset):
+    """D as a device tensor: aligned with even n (two entries per access), a view 4 bytes into its
+    buffer (not 8-byte aligned: one entry per access) and odd n; D equals the oracle's after each
+    added edge."""
+    A = graphs.er(n, 0.02, 9)
+    g = 0.5 / (graphs.max_out_degree(A) + 3)
+    rng = np.random.default_rng(4)
+    buf = torch.empty(n * n + offset, dtype=torch.int32, device="cuda")
+    D = buf[offset:].view(n, n)
+    assert (D.data_ptr() % 8 == 0) == (offset == 0)
+    with rd.Handle(A, g) as h:
+        h.set_precision(rd.RD_PREC_FP64, 0)
+        h.apsp(D)
+        B = A.copy()
+        for _ in range(3):
+            while True:
+                i, j = (int(x) for x in rng.integers(0, n, 2))
+                if i != j and not B[i, j]:
+                    break
+            B[i, j] = 1
+            h.update_edge(i, j, True, D)
+            torch.cuda.synchronize()
+            assert np.array_equal(D.cpu().numpy(), oracle.rdistance(B, g))
