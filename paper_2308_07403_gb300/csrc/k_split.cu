@@ -366,6 +366,11 @@ struct SplitArgs {
   // the products of a graph in the locality order write back in the caller's node order
   const int32_t* row_map;
   const int32_t* col_map;
+  // split K: ksplit CTAs per output tile, each over its share of the tile's chunks, writing the
+  // unscaled FP64 partial sums to partial[ks][row][col] (ma_pad x nb_pad each); a reduction
+  // kernel then applies alpha, beta, the bounds and the maps.  ksplit = 1: no partials.
+  int ksplit;
+  double* partial;
 };
 
 template <int KP>
@@ -387,16 +392,27 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int tiles_n = (p.N + TN - 1) / TN;
-  const int m0 = (blockIdx.x / tiles_n) * TM;
-  const int n0 = (blockIdx.x % tiles_n) * TN;
+  const int ks_idx = (int)(blockIdx.x % (unsigned)p.ksplit);
+  const int tile = (int)(blockIdx.x / (unsigned)p.ksplit);
+  const int m0 = (tile / tiles_n) * TM;
+  const int n0 = (tile % tiles_n) * TN;
   int kbeg = 0, kend = p.K;
   if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, m0 + TM);
   if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, m0);
   if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, n0);
   if (p.b_tri == RD_TRI_UPPER) kend = min(kend, n0 + TN);
-  // chunks are aligned to absolute multiples of KP; the first and last may be partial
-  const int cbeg = kbeg / KP;
-  const int nchunks = (kbeg < kend) ? (kend + KP - 1) / KP - cbeg : 0;
+  // chunks are aligned to absolute multiples of KP; the first and last may be partial.  With
+  // split K this CTA takes chunks [c_lo, c_hi) of the tile's range.
+  int cbeg = kbeg / KP;
+  int nchunks = (kbeg < kend) ? (kend + KP - 1) / KP - cbeg : 0;
+  if (p.ksplit > 1) {
+    const int c_lo = cbeg + (int)(((long long)nchunks * ks_idx) / p.ksplit);
+    const int c_hi = cbeg + (int)(((long long)nchunks * (ks_idx + 1)) / p.ksplit);
+    kbeg = max(kbeg, c_lo * KP);
+    kend = min(kend, c_hi * KP);
+    cbeg = c_lo;
+    nchunks = (kbeg < kend) ? c_hi - c_lo : 0;
+  }
   const int s = p.s;
 
   if (threadIdx.x == 0) {
@@ -624,6 +640,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int col = n0 + half * 64 + j;
         if (row >= p.M || col >= p.N) continue;
         double v = ldexp((double)hi[j] + (double)__uint_as_float(lr[jj]), (int)rf[j * TM] - ACC_OFF);
+        if (p.partial) {  // split K: the unscaled partial sum
+          p.partial[((long long)ks_idx * p.ma_pad + row) * p.nb_pad + col] = v;
+          continue;
+        }
         v = p.alpha * v;
         const long long orow = p.row_map ? p.row_map[row] : row;
         const long long ocol = p.col_map ? p.col_map[col] : col;
@@ -688,6 +708,20 @@ __global__ void row_residual_kernel(const double* __restrict__ rows, const int32
 
 // ---- host side ---------------------------------------------------------------------------------
 
+// streaming multiprocessors of the current device (152 on GB300)
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms <= 0) {
+      cudaGetLastError();
+      sms = 152;
+    }
+  }
+  return sms;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -728,6 +762,15 @@ struct View {
 
 struct rd_split_plan {
   int N = 0, s = 0, cap_s = 0;
+  // the operand whose digits digB / eB hold when they may be reused: the final L^-1 of the current
+  // factors (the inverse product, the self-check's and the goal solves' rows all multiply by it)
+  bool b_cached = false;
+  const double* b_p = nullptr;
+  long long b_ld = 0;
+  int b_rows = 0, b_cols = 0, b_tri = 0, b_cols_pad = 0, b_k_pad = 0, b_s = 0, b_kappa = 0;
+  unsigned long long b_gen = 0;
+  double* part = nullptr;  // split-K partial sums (grown on demand)
+  size_t part_bytes = 0;
   __nv_bfloat16* digA = nullptr;
   __nv_bfloat16* digB = nullptr;
   int* eA = nullptr;
@@ -754,9 +797,43 @@ cudaError_t slice_a(rd_ctx* h, const View& v, int rows_pad, int k_pad, cudaStrea
   return rd_prof_end(h, st, RD_PROF_NONE, 0.0);
 }
 
-// Slice the B operand (k x cols, row-major) into digB/eB (K-major per column).
-cudaError_t slice_b(rd_ctx* h, const View& v, int cols_pad, int k_pad, cudaStream_t st) {
+// Split-K reduction: C[map(row)][map(col)] = alpha sum_ks partial[ks][row][col] (+ beta C) over
+// rows < c_rows, cols < c_cols, the partials summed in order of ks (deterministic; the partials of
+// a sign-definite product share one sign, so the sum does not cancel).
+__global__ void ksplit_reduce_kernel(const double* __restrict__ part, int ksplit, int ma_pad, int nb_pad, int rows,
+                                     int cols, double alpha, double beta, double* C, long long ldc,
+                                     const int32_t* __restrict__ row_map, const int32_t* __restrict__ col_map) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * cols) return;
+  const int r = (int)(t / cols), c = (int)(t % cols);
+  double v = 0.0;
+  for (int k = 0; k < ksplit; ++k) v += part[((long long)k * ma_pad + r) * nb_pad + c];
+  v *= alpha;
+  double* cp = C + (long long)(row_map ? row_map[r] : r) * ldc + (col_map ? col_map[c] : c);
+  if (beta != 0.0) v = fma(beta, *cp, v);
+  *cp = v;
+}
+
+// Slice the B operand (k x cols, row-major) into digB/eB (K-major per column).  With cacheable
+// (B is the final L^-1 of the current factors), digits already sliced from the same view, digit
+// count and chunk width for the same factorisation are reused.
+cudaError_t slice_b(rd_ctx* h, const View& v, int cols_pad, int k_pad, cudaStream_t st, bool cacheable) {
   rd_split_plan* P = h->split;
+  if (cacheable && P->b_cached && P->b_p == v.p && P->b_ld == v.ld && P->b_rows == v.rows && P->b_cols == v.cols &&
+      P->b_tri == v.tri && P->b_cols_pad == cols_pad && P->b_k_pad == k_pad && P->b_s == P->s &&
+      P->b_kappa == h->kappa && P->b_gen == h->factor_gen)
+    return cudaSuccess;
+  P->b_cached = cacheable;
+  P->b_p = v.p;
+  P->b_ld = v.ld;
+  P->b_rows = v.rows;
+  P->b_cols = v.cols;
+  P->b_tri = v.tri;
+  P->b_cols_pad = cols_pad;
+  P->b_k_pad = k_pad;
+  P->b_s = P->s;
+  P->b_kappa = h->kappa;
+  P->b_gen = h->factor_gen;
   cudaError_t e = rd_prof_begin(h, st, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   const dim3 grid(cols_pad / 16, k_pad / h->kappa);
@@ -789,14 +866,15 @@ cudaError_t launch_split(const CUtensorMap& ta, const CUtensorMap& tb, const Spl
 // product; the profile counts the issued digit products.
 cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, int K, double alpha, double beta,
                        double* C, long long ldc, int c_rows, int c_cols, int32_t* D, double* Ystore, double flops,
-                       cudaStream_t st, const int32_t* row_map = nullptr, const int32_t* col_map = nullptr) {
+                       cudaStream_t st, const int32_t* row_map = nullptr, const int32_t* col_map = nullptr,
+                       bool b_is_final_linv = false) {
   rd_split_plan* P = h->split;
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   if (M % 64 || N % 64 || K % 64) return cudaErrorInvalidValue;
   const int ma_pad = round_up(M, TM), nb_pad = round_up(N, TN), k_pad = round_up(K, h->kappa);  // k_pad <= N + 128
   cudaError_t e;
   if ((e = slice_a(h, A, ma_pad, k_pad, st)) != cudaSuccess) return e;
-  if ((e = slice_b(h, B, nb_pad, k_pad, st)) != cudaSuccess) return e;
+  if ((e = slice_b(h, B, nb_pad, k_pad, st, b_is_final_linv)) != cudaSuccess) return e;
   CUtensorMap ta, tb;
   if ((e = make_map(&ta, P->digA, k_pad, (long long)P->s * ma_pad)) != cudaSuccess) return e;
   if ((e = make_map(&tb, P->digB, k_pad, (long long)P->s * nb_pad)) != cudaSuccess) return e;
@@ -829,11 +907,50 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   a.row_map = row_map;
   a.col_map = col_map;
   const int tiles = (ma_pad / TM) * (nb_pad / TN);
+  // split K when the tiles leave SMs idle (products of a few tiles: the goal and self-check rows,
+  // the middle of the recursion), up to two CTAs per SM; not with the fused decode
+  int ksplit = 1;
+  const int nch = k_pad / h->kappa, sms = num_sms();
+  if (!D && a.store_c && tiles < sms) {
+    ksplit = (2 * sms) / tiles;
+    if (ksplit > 8) ksplit = 8;
+    if (ksplit > nch) ksplit = nch;
+    if (ksplit < 1) ksplit = 1;
+  }
+  a.ksplit = ksplit;
+  a.partial = nullptr;
+  if (ksplit > 1) {
+    const size_t need = (size_t)ksplit * ma_pad * nb_pad * sizeof(double);
+    if (P->part_bytes < need) {
+      if (P->part) {
+        cudaFree(P->part);
+        h->bytes -= (int64_t)P->part_bytes;
+        P->bytes -= (int64_t)P->part_bytes;
+        P->part = nullptr;
+        P->part_bytes = 0;
+      }
+      if ((e = cudaMalloc((void**)&P->part, need)) != cudaSuccess) return e;
+      P->part_bytes = need;
+      P->bytes += (int64_t)need;
+      h->bytes += (int64_t)need;
+    }
+    a.partial = P->part;
+  }
   if ((e = rd_prof_begin(h, st, RD_PROF_SPLIT)) != cudaSuccess) return e;
-  e = (h->kappa == KAPPA_NARROW) ? launch_split<KAPPA_NARROW>(ta, tb, a, tiles, st)
-                                 : launch_split<KAPPA_WIDE>(ta, tb, a, tiles, st);
+  e = (h->kappa == KAPPA_NARROW) ? launch_split<KAPPA_NARROW>(ta, tb, a, tiles * ksplit, st)
+                                 : launch_split<KAPPA_WIDE>(ta, tb, a, tiles * ksplit, st);
   if (e != cudaSuccess) return e;
-  return rd_prof_end(h, st, RD_PROF_SPLIT, flops * (double)P->s * (P->s + 1) / 2.0);
+  if ((e = rd_prof_end(h, st, RD_PROF_SPLIT, flops * (double)P->s * (P->s + 1) / 2.0)) != cudaSuccess) return e;
+  if (ksplit > 1) {
+    if ((e = rd_prof_begin(h, st, RD_PROF_NONE)) != cudaSuccess) return e;
+    const long long total = (long long)a.c_rows * a.c_cols;
+    ksplit_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P->part, ksplit, ma_pad, nb_pad, a.c_rows,
+                                                                          a.c_cols, alpha, beta, a.C, a.ldc, row_map,
+                                                                          col_map);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = rd_prof_end(h, st, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 inline View full(const double* p, long long ld, int rows, int cols) { return View{p, ld, rows, cols, RD_TRI_FULL}; }
@@ -989,7 +1106,7 @@ rd_status rd_split_prepare(rd_ctx* h, int s) {
 void rd_split_release(rd_ctx* h) {
   rd_split_plan* P = h->split;
   if (!P) return;
-  void* ptrs[] = {P->digA, P->digB, P->eA, P->eB};
+  void* ptrs[] = {P->digA, P->digB, P->eA, P->eB, P->part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   h->bytes -= (h->bytes >= P->bytes) ? P->bytes : 0;
@@ -1007,7 +1124,7 @@ cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t 
   const double Nd = (double)N;
   const int32_t* map = h->ordered ? h->dOrd : nullptr;  // D and Y back in the caller's node order
   return split_gemm(h, tri(h->dT, N, N, RD_TRI_UPPER), tri(h->dT, N, N, RD_TRI_LOWER_UNIT), N, N, N, 1.0, 0.0,
-                    nullptr, 0, 0, 0, D, Y, 2.0 * Nd * (Nd + 1) * (2 * Nd + 1) / 6.0, s, map, map);
+                    nullptr, 0, 0, 0, D, Y, 2.0 * Nd * (Nd + 1) * (2 * Nd + 1) / 6.0, s, map, map, true);
 }
 
 // Self-check of the split result: 64 rows of Y spread over the graph, computed like the goal
@@ -1058,5 +1175,5 @@ cudaError_t rd_goal_split(rd_ctx* h, const int32_t* dgoals, int k, double* out, 
   const double Nd = (double)N;
   return split_gemm(h, full(h->dR, N, RD_MAX_GOALS, (int)N), tri(h->dT, N, (int)N, RD_TRI_LOWER_UNIT), RD_MAX_GOALS,
                     (int)N, (int)N, 1.0, 0.0, out, h->n, k, h->n, nullptr, nullptr, RD_MAX_GOALS * Nd * (Nd + 1),
-                    s, nullptr, h->ordered ? h->dOrd : nullptr);
+                    s, nullptr, h->ordered ? h->dOrd : nullptr, true);
 }

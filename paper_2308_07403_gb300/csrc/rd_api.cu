@@ -239,7 +239,7 @@ double choose_locality_order(rd_ctx* h, double wf, rd_status* st);
 
 // Each added digit carries 7 more bits of every operand chunk, so a residual r at s digits asks
 // for about log2(r / 2^-40) / 7 more digits to reach the 2^-40 of result the screen aims at (a
-// residual near 1, entries lost below the digits altogether, reads as at least 40 missing bits).
+// residual near 1, entries lost below the digits altogether, reads as at least RD_SCREEN_RESULT_BITS missing bits).
 // Beyond RD_SPLIT_MAX digits the natural order moves to the locality order (RD_SPLIT_MAX_ORDERED
 // at most); beyond that the graph runs in FP64.  The count grows by at least one digit per failure, so
 // the loop ends.
@@ -373,6 +373,7 @@ rd_status ensure_factored(rd_ctx* h) {
   }
   RD_CK(h, cudaEventRecord(h->ev[0], h->stream));
   for (;;) {
+    h->factor_gen++;  // new factors: digits sliced from the old ones are stale
     const bool split = h->precision == RD_PREC_SPLIT_BF16 && h->split_floor >= 0;
     if (!split) {
       h->ordered = 0;  // the FP64 path works in the caller's node order

@@ -35,7 +35,12 @@
 #define RD_SCREEN_SOURCES 8  // BFS sources of the split path's range screen
 #define RD_SCREEN_CHUNK 256  // operand chunk along K that shares one scale (the split path's KAPPA)
 #define RD_SCREEN_CHUNK_ORDERED 64  // the same with the locality order
-#define RD_SCREEN_RESULT_BITS 40  // bits the digits must keep below a chunk's spread (2^-40 ~ 1e-12)
+// Bits the digits keep below a chunk's spread (2^-40 ~ 1e-12).  D is exact only while Y's relative
+// error stays below tau |ln gamma| (entries gamma^d of single paths sit exactly on the decode's
+// integer boundaries): 1.6e-10 at gamma = 0.85.  With 34 bits a directed path at gamma = 0.85
+// decoded wrongly (errors up to the self-check's 1e-9) although the six bench graphs, whose gains
+// are small, stayed exact at 6 % less step time.
+#define RD_SCREEN_RESULT_BITS 40
 // Weighted graphs: the operands of the inverse products are path sums restricted to the
 // elimination order, and with unequal edge weights those restricted paths can cost more than the
 // true shortest paths that the weighted spread samples.  The largest operand-chunk scale over a
@@ -53,6 +58,7 @@ struct rd_ctx {
   int32_t n = 0, N = 0;
   double gamma = 0.0, tau = 1e-9, max_colsum = 0.0;
   int weighted = 0;
+  unsigned long long factor_gen = 0;  // counts factorisations: keys reuse of derived data (sliced L^-1)
   int order_ready = 0;  // h->dOrd / h->dPos hold a locality order of the resident graph: 1 landmark, 2 scored
   int precision = RD_PREC_FP64;
   int slices_req = 0, slices = 0;

@@ -231,11 +231,11 @@ def screen_spread(A):
 SCREEN_CASES = {  # (graph, gain): the branch follows from spread x log2(1/gamma)
     "grid1000x40": lambda: (graphs.grid4(1000, 40), None),   # ~95 bits natural: locality order
     "grid600x16": lambda: (graphs.grid4(600, 16), None),     # ~65 bits: 15 digits
-    "dpath300_g0.85": lambda: (graphs.directed_path(300), 0.85),  # ~56 bits: 15 digits
-    "dpath300_g0.9": lambda: (graphs.directed_path(300), 0.9),    # ~36 bits: 12 digits
+    "dpath300_g0.85": lambda: (graphs.directed_path(300), 0.85),  # ~56 bits: 14 digits
+    "dpath300_g0.9": lambda: (graphs.directed_path(300), 0.9),    # ~36 bits: 11 digits
     "tree700": lambda: (graphs.binary_tree(700), None),      # a few levels per chunk
-    "ws1000": lambda: (graphs.ws(1000, 10, 0.1, 5), None),   # small world: 12 digits
-    "er800": lambda: (graphs.er(800, 0.02, 2), None),        # small world: 12 digits
+    "ws1000": lambda: (graphs.ws(1000, 10, 0.1, 5), None),   # small world
+    "er800": lambda: (graphs.er(800, 0.02, 2), None),        # small world
 }
 
 
