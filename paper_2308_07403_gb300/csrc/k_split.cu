@@ -401,18 +401,18 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, m0);
   if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, n0);
   if (p.b_tri == RD_TRI_UPPER) kend = min(kend, n0 + TN);
-  // chunks are aligned to absolute multiples of KP; the first and last may be partial.  With
-  // split K this CTA takes chunks [c_lo, c_hi) of the tile's range.
-  int cbeg = kbeg / KP;
-  int nchunks = (kbeg < kend) ? (kend + KP - 1) / KP - cbeg : 0;
-  if (p.ksplit > 1) {
-    const int c_lo = cbeg + (int)(((long long)nchunks * ks_idx) / p.ksplit);
-    const int c_hi = cbeg + (int)(((long long)nchunks * (ks_idx + 1)) / p.ksplit);
-    kbeg = max(kbeg, c_lo * KP);
-    kend = min(kend, c_hi * KP);
-    cbeg = c_lo;
-    nchunks = (kbeg < kend) ? c_hi - c_lo : 0;
+  // With split K this CTA takes K steps [s_lo, s_hi) of the tile's range (a share of a chunk
+  // keeps its group sums exact, and the chunk's scales are the same).  Chunks are aligned to
+  // absolute multiples of KP; the first and last may be partial.
+  if (p.ksplit > 1 && kbeg < kend) {
+    const int steps = (kend - kbeg) / TK;
+    const int s_lo = (int)(((long long)steps * ks_idx) / p.ksplit);
+    const int s_hi = (int)(((long long)steps * (ks_idx + 1)) / p.ksplit);
+    kend = kbeg + s_hi * TK;
+    kbeg = kbeg + s_lo * TK;
   }
+  const int cbeg = kbeg / KP;
+  const int nchunks = (kbeg < kend) ? (kend + KP - 1) / KP - cbeg : 0;
   const int s = p.s;
 
   if (threadIdx.x == 0) {
@@ -908,13 +908,14 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   a.col_map = col_map;
   const int tiles = (ma_pad / TM) * (nb_pad / TN);
   // split K when the tiles leave SMs idle (products of a few tiles: the goal and self-check rows,
-  // the middle of the recursion), up to two CTAs per SM; not with the fused decode
+  // the middle of the recursion), up to two CTAs per SM and 8 per tile, at least one K step
+  // (64) each; not with the fused decode
   int ksplit = 1;
-  const int nch = k_pad / h->kappa, sms = num_sms();
+  const int ksteps = K / TK, sms = num_sms();
   if (!D && a.store_c && tiles < sms) {
     ksplit = (2 * sms) / tiles;
     if (ksplit > 8) ksplit = 8;
-    if (ksplit > nch) ksplit = nch;
+    if (ksplit > ksteps) ksplit = ksteps;
     if (ksplit < 1) ksplit = 1;
   }
   a.ksplit = ksplit;
@@ -956,10 +957,11 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
 inline View full(const double* p, long long ld, int rows, int cols) { return View{p, ld, rows, cols, RD_TRI_FULL}; }
 inline View tri(const double* p, long long ld, int n, int mode) { return View{p, ld, n, n, mode}; }
 
-// Below this node size the recursion's products run in FP64 with small tiles: they are too
-// small to fill the tensor cores (one or a few 128 x 128 tiles), while an FP64 product on 16 x 16
-// tiles spreads over every SM.
-constexpr int FP64_NODE = 1024;
+// Up to this node size the recursion's products run in FP64 with small tiles: 256^3 products are
+// 4 tiles of 128 x 128, too few for the tensor cores even with split K, while an FP64 product on
+// 16 x 16 tiles spreads over every SM.  At n = 8192 the 512^3 products of the 1024-row nodes took
+// 167 us each in FP64; with split K over 64-wide K steps they fill the SMs on the tensor cores.
+constexpr int FP64_NODE = 512;
 
 cudaError_t product(rd_ctx* h, bool fp64, const View& A, const View& B, int M, int N, int K, double alpha,
                     double beta, double* C, long long ldc, double flops, cudaStream_t st) {
