@@ -227,54 +227,84 @@ __device__ __forceinline__ double view_load(const double* X, long long ld, int r
   return X[(long long)r * ld + c];
 }
 
-// exponent e of a chunk with largest magnitude `mx`: mx * 2^-e in [1/4, 1/2)
-__device__ __forceinline__ int chunk_exponent(double mx) { return mx > 0.0 ? ilogb(mx) + 2 : EXP_ZERO; }
+// |x| as an integer that orders like the value (the bit pattern of a non-negative double)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
 
-// balanced base-128 digits of x * 2^-e (|x| 2^-e < 1/2), most significant first, written to
-// plane p at out[p * plane]
-__device__ __forceinline__ void write_digits(double x, int e, int s, __nv_bfloat16* out, long long plane) {
+// exponent e of a chunk whose largest magnitude has the bit pattern mb: |mx| 2^-e in [1/4, 1/2)
+// (ilogb(mx) + 2, from the bits: no FP64 instruction)
+__device__ __forceinline__ int chunk_exponent_bits(unsigned long long mb) {
+  if (mb == 0) return EXP_ZERO;
+  const int ex = (int)(mb >> 52);
+  if (ex != 0) return ex - 1023 + 2;
+  return (63 - __clzll((long long)mb)) - 1074 + 2;  // subnormal: the leading mantissa bit
+}
+
+// F = round(|x| 2^(-e) 2^(7 s)) < 2^(7 s - 1) as F' 128^z: when the shift is a left shift,
+// F = (m 2^(sh mod 7)) 128^z with z zero digits at the least significant end and F' < 2^59;
+// otherwise F = round(m 2^sh) < 2^53 and z = 0 (m the 53-bit significand).
+struct DigitSrc {
+  uint64_t F;
+  int z;
+  bool neg;
+};
+__device__ __forceinline__ DigitSrc digit_src(double x, int e, int s) {
   const uint64_t bits = (uint64_t)__double_as_longlong(x);
-  const bool neg = (bits >> 63) != 0;
+  DigitSrc d;
+  d.neg = (bits >> 63) != 0;
+  d.F = 0;
+  d.z = 0;
   int ex = (int)((bits >> 52) & 0x7FF);
   uint64_t m = bits & ((1ull << 52) - 1);
   if (ex == 0)
     ex = 1;  // subnormal: no implicit bit
   else
     m |= (1ull << 52);
-  // F = round(|x| 2^(-e) 2^(7 s)) = m 2^(ex - 1075 - e + 7 s) < 2^(7 s - 1).  When the shift
-  // is a left shift, F = (m 2^(sh mod 7)) 128^z: its z lowest digits are zero (no carry), and
-  // the rest are the digits of m 2^(sh mod 7) < 2^59.  Otherwise F = round(m 2^sh) < 2^53.
-  uint64_t F = 0;
-  int z = 0;  // zero digits at the least significant end
   if (m != 0 && e != EXP_ZERO) {
     const int sh = ex - 1075 - e + SIGMA * s;
     if (sh >= 0) {
-      z = sh / SIGMA;
-      F = m << (sh - SIGMA * z);
+      d.z = sh / SIGMA;
+      d.F = m << (sh - SIGMA * d.z);
     } else if (sh > -64) {
       const uint64_t half = 1ull << (-sh - 1);  // round half up
-      F = (m + half) >> (-sh);              // m + half < 2^63
+      d.F = (m + half) >> (-sh);                // m + half < 2^63
     }
   }
-  for (int p = s - 1; p >= 1; --p) {
-    if (s - 1 - p < z) {
-      out[(long long)p * plane] = __float2bfloat16_rn(0.f);
-      continue;
-    }
-    int d = (int)(uint32_t)(F & 127u);
-    F >>= SIGMA;
-    if (d >= 64) {
-      d -= 128;
-      F += 1;
-    }
-    out[(long long)p * plane] = __float2bfloat16_rn((float)(neg ? -d : d));
-  }
-  const int d0 = (int)(uint32_t)F;
-  out[0] = __float2bfloat16_rn((float)(neg ? -d0 : d0));
+  return d;
 }
 
-// Role A (row chunks contiguous in memory): one warp per (row, chunk).
-// digits[p][row][k] (plane = rows_pad * k_pad), exps[chunk][row].
+// the next balanced base-128 digit (least significant first) of a DigitSrc; idx counts the
+// digits taken so far
+__device__ __forceinline__ int next_digit(DigitSrc& d, int idx) {
+  if (idx < d.z) return 0;
+  int v = (int)(uint32_t)(d.F & 127u);
+  d.F >>= SIGMA;
+  if (v >= 64) {
+    v -= 128;
+    d.F += 1;
+  }
+  return v;
+}
+
+// The balanced base-128 digits of x0 2^-e and x1 2^-e (|x| 2^-e < 1/2) for two adjacent K
+// positions, most significant first: digit plane p at out[p * plane], the pair in one 4-byte
+// store (out is 4-byte aligned).  Every digit is an integer in [-64, 64], exact in BF16.
+__device__ __forceinline__ void write_digits2(double x0, double x1, int e, int s, __nv_bfloat16* out,
+                                              long long plane) {
+  DigitSrc a = digit_src(x0, e, s), b = digit_src(x1, e, s);
+  for (int p = s - 1; p >= 1; --p) {
+    const int da = next_digit(a, s - 1 - p), db = next_digit(b, s - 1 - p);
+    *reinterpret_cast<__nv_bfloat162*>(out + (long long)p * plane) =
+        __floats2bfloat162_rn((float)(a.neg ? -da : da), (float)(b.neg ? -db : db));
+  }
+  const int ta = (int)(uint32_t)a.F, tb = (int)(uint32_t)b.F;
+  *reinterpret_cast<__nv_bfloat162*>(out) = __floats2bfloat162_rn((float)(a.neg ? -ta : ta), (float)(b.neg ? -tb : tb));
+}
+
+// Role A (row chunks contiguous in memory): one warp per (row, chunk), each lane taking pairs of
+// adjacent K positions c0 + 2 lane + 64 t.  digits[p][row][k] (plane = rows_pad * k_pad),
+// exps[chunk][row].
 template <int KP>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, long long ld, int tri,
                                                          int rows, int cols, int rows_pad, int k_pad, int s,
@@ -288,24 +318,28 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
   const int c0 = (int)(w % nch) * KP;
   const long long plane = (long long)rows_pad * k_pad;
   double v[KP / 32];
-  double mx = 0.0;
+  unsigned long long mb = 0;
 #pragma unroll
-  for (int t = 0; t < KP / 32; ++t) {
-    v[t] = view_load(X, ld, r, c0 + lane + 32 * t, tri, rows, cols);
-    mx = fmax(mx, fabs(v[t]));
+  for (int t = 0; t < KP / 64; ++t) {
+    const int c = c0 + 2 * lane + 64 * t;
+    v[2 * t] = view_load(X, ld, r, c, tri, rows, cols);
+    v[2 * t + 1] = view_load(X, ld, r, c + 1, tri, rows, cols);
+    mb = max(mb, max(abs_bits(v[2 * t]), abs_bits(v[2 * t + 1])));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const int e = chunk_exponent(mx);
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  const int e = chunk_exponent_bits(mb);
   if (lane == 0) exps[(long long)(c0 / KP) * rows_pad + r] = e;
 #pragma unroll
-  for (int t = 0; t < KP / 32; ++t) write_digits(v[t], e, s, dig + (long long)r * k_pad + c0 + lane + 32 * t, plane);
+  for (int t = 0; t < KP / 64; ++t)
+    write_digits2(v[2 * t], v[2 * t + 1], e, s, dig + (long long)r * k_pad + c0 + 2 * lane + 64 * t, plane);
   (void)status;
 }
 
 // Role B (the operand is K x N row-major; digits are wanted K-major per column): a block of 256
 // threads owns 16 columns of one chunk, stages the KP x 16 block through shared memory, and
-// each warp slices 2 columns.  digits[p][col][k], exps[chunk][col].
+// each warp slices 2 columns, each lane taking pairs of adjacent K positions.  digits[p][col][k],
+// exps[chunk][col].
 template <int KP>
 __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ X, long long ld, int tri,
                                                          int krows, int cols, int cols_pad, int k_pad, int s,
@@ -325,19 +359,21 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
   for (int cc = 0; cc < 2; ++cc) {
     const int col = warp * 2 + cc;
     double v[KP / 32];
-    double mx = 0.0;
+    unsigned long long mb = 0;
 #pragma unroll
-    for (int t = 0; t < KP / 32; ++t) {
-      v[t] = tile[lane + 32 * t][col];
-      mx = fmax(mx, fabs(v[t]));
+    for (int t = 0; t < KP / 64; ++t) {
+      v[2 * t] = tile[2 * lane + 64 * t][col];
+      v[2 * t + 1] = tile[2 * lane + 1 + 64 * t][col];
+      mb = max(mb, max(abs_bits(v[2 * t]), abs_bits(v[2 * t + 1])));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = chunk_exponent(mx);
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    const int e = chunk_exponent_bits(mb);
     const int n = n0 + col;
     if (lane == 0) exps[(long long)(c0 / KP) * cols_pad + n] = e;
 #pragma unroll
-    for (int t = 0; t < KP / 32; ++t) write_digits(v[t], e, s, dig + (long long)n * k_pad + c0 + lane + 32 * t, plane);
+    for (int t = 0; t < KP / 64; ++t)
+      write_digits2(v[2 * t], v[2 * t + 1], e, s, dig + (long long)n * k_pad + c0 + 2 * lane + 64 * t, plane);
   }
   (void)status;
 }
