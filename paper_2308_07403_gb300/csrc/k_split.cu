@@ -999,6 +999,28 @@ inline View tri(const double* p, long long ld, int n, int mode) { return View{p,
 // 167 us each in FP64; with split K over 64-wide K steps they fill the SMs on the tensor cores.
 constexpr int FP64_NODE = 512;
 
+rd_gemm_f64_args f64_args(const View& A, const View& B, int M, int N, int K, double alpha, double beta, double* C,
+                          long long ldc) {
+  rd_gemm_f64_args g{};
+  g.A = A.p;
+  g.lda = A.ld;
+  g.a_tri = A.tri;
+  g.B = B.p;
+  g.ldb = B.ld;
+  g.b_tri = B.tri;
+  g.C = C;
+  g.ldc = ldc;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.store_c = 1;
+  g.c_rows = M;
+  g.c_cols = N;
+  return g;
+}
+
 cudaError_t product(rd_ctx* h, bool fp64, const View& A, const View& B, int M, int N, int K, double alpha,
                     double beta, double* C, long long ldc, double flops, cudaStream_t st) {
   if (!fp64) return split_gemm(h, A, B, M, N, K, alpha, beta, C, ldc, M, N, nullptr, nullptr, flops, st);
@@ -1045,14 +1067,14 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
   // write to the scratch and the result is copied back.
   double* W0 = h->dS;  // free until the inverse products below
   if (f64) {
-    if ((e = product(h, true, tri(T11, N, m1, RD_TRI_LOWER_UNIT), full(A12, N, m1, m2), m1, m2, m1, 1.0, 0.0, W0, m2,
-                     2.0 * t1 * m2, st)) != cudaSuccess)
-      return e;
+    // the two independent products of the pair in one launch (each fills only part of the GPU)
+    double* W1 = h->dS + (long long)m1 * m2;
+    const rd_gemm_f64_args pr[2] = {
+        f64_args(tri(T11, N, m1, RD_TRI_LOWER_UNIT), full(A12, N, m1, m2), m1, m2, m1, 1.0, 0.0, W0, m2),
+        f64_args(full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_UPPER), m2, m1, m1, 1.0, 0.0, W1, m1)};
+    if ((e = rd_gemm_f64(h, pr, 2, st, 4.0 * t1 * m2)) != cudaSuccess) return e;
     if ((e = rd_copy_rows_out(h, W0, m2, m1, m2, A12, N, st)) != cudaSuccess) return e;
-    if ((e = product(h, true, full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_UPPER), m2, m1, m1, 1.0, 0.0, W0, m1,
-                     2.0 * t1 * m2, st)) != cudaSuccess)
-      return e;
-    if ((e = rd_copy_rows_out(h, W0, m1, m2, m1, A21, N, st)) != cudaSuccess) return e;
+    if ((e = rd_copy_rows_out(h, W1, m1, m2, m1, A21, N, st)) != cudaSuccess) return e;
   } else {
     if ((e = product(h, false, tri(T11, N, m1, RD_TRI_LOWER_UNIT), full(A12, N, m1, m2), m1, m2, m1, 1.0, 0.0, A12,
                      N, 2.0 * t1 * m2, st)) != cudaSuccess)
@@ -1069,6 +1091,19 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
   // L^-1_21 = -L22^-1 (L21 L11^-1) ; U^-1_12 = -U11^-1 (U12 U22^-1)
   double* SL = h->dS;                         // m2 x m1
   double* SU = h->dS + (long long)m1 * m2;    // m1 x m2
+  if (f64) {  // the L and U chains side by side, two problems per launch
+    const double fl = 2.0 * (m2 * t1 + m1 * t2);
+    const rd_gemm_f64_args w[2] = {
+        f64_args(full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_LOWER_UNIT), m2, m1, m1, 1.0, 0.0, SL, m1),
+        f64_args(full(A12, N, m1, m2), tri(T22, N, m2, RD_TRI_UPPER), m1, m2, m2, 1.0, 0.0, SU, m2)};
+    if ((e = rd_gemm_f64(h, w, 2, st, fl)) != cudaSuccess) return e;
+    const rd_gemm_f64_args x[2] = {
+        f64_args(tri(T22, N, m2, RD_TRI_LOWER_UNIT), full(SL, m1, m2, m1), m2, m1, m2, -1.0, 0.0,
+                 T + (long long)mid * N + lo, N),
+        f64_args(tri(T11, N, m1, RD_TRI_UPPER), full(SU, m2, m1, m2), m1, m2, m1, -1.0, 0.0, T + (long long)lo * N + mid,
+                 N)};
+    return rd_gemm_f64(h, x, 2, st, fl);
+  }
   if ((e = product(h, f64, full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_LOWER_UNIT), m2, m1, m1, 1.0, 0.0, SL, m1,
                    2.0 * t1 * m2, st)) != cudaSuccess)
     return e;
