@@ -53,12 +53,14 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--verify", type=int, default=1, help="hash D of every graph against the oracle's")
     p.add_argument("--cpu-sample", type=int, default=1536, help="oracle sample size (leading block)")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "serving", "weighted", "update"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "serving", "weighted", "update", "product"],
                    help="single: the n=8192 graphs (default); batched: 4096 graphs n~U[32,512] in one launch; "
                         "serving: a Poisson stream of requests over a pool of graphs; "
                         "weighted: n=32768 king grid, split inverse + 1024 goal rows + greedy; "
-                        "update: edge removals and restores on the n=8192 grid (Sherman-Morrison)")
+                        "update: edge removals and restores on the n=8192 grid (Sherman-Morrison); "
+                        "product: the inverse product with the fused decode alone, on resident split factors")
     p.add_argument("--obstacles", type=int, default=64, help="update: edge pairs removed, then restored")
+    p.add_argument("--product-n", type=int, default=4096, help="product: graph size")
     p.add_argument("--weighted-rows", type=int, default=128)
     p.add_argument("--weighted-cols", type=int, default=256)
     p.add_argument("--batch-graphs", type=int, default=4096)
@@ -796,8 +798,78 @@ def run_update(args):
     print(json.dumps(line), flush=True)
 
 
+PRODUCT_METRIC = "split inverse product Y = U^-1 L^-1 with the fused decode, issued digit-product TFLOP/s"
+
+
+def run_product(args):
+    """The largest split launch alone: the factors of an ER graph (p = 0.01, 0.5/Delta) are made once,
+    then rd_apsp re-runs only the inverse product with the fused decode (the factors stay
+    resident).  The timed launches run inside the NVTX range "inverse_product", so that an ncu
+    capture can select exactly them (--nvtx --nvtx-include inverse_product/)."""
+    import torch
+
+    from paper_2308_07403_gb300 import build, graphs, rd
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    rd.load()
+    n = args.product_n
+    A = graphs.er(n, 0.01, graphs.seed_for(1))
+    g = graphs.gamma_frac(A, 0.5)
+    stream = torch.cuda.current_stream(dev)
+    A_dev = torch.from_numpy(A).to(dev)
+    D = torch.empty((n, n), dtype=torch.int32, device=dev)
+    h = rd.rd_create(A_dev, n, g)
+    rd.rd_set_stream(h, stream.cuda_stream)
+    rd.rd_set_precision(h, rd.RD_PREC_SPLIT_BF16, 0)
+    rd.rd_apsp(h, D, None)  # factors, self-check, first product
+    for _ in range(max(3, args.warmup)):
+        rd.rd_apsp(h, D, None)
+    torch.cuda.synchronize()
+    rd.rd_set_profiling(h, True)
+    st0 = rd.rd_get_stats(h)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.nvtx.range_push("inverse_product")
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        rd.rd_apsp(h, D, None)
+    ev[1].record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    st = rd.rd_get_stats(h)
+    rd.rd_destroy(h)
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    kms = (st["prof_split_ms"] - st0["prof_split_ms"]) / args.steps
+    fl = (st["prof_split_flops"] - st0["prof_split_flops"]) / args.steps
+    pk, pk_kind = peaks()
+    achieved = fl / (kms * 1e-3) / 1e12
+    line = {
+        "metric": PRODUCT_METRIC, "value": achieved, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16-digits", "data": "synthetic",
+        "config": {"workload": f"ER n={n} p=0.01 at 0.5/Delta, split factors resident; Y = U^-1 L^-1 + decode",
+                   "n": n, "digits": st["slices"],
+                   "l2": "no flush: the digit planes of both operands exceed the 129 MB L2"},
+        "kernel_ms": kms, "effective_tflops_2n3_over_3": (2.0 * n ** 3 / 3.0) / (ms * 1e-3) / 1e12,
+        "roofline": {"kernel": "split_gemm_kernel", "bound": "tensor", "achieved": achieved,
+                     "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
+                     # DRAM bytes of this launch from the ncu capture of this build
+                     # (profiles/split_gemm_inverse_product_n4096.md); the kernel or the graph
+                     # changing makes it stale
+                     "traffic": 2.345e9 if (n == 4096 and st["slices"] == 9) else None,
+                     "traffic_unit": "B", "peak_source": f"{pk_kind} bf16 burst (cuBLAS)",
+                     "work": "issued BF16 digit products, s(s+1)/2 x 2MNK"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "product":
+        run_product(args)
+        return
     if args.workload == "update":
         run_update(args)
         return
