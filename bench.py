@@ -855,9 +855,8 @@ def run_product(args):
         "kernel_ms": kms, "effective_tflops_2n3_over_3": (2.0 * n ** 3 / 3.0) / (ms * 1e-3) / 1e12,
         "roofline": {"kernel": "split_gemm_kernel", "bound": "tensor", "achieved": achieved,
                      "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
-                     # DRAM bytes of this launch from the ncu capture of this build
-                     # (profiles/split_gemm_inverse_product_n4096.md); the kernel or the graph
-                     # changing makes it stale
+                     # DRAM bytes of this launch (read + write) from an ncu capture of this
+                     # kernel build on this graph; stale once either changes
                      "traffic": 2.345e9 if (n == 4096 and st["slices"] == 9) else None,
                      "traffic_unit": "B", "peak_source": f"{pk_kind} bf16 burst (cuBLAS)",
                      "work": "issued BF16 digit products, s(s+1)/2 x 2MNK"},
