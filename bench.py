@@ -455,7 +455,8 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
-SERVE_METRIC = "serving: Poisson 200 req/s over 128 graphs n log-uniform [64,4096], solves/s (p50/p99 latency)"
+def serve_metric(rate):
+    return f"serving: Poisson {rate:g} req/s over 128 graphs n log-uniform [64,4096], solves/s (p50/p99 latency)"
 
 
 def run_serving(args):
@@ -529,7 +530,7 @@ def run_serving(args):
     srv.close()
     n_req = len(plan)
     line = {
-        "metric": SERVE_METRIC, "value": n_req / wall, "unit": "solves/s", "n_gpus": 1, "steps": n_req,
+        "metric": serve_metric(args.serve_rate), "value": n_req / wall, "unit": "solves/s", "n_gpus": 1, "steps": n_req,
         "warmup": len(pool), "ms_per_step": wall * 1e3 / max(1, n_req), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16-digits+f64", "data": "synthetic",
         "config": {"workload": f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s over 128 graphs, "
