@@ -323,3 +323,31 @@ def test_split_full_size_D_identical(rd, kind, frac):
                if hashlib.sha256(np.ascontiguousarray(Dg[b * B:(b + 1) * B], dtype="<i4").tobytes())
                .hexdigest()[:16] != hx]
         pytest.fail(f"{len(bad)} of {len(rec['block_sha256_16'])} row blocks differ")
+
+
+def test_goal_rows_follow_reloaded_graphs(rd):
+    """The digits of the final L^-1 are reused between the inverse product, the self-check and the
+    goal products of one factorisation.  Loading another graph of the same size (same buffers,
+    same views), switching precision and back, and a second load must each give goal rows and D
+    of the graph now resident: parity with the oracle after every change."""
+    n = 1000
+    goals = np.array([0, 17, 500, 999], np.int32)
+    rows = np.empty((goals.size, n))
+    D = np.empty((n, n), np.int32)
+    cases = [graphs.er(n, 0.02, 11), graphs.ws(n, 10, 0.1, 12), graphs.er(n, 0.03, 13)]
+    with rd.Handle(cases[0], graphs.gamma_frac(cases[0], 0.5)) as h:
+        for step, A in enumerate(cases):
+            g = graphs.gamma_frac(A, 0.5)
+            if step:
+                h.load(A, g)
+            h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
+            h.apsp(D)
+            h.goal_solve(goals, rows)
+            Do, Yo = oracle.rdistance(A, g, want_y=True)
+            assert np.array_equal(D, Do), step
+            assert rel_err(rows, Yo[goals]) < YTOL, step
+            h.set_precision(rd.RD_PREC_FP64, 0)      # and back: the factors are recomputed
+            h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
+            h.goal_solve(goals, rows)
+            assert rel_err(rows, Yo[goals]) < YTOL, step
+        assert h.stats()["precision_used"] == rd.RD_PREC_SPLIT_BF16
