@@ -159,6 +159,16 @@ rd_status rd_set_tau(rd_handle h, double tau);
  * precision_used and fallbacks report what was used. */
 rd_status rd_apsp(rd_handle h, int32_t* D, double* Y);
 
+/* Bracket of the spectral radius of X = gamma A (or gamma^W): after `iters` (1..1e6) steps of
+ * power iteration on X^T + I over the graph's successor lists, *lo and *hi receive the
+ * Collatz-Wielandt bounds min_j and max_j of (B x)_j / x_j - 1, B = X^T + I, x > 0, which
+ * enclose rho(X) for every non-negative X and close in on it for a strongly connected graph.
+ * Theorem 1: the walk series sum gamma^k A^k (Sec. 3.1) converges, and Y = M^-1 is its sum, iff
+ * rho(X) < 1; the gain check of rd_create (largest column sum of X < 1, Theorem 4's condition) is
+ * the sufficient bound the factorisation needs.  Synchronises once.  RD_ERR_UNSUPPORTED for
+ * graphs of more than 2^31 edges. */
+rd_status rd_spectral_radius(rd_handle h, int32_t iters, double* lo, double* hi);
+
 /* Goal rows (the local mode of Sec. 4.2): for each goal g = goals[c], 0 <= c < k, writes row
  * g of Y, Y_out[c*n + j] = Y_{g j} (the signal from j at the goal), by solving M^T y = e_g on
  * the resident LU factors (factoring first if needed).  1 <= k <= 64; goals in [0, n). */

@@ -111,6 +111,18 @@ def build_m(A, gamma: float, W=None) -> np.ndarray:
     return M
 
 
+def spectral_radius(A, gamma: float = 1.0, W=None) -> float:
+    """rho(X) for X = gamma A (or gamma^W on the edges): the largest eigenvalue modulus, from a
+    dense eigenvalue routine (a library primitive).  Theorem 1: the walk series of Sec. 3.1
+    converges iff rho(X) < 1.  Plain numpy, for tests."""
+    n = np.asarray(A).shape[0]
+    if n == 0:
+        return 0.0
+    X = np.asarray(A, dtype=np.float64) * gamma if W is None else \
+        np.where(np.asarray(A) != 0, np.power(gamma, np.asarray(W, dtype=np.float64)), 0.0)
+    return float(np.max(np.abs(np.linalg.eigvals(X))))
+
+
 def max_column_sum(M: np.ndarray) -> float:
     M = np.ascontiguousarray(M, dtype=np.float64)
     return float(_load().rdo_max_column_sum(_ptr(M), M.shape[0]))

@@ -11,6 +11,8 @@
 // per step and writes consecutive doubles of M.
 #include <vector>
 
+#include <cstring>
+
 #include "rd_internal.cuh"
 
 namespace {
@@ -582,6 +584,47 @@ cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s) {
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }
 
+// ---- spectral radius of X (the convergence condition of Theorem 1) ----------------------------
+//
+// Power iteration on B = X^T + I over the successor lists (a gather: y_j = x_j + sum over the
+// successors i of j of X_ij x_i), which has the spectral radius rho(X) + 1 and keeps x positive.
+// For a non-negative matrix and a positive vector, min_j (Bx)_j / x_j <= rho(B) <= max_j
+// (Bx)_j / x_j (Collatz-Wielandt); the step reports both ratios and the largest y (bits of
+// positive doubles, ordered as integers), one warp per node.
+__global__ void spectral_step_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ succ,
+                                     const float* __restrict__ w, double gamma, double log_gamma, int n,
+                                     const double* __restrict__ x, double* __restrict__ y,
+                                     unsigned long long* __restrict__ red) {
+  const int lane = threadIdx.x & 31;
+  const int j = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (j >= n) return;
+  double acc = 0.0;
+  for (int q = ptr[j] + lane; q < ptr[j + 1]; q += 32) {
+    const double xe = w ? exp((double)w[q] * log_gamma) : gamma;
+    acc += xe * x[succ[q]];
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const double yj = x[j] + acc;
+    y[j] = yj;
+    const unsigned long long rb = (unsigned long long)__double_as_longlong(yj / x[j]);
+    atomicMin(&red[0], rb);
+    atomicMax(&red[1], rb);
+    atomicMax(&red[2], (unsigned long long)__double_as_longlong(yj));
+  }
+}
+
+__global__ void spectral_scale_kernel(const double* __restrict__ y, int n, const unsigned long long* __restrict__ red,
+                                      double* __restrict__ x) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) x[j] = y[j] / __longlong_as_double((long long)red[2]);
+}
+
+__global__ void fill_kernel(double* __restrict__ x, int n, double v) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) x[j] = v;
+}
+
 cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows, int cols,
                              double* out, long long ldo, cudaStream_t s) {
   const long long total = (long long)rows * cols;
@@ -593,6 +636,42 @@ cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows
                                                                                  out, ldo);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
+}
+
+// Collatz-Wielandt bracket of rho(X) after `iters` steps (successor lists built; x, y: n doubles
+// each, red: 3 words).  Synchronises once.
+cudaError_t rd_spectral(rd_ctx* h, int iters, double* x, double* y, unsigned long long* red, double* lo, double* hi,
+                        cudaStream_t s) {
+  const int n = h->n;
+  const int32_t* ptr = h->dDeg + (n + 1);
+  const unsigned long long init[3] = {~0ull, 0ull, 0ull};
+  unsigned long long out[3] = {0, 0, 0};
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
+  if (e != cudaSuccess) return e;
+  fill_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, n, 1.0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  for (int it = 0; it < iters; ++it) {
+    if ((e = cudaMemcpyAsync(red, init, sizeof(init), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
+    spectral_step_kernel<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, s>>>(
+        ptr, h->dSucc, h->weighted ? h->dSuccW : nullptr, h->gamma, log(h->gamma), n, x, y, red);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+    if (it + 1 == iters) break;  // the last step's x is the one the ratios refer to
+    if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
+    spectral_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(y, n, red, x);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
+  }
+  if ((e = cudaMemcpyAsync(out, red, sizeof(out), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  double rmin, rmax;
+  memcpy(&rmin, &out[0], sizeof(double));
+  memcpy(&rmax, &out[1], sizeof(double));
+  *lo = rmin - 1.0 > 0.0 ? rmin - 1.0 : 0.0;
+  *hi = rmax - 1.0 > 0.0 ? rmax - 1.0 : 0.0;
+  return cudaSuccess;
 }
 
 cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, const int32_t* ord, int32_t* dist,

@@ -705,6 +705,21 @@ rd_status rd_goal_solve(rd_handle h, const int32_t* goals, int32_t k, double* Y_
   return RD_OK;
 }
 
+rd_status rd_spectral_radius(rd_handle h, int32_t iters, double* lo, double* hi) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  if (!lo || !hi) return fail(h, RD_ERR_ARG, "lo and hi must not be NULL");
+  if (iters < 1 || iters > 1000000) return fail(h, RD_ERR_ARG, "iters must lie in [1, 1000000]");
+  if (!h->dSucc) return fail(h, RD_ERR_UNSUPPORTED, "no successor lists (more than 2^31 edges)");
+  RD_CK(h, cudaSetDevice(h->device));
+  if (!h->succ_ready) {
+    RD_CK(h, rd_build_succ(h, h->stream));
+    h->succ_ready = 1;
+  }
+  RD_CK(h, rd_spectral(h, iters, h->dR, h->dR + h->n, reinterpret_cast<unsigned long long*>(h->dRed), lo, hi,
+                       h->stream));
+  return RD_OK;
+}
+
 rd_status rd_greedy_next(rd_handle h, const int32_t* goals, int32_t k, const double* Yrows, int32_t* next) {
   if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
   if (!Yrows || !next) return fail(h, RD_ERR_ARG, "Yrows and next must not be NULL");

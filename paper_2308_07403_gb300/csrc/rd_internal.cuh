@@ -184,6 +184,9 @@ cudaError_t rd_chunk_spread(rd_ctx* h, int nsrc, int chunk, const int32_t* ord, 
 // locality order for the split path (dOrd, dPos; uses dS as scratch; synchronises once): the
 // landmark bisection (scored = 0) or the bisection that scores four keys per part (scored = 1)
 cudaError_t rd_locality_order(rd_ctx* h, int scored, cudaStream_t s);
+// Collatz-Wielandt bracket [lo, hi] of the spectral radius of X after iters power-iteration steps
+cudaError_t rd_spectral(rd_ctx* h, int iters, double* x, double* y, unsigned long long* red, double* lo, double* hi,
+                        cudaStream_t s);
 // dLU <- P M P^T (the permuted M; dT is used as the staging buffer and swapped in)
 cudaError_t rd_permute_m(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows, int cols,

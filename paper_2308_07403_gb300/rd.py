@@ -45,6 +45,7 @@ _SIGS = {
     "rd_apsp": (ctypes.c_int, [_P, _P, _P]),
     "rd_goal_solve": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
     "rd_greedy_next": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "rd_spectral_radius": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "rd_set_profiling": (ctypes.c_int, [_P, ctypes.c_int32]),
     "rd_sync": (ctypes.c_int, [_P]),
     "rd_get_stats": (ctypes.c_int, [_P, _P]),
@@ -184,6 +185,13 @@ def rd_set_tau(h, tau: float):
     _check(load().rd_set_tau(h, float(tau)), h)
 
 
+def rd_spectral_radius(h, iters: int = 200):
+    """(lo, hi): Collatz-Wielandt bracket of the spectral radius of X after `iters` power steps."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(load().rd_spectral_radius(h, int(iters), ctypes.byref(lo), ctypes.byref(hi)), h)
+    return lo.value, hi.value
+
+
 def rd_apsp(h, D, Y=None):
     _np_out(D)
     _np_out(Y)
@@ -282,6 +290,9 @@ class Handle:
 
     def sync(self):
         rd_sync(self.h)
+
+    def spectral_radius(self, iters=200):
+        return rd_spectral_radius(self.h, iters)
 
     def stats(self):
         return rd_get_stats(self.h)

@@ -357,3 +357,20 @@ def test_decode_vector_matches_matrix_decode(oracle_lib):
     for i in (0, 45, 89):
         assert np.array_equal(oracle.decode_vector(Y[i], i, g), D[i])
         assert np.array_equal(oracle.decode_vector(Y[:, i], i, g), D[:, i])
+
+
+def test_spectral_radius_closed_forms():
+    """rho(X) of Theorem 1's convergence condition, pinned by spectra known in closed form: a
+    directed cycle (the n-th roots of unity: 1), the complete graph K_n (n - 1), a directed path
+    (nilpotent: 0), the undirected path P_n (2 cos(pi / (n + 1))), Example 4.1's three-node path
+    (sqrt 2), and the scaling rho(gamma A) = gamma rho(A)."""
+    assert oracle.spectral_radius(graphs.directed_cycle(7)) == pytest.approx(1.0, abs=1e-12)
+    assert oracle.spectral_radius(graphs.complete(5)) == pytest.approx(4.0, abs=1e-12)
+    assert oracle.spectral_radius(graphs.directed_path(6)) == pytest.approx(0.0, abs=1e-12)
+    assert oracle.spectral_radius(graphs.path3()) == pytest.approx(np.sqrt(2.0), abs=1e-12)
+    n = 11
+    P = np.zeros((n, n), np.uint8)
+    for i in range(n - 1):
+        P[i, i + 1] = P[i + 1, i] = 1
+    assert oracle.spectral_radius(P) == pytest.approx(2.0 * np.cos(np.pi / (n + 1)), abs=1e-12)
+    assert oracle.spectral_radius(P, 0.3) == pytest.approx(0.6 * np.cos(np.pi / (n + 1)), abs=1e-12)
