@@ -427,11 +427,30 @@ __global__ void __launch_bounds__(THREADS, 1)
   int16_t* ref_s = (int16_t*)(smem + REF_OFFSET);                // [TN][TM], column-major
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int tiles_n = (p.N + TN - 1) / TN;
+  const int tiles_n = (p.N + TN - 1) / TN, tiles_m = (p.M + TM - 1) / TM;
   const int ks_idx = (int)(blockIdx.x % (unsigned)p.ksplit);
   const int tile = (int)(blockIdx.x / (unsigned)p.ksplit);
-  const int m0 = (tile / tiles_n) * TM;
-  const int n0 = (tile % tiles_n) * TN;
+  // Longest tiles first (the block scheduler starts CTAs in index order, so the last wave then
+  // holds the short ones): with a triangular operand the K range of a tile depends on its row or
+  // column (see kbeg / kend below).
+  int tr = tile / tiles_n, tc = tile % tiles_n;
+  if (p.a_tri == RD_TRI_UPPER && p.b_tri == RD_TRI_LOWER_UNIT && tiles_m == tiles_n) {
+    // K from max(row, col) on: shells of equal max(tr, tc), the outermost (shortest) last
+    const int sh = (int)sqrtf((float)tile);
+    const int shell = (sh + 1) * (sh + 1) <= tile ? sh + 1 : (sh * sh > tile ? sh - 1 : sh);
+    const int o = tile - shell * shell;  // 0 .. 2 shell
+    tr = o <= shell ? o : shell;
+    tc = o <= shell ? shell : o - shell - 1;
+  } else if (p.a_tri == RD_TRI_FULL && p.b_tri != RD_TRI_FULL) {
+    // K depends on the tile column alone: column-major, so that a wave takes whole columns
+    tr = tile % tiles_m;
+    tc = tile / tiles_m;
+    if (p.b_tri == RD_TRI_UPPER) tc = tiles_n - 1 - tc;  // K up to the column's end: the last columns first
+  } else if (p.a_tri == RD_TRI_LOWER_UNIT) {
+    tr = tiles_m - 1 - tr;  // K up to the tile row's end
+  }
+  const int m0 = tr * TM;
+  const int n0 = tc * TN;
   int kbeg = 0, kend = p.K;
   if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, m0 + TM);
   if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, m0);
