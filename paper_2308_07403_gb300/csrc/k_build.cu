@@ -81,13 +81,26 @@ __global__ void scan_kernel(const int32_t* __restrict__ deg, int n, int32_t* __r
   if (n == 0 && t == 0) ptr[0] = 0;
 }
 
-// successors of node v: {j : A[j][v] != 0} (edge v -> j), ascending j; with W, also the edge weights
-__global__ void succ_fill_kernel(const uint8_t* __restrict__ A, const float* __restrict__ W, int n,
-                                 const int32_t* __restrict__ ptr, int32_t* __restrict__ idx, float* __restrict__ wt) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+// successors of node v: {j : A[j][v] != 0} (edge v -> j), ascending j; with W, also the edge weights.
+// A block owns 32 consecutive columns (lane = column): its 8 warps split the rows into 8 ranges,
+// count each column's non-zeros per range, offset the ranges by a prefix over the warps, and write
+// in a second pass, so the lists come out in ascending j with coalesced row reads.
+__global__ void __launch_bounds__(256) succ_fill_kernel(const uint8_t* __restrict__ A, const float* __restrict__ W,
+                                                        int n, const int32_t* __restrict__ ptr,
+                                                        int32_t* __restrict__ idx, float* __restrict__ wt) {
+  __shared__ int cnt[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int v = blockIdx.x * 32 + lane;
+  const int rows = (n + 7) / 8, j0 = warp * rows, j1 = min(n, j0 + rows);
+  int c = 0;
+  if (v < n)
+    for (int j = j0; j < j1; ++j) c += A[(long long)j * n + v] != 0;
+  cnt[warp][lane] = c;
+  __syncthreads();
   if (v >= n) return;
   int w = ptr[v];
-  for (int j = 0; j < n; ++j)
+  for (int q = 0; q < warp; ++q) w += cnt[q][lane];
+  for (int j = j0; j < j1; ++j)
     if (A[(long long)j * n + v]) {
       if (W) wt[w] = W[(long long)j * n + v];
       idx[w++] = j;
@@ -578,8 +591,8 @@ cudaError_t rd_build_succ(rd_ctx* h, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
-  succ_fill_kernel<<<(h->n + 127) / 128, 128, 0, s>>>(h->dA, h->weighted ? h->dW : nullptr, h->n, ptr, h->dSucc,
-                                                      h->dSuccW);
+  succ_fill_kernel<<<(h->n + 31) / 32, 256, 0, s>>>(h->dA, h->weighted ? h->dW : nullptr, h->n, ptr, h->dSucc,
+                                                    h->dSuccW);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }
