@@ -206,12 +206,14 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[8]) {
 
 // store 8 columns of this warp's 32 lanes, then wait for it (registers and columns are free
 // to reuse after the call)
+// 8 columns of this warp's lanes to tensor memory; the write completes at the next tmem_wait_st
+// (each pass of the epilogue stores distinct columns, then waits once before they are read again)
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
                "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
                : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---- slicing --------------------------------------------------------------------------------
 
@@ -591,6 +593,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int q = 0; q < 8; ++q) z[q] = 0u;
 #pragma unroll
       for (int t = 0; t < 8; ++t) tmem_st8(tl + TMEM_LO + t * 8, z);
+      tmem_wait_st();
     }
 #pragma unroll
     for (int j = 0; j < 64; ++j) {
@@ -642,6 +645,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         tmem_st8(tl + TMEM_LO + t * 8, lr);
         tmem_st8(tl + TMEM_SCALE + t * 8, sr);
       }
+      tmem_wait_st();
       for (int g = 0; g < s; ++g, ++gi) {
         const int buf = gi & 1;
         const uint32_t use = (uint32_t)(gi >> 1);
@@ -678,6 +682,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           tmem_st8(tl + TMEM_LO + t * 8, lr);
         }
+        tmem_wait_st();
       }
     }
     // final values, 16 columns at a time (the tensor-memory loads are warp-wide: outside any
