@@ -106,7 +106,7 @@ rd_status check_device_status(rd_ctx* h) {
 // successor lists (and, for a weighted graph, their edge weights) for `edges` edges
 rd_status ensure_succ_capacity(rd_ctx* h, int64_t edges) {
   const bool need_w = h->weighted && !h->dSuccW;
-  if (edges <= h->succ_cap && !need_w) return RD_OK;
+  if (h->dSucc && edges <= h->succ_cap && !need_w) return RD_OK;  // (a graph without edges still gets lists)
   const int64_t cap = edges > h->succ_cap ? edges + edges / 8 + 1024 : h->succ_cap;
   if (h->dSucc) cudaFree(h->dSucc);
   if (h->dSuccW) cudaFree(h->dSuccW);

@@ -198,3 +198,31 @@ def test_errors(rd):
         D = np.empty((100, 100), np.int32)
         h.apsp(D)
         assert np.array_equal(D, oracle.rdistance(A, 0.5 / delta))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+@pytest.mark.parametrize("n", [1, 2, 65, 300])
+def test_degenerate_graphs(rd, n, precision):
+    """No edges at all (Y = I: D is 0 on the diagonal and the unreachable sentinel elsewhere) and a
+    single node, in both precisions; goal rows are the unit rows and every greedy next hop is -1."""
+    A = np.zeros((n, n), np.uint8)
+    prec = (rd.RD_PREC_FP64, 0) if precision == "fp64" else (rd.RD_PREC_SPLIT_BF16, 0)
+    D, Y = run_gpu(rd, A, 0.5, precision=prec)
+    Do, Yo = oracle.rdistance(A, 0.5, want_y=True)
+    assert np.array_equal(D, Do)
+    assert np.array_equal(Y, np.eye(n)) and np.array_equal(Yo, np.eye(n))
+    goals = np.arange(min(n, 4), dtype=np.int32)
+    rows = np.empty((goals.size, n))
+    nxt = np.empty((goals.size, n), np.int32)
+    with rd.Handle(A, 0.5) as h:
+        h.set_precision(*prec)
+        h.goal_solve(goals, rows)
+        h.greedy_next(goals, rows, nxt)
+    assert np.array_equal(rows, np.eye(n)[goals])
+    assert np.array_equal(nxt, oracle.greedy_next(A, goals, rows))
+
+
+def test_empty_graph_is_refused(rd):
+    with pytest.raises(rd.RDError) as ei:
+        rd.Handle(np.zeros((0, 0), np.uint8), 0.5)
+    assert ei.value.status == rd.RD_ERR_ARG
