@@ -19,6 +19,12 @@ namespace {
 
 // M for the rows of one row block; per-column edge counts and column sums are added with atomics
 // (the column sums only feed the gain check, so their summation order does not matter).
+// the edge j -> i exists: A_ij != 0 and, on a weighted graph, a finite weight (W_ij = +inf is the
+// weight of a missing edge, Sec. 3.2: gamma^inf = 0)
+__device__ __forceinline__ bool edge_on(const uint8_t* __restrict__ A, const float* __restrict__ W, long long at) {
+  return A[at] != 0 && (!W || W[at] < __int_as_float(0x7f800000));
+}
+
 __global__ void build_m_kernel(const uint8_t* __restrict__ A, const float* __restrict__ W, int n, int N,
                                int rows_per_block, double gamma, double* __restrict__ M,
                                int32_t* __restrict__ deg, double* __restrict__ colsum) {
@@ -30,7 +36,7 @@ __global__ void build_m_kernel(const uint8_t* __restrict__ A, const float* __res
   double cs = 0.0;
   for (int i = r0; i < r1; ++i) {
     double x = 0.0;
-    if (i < n && j < n && A[(long long)i * n + j]) {
+    if (i < n && j < n && edge_on(A, W, (long long)i * n + j)) {
       ++cnt;
       x = W ? pow(gamma, (double)W[(long long)i * n + j]) : gamma;
       cs += x;
@@ -94,14 +100,14 @@ __global__ void __launch_bounds__(256) succ_fill_kernel(const uint8_t* __restric
   const int rows = (n + 7) / 8, j0 = warp * rows, j1 = min(n, j0 + rows);
   int c = 0;
   if (v < n)
-    for (int j = j0; j < j1; ++j) c += A[(long long)j * n + v] != 0;
+    for (int j = j0; j < j1; ++j) c += edge_on(A, W, (long long)j * n + v);
   cnt[warp][lane] = c;
   __syncthreads();
   if (v >= n) return;
   int w = ptr[v];
   for (int q = 0; q < warp; ++q) w += cnt[q][lane];
   for (int j = j0; j < j1; ++j)
-    if (A[(long long)j * n + v]) {
+    if (edge_on(A, W, (long long)j * n + v)) {
       if (W) wt[w] = W[(long long)j * n + v];
       idx[w++] = j;
     }

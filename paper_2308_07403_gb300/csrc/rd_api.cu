@@ -637,15 +637,17 @@ rd_status rd_update_edge(rd_handle h, int32_t i, int32_t j, int32_t present, flo
   if (h->weighted) RD_CK(h, cudaMemcpyAsync(&w_old, h->dW + at, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
   RD_CK(h, cudaMemcpyAsync(&colsum, h->dColsum + j, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   RD_CK(h, cudaStreamSynchronize(h->stream));
-  const double x_old = a_old ? (h->weighted ? std::pow(h->gamma, (double)w_old) : h->gamma) : 0.0;
+  // an edge of infinite weight is a missing edge (gamma^inf = 0): not counted in the degrees
+  const bool old_on = a_old != 0 && (!h->weighted || std::isfinite(w_old));
+  const double x_old = old_on ? (h->weighted ? std::pow(h->gamma, (double)w_old) : h->gamma) : 0.0;
   const double x_new = present ? (h->weighted ? std::pow(h->gamma, (double)w) : h->gamma) : 0.0;
   const double delta = x_new - x_old;
   if (!(colsum + delta < 1.0)) return fail(h, RD_ERR_GAMMA, "the update would make a column sum of X reach 1");
   rd_status st;
   if (!h->y_current && (st = materialize_y(h, dD)) != RD_OK) return st;
   unsigned int* lost = reinterpret_cast<unsigned int*>(h->dRed);
-  if (delta != 0.0 || (a_old != 0) != (present != 0) || (present && w != w_old)) {
-    const int ddeg = (present ? 1 : 0) - (a_old ? 1 : 0);
+  if (delta != 0.0 || old_on != (present != 0) || (present && w != w_old)) {
+    const int ddeg = (present ? 1 : 0) - (old_on ? 1 : 0);
     h->n_edges += ddeg;
     if ((st = ensure_succ_capacity(h, h->n_edges)) != RD_OK) return st;
     RD_CK(h, rd_set_edge(h, i, j, present ? 1 : 0, present ? w : 0.f, delta, ddeg, h->stream));

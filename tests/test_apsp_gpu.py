@@ -226,3 +226,42 @@ def test_empty_graph_is_refused(rd):
     with pytest.raises(rd.RDError) as ei:
         rd.Handle(np.zeros((0, 0), np.uint8), 0.5)
     assert ei.value.status == rd.RD_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_infinite_weights_are_absent_edges(rd, precision):
+    """W may be +inf on an edge (Sec. 3.2: the weight of a missing edge): gamma^inf = 0, so the
+    result equals that of the graph without those edges, and the oracle's."""
+    A, W, g = graphs.workload_weighted(12, 16)
+    rng = np.random.default_rng(5)
+    ii, jj = np.nonzero(A)
+    cut = rng.random(ii.size) < 0.2
+    Winf = W.copy()
+    Winf[ii[cut], jj[cut]] = np.inf
+    Acut = A.copy()
+    Acut[ii[cut], jj[cut]] = 0
+    prec = (rd.RD_PREC_FP64, 0) if precision == "fp64" else (rd.RD_PREC_SPLIT_BF16, 0)
+    D, Y = run_gpu(rd, A, g, W=Winf, precision=prec)
+    Do, Yo = oracle.rdistance(Acut, g, W=W, want_y=True)
+    assert np.array_equal(D, Do)
+    y_close(Y, Yo)
+    # the greedy step never takes an edge of infinite weight
+    goals = np.array([0, 77, 191], np.int32)
+    rows = np.empty((goals.size, A.shape[0]))
+    nxt = np.empty((goals.size, A.shape[0]), np.int32)
+    with rd.Handle(A, g, W=Winf) as h:
+        h.set_precision(*prec)
+        h.goal_solve(goals, rows)
+        h.greedy_next(goals, rows, nxt)
+    assert np.array_equal(nxt, oracle.greedy_next(Acut, goals, rows))
+
+
+def test_zero_weight_breaks_the_gain_condition(rd):
+    """A zero weight makes X_ij = gamma^0 = 1: the column sum of X reaches 1, refused."""
+    A, W, g = graphs.workload_weighted(8, 8)
+    W0 = W.copy()
+    i, j = (int(x[0]) for x in np.nonzero(A))
+    W0[i, j] = 0.0
+    with pytest.raises(rd.RDError) as ei:
+        rd.Handle(A, g, W=W0)
+    assert ei.value.status == rd.RD_ERR_GAMMA
