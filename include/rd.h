@@ -142,8 +142,9 @@ rd_status rd_set_stream(rd_handle h, void* stream);
  * order (compact 64-node parts, 64-wide chunks: rd_stats.split_order) and takes it when it needs
  * fewer; beyond 15 digits (22 in the locality order) the graph runs in FP64
  * (rd_stats.split_screen_bits, rd_stats.slices).  It then checks every split factorisation,
- * before any product uses it: 64 sampled rows of Y must satisfy y^T M = e_g^T to a relative 1e-9
- * per entry (rd_stats.split_residual).  When the check fails it recomputes the graph's inverse with
+ * before any product uses it: 64 sampled rows of Y must satisfy y^T M = e_g^T to a relative
+ * min(1e-9, tau |ln gamma| / 16) per entry, at least 1e-12 (rd_stats.split_residual; D is exact
+ * while Y's relative error stays below tau |ln gamma|).  When the check fails it recomputes the graph's inverse with
  * the digits the residual r asks for (about log2(r / 2^-40) / 7 more), or in FP64 beyond the
  * order's limit.  Drops cached factors when the mode changes. */
 rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices);

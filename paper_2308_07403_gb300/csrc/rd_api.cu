@@ -8,6 +8,7 @@
 //   factor:   blocked no-pivot LU of M (FP64, or split BF16 products on the tensor cores)
 //   inverse:  blocked triangular inverses L^-1, U^-1
 //   product:  Y = U^-1 L^-1 with D = ceil(log_gamma Y - tau) fused into the epilogue
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -229,11 +230,20 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
 }
 
 // Split mode with the self-check: after the factorisation, 64 sampled rows of Y (computed with
-// the same digit products) must satisfy y^T M = e_g^T to RD_SPLIT_RESIDUAL per entry.  When the
+// the same digit products) must satisfy y^T M = e_g^T to residual_limit(h) per entry.  When the
 // caller leaves the digit count open, the library starts where the range screen says; a failed
 // check sets the next count from the residual (escalate) or moves the graph to FP64, and the
 // inverse is recomputed from M.
 bool split_auto(const rd_ctx* h) { return h->precision == RD_PREC_SPLIT_BF16 && h->slices_req == 0; }
+
+// The sampled-row residual a split result must meet.  D is exact while Y's relative error stays
+// below tau |ln gamma| (the decode snaps within tau of an integer, and single-path entries gamma^d
+// sit exactly on integers): the limit is that over 16, at most RD_SPLIT_RESIDUAL and at least
+// 1e-12 (tau = 0 asks for no snap at all).
+double residual_limit(const rd_ctx* h) {
+  const double lim = h->tau * std::fabs(std::log(h->gamma)) / 16.0;
+  return std::min(RD_SPLIT_RESIDUAL, std::max(lim, 1e-12));
+}
 
 double choose_locality_order(rd_ctx* h, double wf, rd_status* st);
 
@@ -398,7 +408,7 @@ rd_status ensure_factored(rd_ctx* h) {
       double worst = 0.0;
       RD_CK(h, rd_split_row_check(h, &worst, h->stream));
       h->last_residual = worst;
-      if (worst > RD_SPLIT_RESIDUAL) {
+      if (worst > residual_limit(h)) {
         // failed: more digits as the residual asks, or FP64; the loop factors M again
         if ((st = escalate(h, worst)) != RD_OK) return st;
         continue;
