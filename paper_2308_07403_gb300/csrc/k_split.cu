@@ -23,12 +23,17 @@
 // The operands of every product of the inverse are sign-definite, so the accumulated value is
 // accurate relative to itself; the digit count s sets the precision.
 //
-// Kernel structure (one CTA per 128 x 128 output tile, 320 threads):
-//   warp 0      TMA producer: digit tiles A_p[128 x 64] and B_q[128 x 64] into a 4-stage ring
+// Kernel structure (one CTA per 128 x 128 output tile, 320 threads, 512 tensor-memory columns):
+//   warp 0      TMA producer: digit tiles A_p[128 x 64] and B_q[128 x 64] into a 3-stage ring,
+//               two (pair, K step) items per stage
 //   warp 1      TMEM allocator and MMA issuer (one thread): tcgen05.mma.kind::f16, M=N=128,
-//               K=16, accumulators double-buffered in tensor memory (2 x 128 columns)
-//   warps 2..9  epilogue: tcgen05.ld of each group sum, float-float accumulation, final
-//               FP64 scale, the C update or the fused R-distance decode
+//               K=16, 8 MMAs per wait; group accumulators double-buffered in tensor memory
+//               (columns 0..255)
+//   warps 2..9  epilogue: tcgen05.ld of each group sum, float-float accumulation with the low
+//               words and each chunk's per-entry scale in tensor memory (columns 256..511),
+//               final FP64 scale, the C update, a split-K partial, or the fused decode
+// Tiles are launched longest K range first (triangular operands), and products of fewer tiles
+// than SMs split K over several CTAs per tile (partials summed by ksplit_reduce_kernel).
 // Every wait is bounded (about four seconds of %globaltimer); on expiry the CTA records
 // RD_DEV_TIMEOUT, every role leaves its loop, and the tensor memory is freed.
 //
