@@ -6,9 +6,13 @@
 // Delta) and, for weighted graphs, the column sum of X; the host accepts the gain when the
 // largest column sum of X is below one (strict column diagonal dominance of M).
 //
-// The kernels are HBM-bound streams over the n x n byte matrix (and the N x N FP64 M): one
-// thread per column walks down a block of rows, so a warp reads 32 consecutive bytes of a row
-// per step and writes consecutive doubles of M.
+// The build is an HBM-bound stream over the n x n byte matrix (and the N x N FP64 M): one thread
+// per column walks down a block of rows, so a warp reads 32 consecutive bytes of a row per step
+// and writes consecutive doubles of M.  The successor lists (8 warps per 32 columns) serve the
+// greedy next hop, the split path's range screen (chunk_spread_kernel: BFS or Bellman-Ford
+// spreads), its locality order (landmark_kernel, rcb_kernel: landmark and scored bisections into
+// 64-node parts, permute_m_kernel) and the spectral-radius bracket of Theorem 1's condition
+// (spectral_step_kernel).
 #include <vector>
 
 #include <cstring>
