@@ -764,7 +764,9 @@ __global__ void row_residual_kernel(const double* __restrict__ rows, const int32
       scale += fabs(term);
     }
     (void)A;
-    worst = scale > 0.0 ? fabs(acc) / scale : (acc != 0.0 ? 1.0 : 0.0);
+    // an entry whose scale lies in FP64's subnormal range holds no digits to check (far entries
+    // of a graph whose Y spans more than FP64's exponent range underflow on any path)
+    worst = scale >= 0x1p-1022 ? fabs(acc) / scale : 0.0;
     if (!(worst <= 1.0)) worst = 1.0;
   }
   for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
