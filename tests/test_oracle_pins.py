@@ -374,3 +374,32 @@ def test_spectral_radius_closed_forms():
         P[i, i + 1] = P[i + 1, i] = 1
     assert oracle.spectral_radius(P) == pytest.approx(2.0 * np.cos(np.pi / (n + 1)), abs=1e-12)
     assert oracle.spectral_radius(P, 0.3) == pytest.approx(0.6 * np.cos(np.pi / (n + 1)), abs=1e-12)
+
+
+def test_weighted_equals_subdivided_unweighted_graph(oracle_lib):
+    """Sec. 3.2 for integer weights: Y_ij = sum_d N_ij^(d) gamma^d, N^(d) the number of walks of
+    total weight d.  Replacing every edge of weight k by a chain of k unit edges through k - 1 new
+    nodes (in- and out-degree one) maps those walks one to one onto the unit-step walks between
+    the original nodes, so the weighted Y and D equal the unweighted ones of the subdivided graph
+    on the original nodes -- a check of X = gamma^W that does not use that formula."""
+    rng = np.random.default_rng(21)
+    for n in (5, 8):
+        A = graphs.er(n, 0.5, 700 + n)
+        W = np.where(A != 0, rng.integers(1, 4, size=(n, n)), 0).astype(np.float32)
+        rows = [(i, j, int(W[i, j])) for i, j in zip(*np.nonzero(A))]  # edge j -> i, weight k
+        m = n + sum(k - 1 for _, _, k in rows)
+        S = np.zeros((m, m), np.uint8)
+        nxt = n
+        for i, j, k in rows:
+            prev = j
+            for _ in range(k - 1):
+                S[nxt, prev] = 1
+                prev = nxt
+                nxt += 1
+            S[i, prev] = 1
+        g = 1.0 / (graphs.max_out_degree(S) + 2)
+        Dw, Yw = oracle.rdistance(A, g, W=W, want_y=True)
+        Ds, Ys = oracle.rdistance(S, g, want_y=True)
+        assert rel_err(Yw[Yw != 0], Ys[:n, :n][Yw != 0]) < 1e-12
+        assert np.array_equal(Yw == 0, Ys[:n, :n] == 0)
+        assert np.array_equal(Dw, Ds[:n, :n])
