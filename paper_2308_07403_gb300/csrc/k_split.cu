@@ -1221,7 +1221,6 @@ void rd_split_release(rd_ctx* h) {
 // LU and both triangular inverses are produced together by the recursion.
 cudaError_t rd_lu_split(rd_ctx* h, cudaStream_t s) { return factor(h, 0, h->N, s); }
 
-cudaError_t rd_trtri_split(rd_ctx*, cudaStream_t) { return cudaSuccess; }
 
 cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s) {
   const int N = h->N;

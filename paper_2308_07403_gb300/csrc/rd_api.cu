@@ -277,8 +277,8 @@ rd_status escalate(rd_ctx* h, double worst) {
   return RD_OK;
 }
 
-// Range screen of the split path, run once per graph when the caller leaves the digit count open.  The digits of a KAPPA-wide chunk of an operand row are scaled to the
-// chunk's largest entry, and the entries of Y fall by log2(1/gamma) bits per hop (Y_ij ~ gamma^d
+// Range screen of the split path, run once per graph when the caller leaves the digit count
+// open.  The digits of a KAPPA-wide chunk of an operand row are scaled to the chunk's largest entry, and the entries of Y fall by log2(1/gamma) bits per hop (Y_ij ~ gamma^d
 // for distance d), so a chunk whose nodes lie S hops apart as seen from one node costs about
 // S log2(1/gamma) of the 7 s bits the digits carry.  The largest S over the chunks, seen from 8
 // sampled sources, sets the digit count: the fewest (at least RD_SPLIT_MIN) whose 7 s bits cover

@@ -216,7 +216,6 @@ cudaError_t rd_greedy(rd_ctx* h, const int32_t* dgoals, int k, const double* yro
 rd_status rd_split_prepare(rd_ctx* h, int slices);
 void rd_split_release(rd_ctx* h);
 cudaError_t rd_lu_split(rd_ctx* h, cudaStream_t s);
-cudaError_t rd_trtri_split(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s);
 cudaError_t rd_goal_split(rd_ctx* h, const int32_t* dgoals, int k, double* out, cudaStream_t s);
 cudaError_t rd_split_row_check(rd_ctx* h, double* worst, cudaStream_t s);
