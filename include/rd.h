@@ -149,7 +149,9 @@ rd_status rd_set_stream(rd_handle h, void* stream);
  * order's limit.  Drops cached factors when the mode changes. */
 rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices);
 
-/* Change the decode snap tau (>= 0, < 0.5). */
+/* Change the decode snap tau (>= 0, < 0.5).  The split path's self-check limit follows tau at
+ * the time of the factorisation; factors made under a larger tau are not re-checked (a change
+ * of precision mode, or rd_load, refactors). */
 rd_status rd_set_tau(rd_handle h, double tau);
 
 /* All-pairs R-distance: D (n*n int32, row-major, D[i*n+j] = distance j -> i).  If Y is not
