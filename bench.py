@@ -459,6 +459,30 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def serve_cpu_baseline(pool, plan, budget_s=10.0):
+    """The oracle serving the stream's first requests on one core (graphs of at most 1024 nodes,
+    in stream order, until about budget_s seconds of work): requests per second."""
+    import oracle
+
+    oracle.build()
+    done, t0 = 0, time.perf_counter()
+    for _, gid, goals in plan:
+        A, g = pool[gid][0], pool[gid][1]
+        if A.shape[0] > 1024:
+            continue
+        if goals is None:
+            oracle.rdistance(A, g)
+        else:
+            oracle.goal_rows(A, g, goals)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    return {"value": done / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"the stream's first {done} requests on graphs of at most 1024 nodes, in order, one core "
+                      "(the larger graphs of the pool are left out: the oracle is O(n^3) per request)"}
+
+
 def serve_metric(rate):
     return f"serving: Poisson {rate:g} req/s over 128 graphs n log-uniform [64,4096], solves/s (p50/p99 latency)"
 
@@ -547,6 +571,12 @@ def run_serving(args):
         "max_inflight": s1["max_inflight"], "evictions": s1["evictions"] - s0["evictions"],
         "resident_graphs": s1["resident_graphs"], "clocks": clk,
         "e2e": {"value": n_req / wall, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+        "gpu_launches": s1["launches"] - s0["launches"],
+        "roofline": {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                     "note": "requests are small (n log-uniform in [64, 4096]; 75 % are 1..64 goal rows on resident "
+                             "factors) and their latency is host synchronisation and launch bound; the kernels' "
+                             "rooflines are those of the single-graph and batched lines"},
+        "cpu_baseline": serve_cpu_baseline(pool, plan),
     }
     print(json.dumps(line), flush=True)
 
@@ -557,7 +587,7 @@ WEIGHTED_METRIC = ("weighted local navigation, n=32768 king-move grid W~U[1,4]: 
 
 def run_weighted(args):
     """Weighted local navigation: factor M = I - gamma^W of a king-move grid in split precision
-    (the screen counts a hop as the largest weight and takes the locality order), 1024 goal rows in
+    (the range screen measures weighted spreads and picks the node order and the digits), 1024 goal rows in
     16 batches of 64, the greedy next hop toward each goal; on the host, Dijkstra on the reversed
     graph (scipy) scores every greedy move: correct when it lies on a shortest path."""
     import scipy.sparse as sp
@@ -628,6 +658,26 @@ def run_weighted(args):
         ok += int(good.sum())
         checked += int(i.size)
     underflow = int(((Yh == 0) & np.isfinite(dist)).sum())
+    # end to end through the C ABI: the graph from pinned host memory (rd_create_weighted copies A
+    # and W in and builds M), goal rows and next hops back to pinned host memory, wall time
+    A_pin = torch.from_numpy(A).pin_memory()
+    W_pin = torch.from_numpy(W).pin_memory()
+    rows_h = torch.empty((G, n), dtype=torch.float64).pin_memory()
+    nxt_h = torch.empty((G, n), dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2 = rd.rd_create_weighted(A_pin.numpy(), W_pin.numpy(), n, g)
+    rd.rd_set_stream(h2, stream.cuda_stream)
+    rd.rd_set_precision(h2, rd.RD_PREC_SPLIT_BF16, 0)
+    rh, nh = rows_h.numpy(), nxt_h.numpy()
+    for b in range(G // 64):
+        gb = np.ascontiguousarray(goals[b * 64:(b + 1) * 64])
+        rd.rd_goal_solve(h2, gb, 64, rh[b * 64:(b + 1) * 64])
+        rd.rd_greedy_next(h2, gb, 64, rh[b * 64:(b + 1) * 64], nh[b * 64:(b + 1) * 64])
+    t_e2e = time.perf_counter() - t0
+    rd.rd_destroy(h2)
+    e2e_same = bool(np.array_equal(nh, nx))
+    del A_pin, W_pin
     # roofline of the dense contraction that carried the factorisation
     if st["precision_used"]:
         pk, pk_kind = peaks()
@@ -670,6 +720,11 @@ def run_weighted(args):
         "greedy_on_shortest_path_fraction": ok / max(1, checked), "greedy_moves_checked": checked,
         "goal_row_entries_underflowed": underflow, "dijkstra_cpu_s": t_dij,
         "clocks": clk, "gpu_launches": st["launches"], "roofline": roof,
+        "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(A.nbytes + W.nbytes + goals.nbytes + rows_h.numel() * 8),
+                "d2h_bytes_per_step": int(rows_h.numel() * 8 + nxt_h.numel() * 4),
+                "note": "rd_create_weighted from pinned host A and W, 16 x (goal rows to host, greedy next hops "
+                        "from host rows to host), wall time; next hops identical to the device run: "
+                        + str(e2e_same)},
         "cpu_baseline": {"value": tcpu, "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"CPU oracle (1 thread, FP64, full R-distance) on the 24 x 32 king grid of the "
                                    f"same recipe, scaled to n={n} by n^3"},
@@ -842,6 +897,8 @@ def run_product(args):
     torch.cuda.synchronize()
     rd.rd_set_profiling(h, True)
     st0 = rd.rd_get_stats(h)
+    clocks = ClockSampler(local)
+    clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     torch.cuda.nvtx.range_push("inverse_product")
     ev[0].record(stream)
@@ -850,8 +907,17 @@ def run_product(args):
     ev[1].record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
+    clk = clocks.stop()
     st = rd.rd_get_stats(h)
     rd.rd_destroy(h)
+    import oracle
+
+    oracle.build()
+    m = 1024
+    As = A[:m, :m]
+    t0 = time.perf_counter()
+    oracle.rdistance(As, graphs.gamma_frac(As, 0.5))
+    tcpu = time.perf_counter() - t0
     ms = ev[0].elapsed_time(ev[1]) / args.steps
     kms = (st["prof_split_ms"] - st0["prof_split_ms"]) / args.steps
     fl = (st["prof_split_flops"] - st0["prof_split_flops"]) / args.steps
@@ -866,6 +932,12 @@ def run_product(args):
                    "n": n, "digits": st["slices"], "locality_order": ["none", "landmark", "scored"][st["split_order"]],
                    "l2": "no flush: the digit planes of both operands exceed the 129 MB L2"},
         "kernel_ms": kms, "effective_tflops_2n3_over_3": (2.0 * n ** 3 / 3.0) / (ms * 1e-3) / 1e12,
+        "clocks": clk, "gpu_launches": (st["launches"] - st0["launches"]) // max(1, args.steps),
+        "e2e": {"value": None, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "kernel diagnostic on resident factors; the end-to-end figure is the single-graph line's"},
+        "cpu_baseline": {"value": (2.0 * m ** 3 / 3.0) / tcpu / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"the oracle's whole R-distance of the leading {m} x {m} principal submatrix, "
+                                   "rated at the product's 2 m^3 / 3 (the oracle has no separate product step)"},
         "roofline": {"kernel": "split_gemm_kernel", "bound": "tensor", "achieved": achieved,
                      "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
                      # DRAM bytes of this launch (read + write) from an ncu capture of this

@@ -308,6 +308,7 @@ typedef struct {
   int64_t bytes_used, evictions, reused;
   double p50_ms, p99_ms;  /* submit-to-completion latency over all completed requests           */
   double seconds;         /* since rd_serve_create                                              */
+  int64_t launches;       /* kernel launches of all requests so far                             */
 } rd_serve_report;
 
 typedef struct rd_server* rd_server_handle;

@@ -76,6 +76,7 @@ struct rd_server {
   bool stop = false;
   int inflight = 0, max_inflight = 0;
   int64_t completed = 0, failed = 0, evictions = 0, reused = 0;
+  int64_t launches = 0;  // kernel launches of the requests' handles (the handles' own counters)
   std::vector<double> lat_ms;
   clock_type::time_point t0;
 };
@@ -140,6 +141,8 @@ void run_job(rd_server* s, Job* j, cudaStream_t st) {
     if (r == RD_OK) r = rd_set_precision(h, j->r.precision, 0);
   }
   if (r == RD_OK) r = rd_set_stream(h, (void*)st);  // this worker's stream, whoever ran it before
+  // the handle is this worker's until the request ends; a handle made for it counts from its creation
+  const int64_t launches0 = (h && !j->fresh) ? h->launches : 0;
   if (r == RD_OK) {
     if (j->r.kind == RD_REQ_APSP)
       r = rd_apsp(h, j->r.D_out, nullptr);
@@ -147,6 +150,7 @@ void run_job(rd_server* s, Job* j, cudaStream_t st) {
       r = rd_goal_solve(h, j->goals.data(), j->r.k, j->r.Y_out);
   }
   std::lock_guard<std::mutex> lk(s->mu);
+  if (h) s->launches += h->launches - launches0;
   j->result = r;
   j->t_done = clock_type::now();
   j->done = true;
@@ -308,6 +312,7 @@ rd_status rd_serve_stats(rd_server_handle s, rd_serve_report* out) {
   out->bytes_used = s->used;
   out->evictions = s->evictions;
   out->reused = s->reused;
+  out->launches = s->launches;
   out->p50_ms = percentile(s->lat_ms, 0.5);
   out->p99_ms = percentile(s->lat_ms, 0.99);
   out->seconds = std::chrono::duration<double>(clock_type::now() - s->t0).count();

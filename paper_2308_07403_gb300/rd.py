@@ -376,7 +376,8 @@ class rd_serve_report(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("resident_graphs", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("bytes_used", ctypes.c_int64), ("evictions", ctypes.c_int64), ("reused", ctypes.c_int64),
-                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
 
 
 class Server:
