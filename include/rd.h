@@ -185,6 +185,14 @@ rd_status rd_goal_solve(rd_handle h, const int32_t* goals, int32_t k, double* Y_
 rd_status rd_greedy_next(rd_handle h, const int32_t* goals, int32_t k, const double* Yrows,
                          int32_t* next);
 
+/* Greedy walks (Sec. 4.2, the local navigation): for c < k, from start[c] follow next (k x n,
+ * the output of rd_greedy_next for the same goals) until a node is its own next hop (the goal), a
+ * node has none, or max_len (0..n) steps.  path (k x (max_len + 1)) receives the nodes visited,
+ * start first, -1 past the end; len[c] the steps to the goal, or -1 if the walk did not reach it.
+ * Buffers on the device or the host (host outputs synchronise). */
+rd_status rd_greedy_walk(rd_handle h, const int32_t* next, int32_t k, const int32_t* start, int32_t max_len,
+                         int32_t* path, int32_t* len);
+
 /* Incremental edge update (the paper's map update when an obstacle appears, Sec. 6): the edge
  * j -> i becomes present (weight w for a weighted handle; ignored otherwise) or absent, and D
  * (n x n) -- and Y when not NULL -- receive the R-distance of the changed graph.  X_ij changes by

@@ -112,6 +112,45 @@ cudaError_t rd_goal_f64(rd_ctx* h, const int32_t* dgoals, int k, double* out, cu
   return rd_copy_rows_out(h, R, N, k, h->n, out, h->n, s);
 }
 
+// The greedy walk of Sec. 4.2 toward goal c from start[c], one thread per goal: follow the next
+// hops (next[c n + x], the output of the greedy step) until a node is its own next hop (the goal),
+// a node has none (-1), or max_len steps.  path[c (max_len + 1) + t] = the node after t steps, -1
+// past the end; len[c] = the steps taken to the goal, or -1 if the walk did not reach it.
+__global__ void walk_kernel(const int32_t* __restrict__ next, int n, int k, const int32_t* __restrict__ start,
+                            int max_len, int32_t* __restrict__ path, int32_t* __restrict__ len) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  int32_t* p = path + (long long)c * (max_len + 1);
+  const int32_t* nx = next + (long long)c * n;
+  int x = start[c];
+  int t = 0, steps = -1;
+  if (x >= 0 && x < n) {
+    p[0] = x;
+    for (; t <= max_len; ++t) {
+      const int y = nx[x];
+      if (y == x) {  // the goal: its own next hop
+        steps = t;
+        break;
+      }
+      if (y < 0 || y >= n || t == max_len) break;  // dead end, or out of steps
+      x = y;
+      p[t + 1] = x;
+    }
+    ++t;  // entries 0..t-1 are set
+  }
+  for (int q = (x >= 0 && x < n) ? t : 0; q <= max_len; ++q) p[q] = -1;
+  len[c] = steps;
+}
+
+cudaError_t rd_walk(rd_ctx* h, const int32_t* dnext, int k, const int32_t* dstart, int max_len, int32_t* dpath,
+                    int32_t* dlen, cudaStream_t s) {
+  cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
+  if (e != cudaSuccess) return e;
+  walk_kernel<<<1, 64, 0, s>>>(dnext, h->n, k, dstart, max_len, dpath, dlen);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
+}
+
 cudaError_t rd_greedy(rd_ctx* h, const int32_t* dgoals, int k, const double* yrows, int32_t* next,
                       cudaStream_t s) {
   const long long total = (long long)k * h->n;

@@ -717,6 +717,42 @@ rd_status rd_goal_solve(rd_handle h, const int32_t* goals, int32_t k, double* Y_
   return RD_OK;
 }
 
+rd_status rd_greedy_walk(rd_handle h, const int32_t* next, int32_t k, const int32_t* start, int32_t max_len,
+                         int32_t* path, int32_t* len) {
+  if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  if (!next || !start || !path || !len) return fail(h, RD_ERR_ARG, "NULL argument");
+  if (k < 1 || k > RD_MAX_GOALS) return fail(h, RD_ERR_ARG, "k must lie in [1, 64]");
+  if (max_len < 0 || max_len > h->n) return fail(h, RD_ERR_ARG, "max_len must lie in [0, n]");
+  RD_CK(h, cudaSetDevice(h->device));
+  const size_t kn = (size_t)k * h->n, kp = (size_t)k * ((size_t)max_len + 1);
+  const bool next_host = !is_device_ptr(next, h->device), start_host = !is_device_ptr(start, h->device);
+  const bool path_host = !is_device_ptr(path, h->device), len_host = !is_device_ptr(len, h->device);
+  if (start_host)
+    for (int c = 0; c < k; ++c)
+      if (start[c] < 0 || start[c] >= h->n) return fail(h, RD_ERR_ARG, "start node out of range");
+  // staging for host buffers: next in dNext, starts and lengths in dR, paths after them in dR
+  // (64 N doubles hold 2 * 64 + 64 (n + 1) ints)
+  if (next_host && !h->dNext) RD_CK(h, dalloc(h, &h->dNext, (size_t)RD_MAX_GOALS * h->n));
+  int32_t* stage = reinterpret_cast<int32_t*>(h->dR);
+  const int32_t* dnext = next;
+  if (next_host) {
+    RD_CK(h, cudaMemcpyAsync(h->dNext, next, kn * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    dnext = h->dNext;
+  }
+  const int32_t* dstart = start;
+  if (start_host) {
+    RD_CK(h, cudaMemcpyAsync(stage, start, k * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    dstart = stage;
+  }
+  int32_t* dlen = len_host ? stage + RD_MAX_GOALS : len;
+  int32_t* dpath = path_host ? stage + 2 * RD_MAX_GOALS : path;
+  RD_CK(h, rd_walk(h, dnext, k, dstart, max_len, dpath, dlen, h->stream));
+  if (path_host) RD_CK(h, cudaMemcpyAsync(path, dpath, kp * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  if (len_host) RD_CK(h, cudaMemcpyAsync(len, dlen, k * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  if (path_host || len_host) RD_CK(h, cudaStreamSynchronize(h->stream));
+  return RD_OK;
+}
+
 rd_status rd_spectral_radius(rd_handle h, int32_t iters, double* lo, double* hi) {
   if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
   if (!lo || !hi) return fail(h, RD_ERR_ARG, "lo and hi must not be NULL");

@@ -211,6 +211,9 @@ cudaError_t rd_rows_from_y(rd_ctx* h, const int32_t* dgoals, int k, double* out,
 cudaError_t rd_goal_f64(rd_ctx* h, const int32_t* dgoals, int k, double* out, cudaStream_t s);
 cudaError_t rd_greedy(rd_ctx* h, const int32_t* dgoals, int k, const double* yrows,
                       int32_t* next, cudaStream_t s);
+// greedy walks of up to max_len steps from start[c] along the next hops of goal c (k <= 64)
+cudaError_t rd_walk(rd_ctx* h, const int32_t* dnext, int k, const int32_t* dstart, int max_len, int32_t* dpath,
+                    int32_t* dlen, cudaStream_t s);
 
 // ---- split path (k_split.cu) -----------------------------------------------------------------
 rd_status rd_split_prepare(rd_ctx* h, int slices);

@@ -46,6 +46,7 @@ _SIGS = {
     "rd_goal_solve": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
     "rd_greedy_next": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
     "rd_spectral_radius": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "rd_greedy_walk": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P]),
     "rd_set_profiling": (ctypes.c_int, [_P, ctypes.c_int32]),
     "rd_sync": (ctypes.c_int, [_P]),
     "rd_get_stats": (ctypes.c_int, [_P, _P]),
@@ -185,6 +186,18 @@ def rd_set_tau(h, tau: float):
     _check(load().rd_set_tau(h, float(tau)), h)
 
 
+def rd_greedy_walk(h, next_hops, start, max_len: int, path, length):
+    """Walks from start[c] along the next hops of goal c (next_hops: k x n), at most max_len steps."""
+    _np_out(path)
+    _np_out(length)
+    k = int(start.shape[0])
+    pn, kn = _ptr(next_hops)
+    ps, ks = _ptr(start)
+    pp, kp = _ptr(path)
+    pl, kl = _ptr(length)
+    _check(load().rd_greedy_walk(h, pn, k, ps, int(max_len), pp, pl), h)
+
+
 def rd_spectral_radius(h, iters: int = 200):
     """(lo, hi): Collatz-Wielandt bracket of the spectral radius of X after `iters` power steps."""
     lo, hi = ctypes.c_double(), ctypes.c_double()
@@ -293,6 +306,10 @@ class Handle:
 
     def spectral_radius(self, iters=200):
         return rd_spectral_radius(self.h, iters)
+
+    def greedy_walk(self, next_hops, start, max_len, path, length):
+        rd_greedy_walk(self.h, next_hops, start, max_len, path, length)
+        return path, length
 
     def stats(self):
         return rd_get_stats(self.h)
