@@ -1014,6 +1014,12 @@ def main():
     per_step, total_ms, st0, st1, clk = time_path(rd, h, step, 0, args.steps, args.warmup, stream, local, world, dist)
     ms_step = total_ms / args.steps
     flop_step = 2.0 * n ** 3
+    # device ms of each graph's steps (step i runs graph i mod 6), median per graph
+    by_graph = {}
+    for i, ms in enumerate(per_step):
+        kind, frac, _, _ = wl[(args.warmup + i) % len(wl)]
+        by_graph.setdefault(f"{kind}_{frac}", []).append(ms)
+    ms_per_graph = {k: round(pct(v, 0.5), 3) for k, v in by_graph.items()}
     value = replica_throughput(world, flop_step, args.steps, total_ms)
     launches = st1["launches"] - st0["launches"]
     pk, pk_kind = peaks()
@@ -1110,7 +1116,7 @@ def main():
                    "slices_last_graph": slices_used, "goals": args.goals,
                    "l2": "no flush: working set (M, LU, inverses) 1.3 GB > 129 MB L2",
                    "parallelism": f"replicas x{world}"},
-        "p50_ms": pct(per_step, 0.5), "p99_ms": pct(per_step, 0.99),
+        "p50_ms": pct(per_step, 0.5), "p99_ms": pct(per_step, 0.99), "ms_per_graph": ms_per_graph,
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
         "cpu_baseline": cpu, "compare": compare, "verify": verify,
     }

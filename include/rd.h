@@ -174,14 +174,18 @@ rd_status rd_spectral_radius(rd_handle h, int32_t iters, double* lo, double* hi)
 
 /* Goal rows (the local mode of Sec. 4.2): for each goal g = goals[c], 0 <= c < k, writes row
  * g of Y, Y_out[c*n + j] = Y_{g j} (the signal from j at the goal), by solving M^T y = e_g on
- * the resident LU factors (factoring first if needed).  1 <= k <= 64; goals in [0, n). */
+ * the resident LU factors (factoring first if needed).  1 <= k <= 64; goals in [0, n).  Host goals
+ * outside [0, n) return RD_ERR_ARG at once; device goals are checked by the kernels that read them:
+ * a goal outside [0, n) is never used as an index (its row of Y_out is left zero) and the next
+ * synchronising call (rd_sync, or any call with a host output) returns RD_ERR_ARG. */
 rd_status rd_goal_solve(rd_handle h, const int32_t* goals, int32_t k, double* Y_out);
 
 /* Greedy next hop (Sec. 4.2, eq. descent, as ascent on Y per Theorem 4's proof): for goal
  * g = goals[c] and node i, next[c*n + i] = g if i == g or g is a successor of i; otherwise
  * the successor j of i (edge i -> j) with the largest Yrows[c*n + j], smallest j among equal
  * values; -1 if i has no successor.  Yrows is the output of rd_goal_solve for the same goals
- * (k x n). */
+ * (k x n).  Goals are checked as in rd_goal_solve (a device goal outside [0, n) gets next hops -1
+ * and RD_ERR_ARG from the next synchronising call). */
 rd_status rd_greedy_next(rd_handle h, const int32_t* goals, int32_t k, const double* Yrows,
                          int32_t* next);
 
@@ -243,10 +247,11 @@ void rd_destroy(rd_handle h);
  * that loads the library holds it until the process exits.  A (n x n bytes) and D (n x n
  * int32) must be device memory of the current device, owned by the caller; the work runs on
  * `stream` (a cudaStream_t, NULL for the default stream) and the call waits for it.
- * n > RD_NOALLOC_MAX_N returns RD_ERR_ARG without touching the GPU.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current, so make that first call before any stream capture.  All calls share the one
- * array: each call resets what must start at zero and overwrites the rest, and calls whose
+ * n > RD_NOALLOC_MAX_N returns RD_ERR_ARG without touching the GPU.  Every call looks up the
+ * array's device address on the current device (cudaGetSymbolAddress, which allocates nothing,
+ * so a context that was reset and made again is followed); the first call on a device also loads
+ * the library's module there, so make that first call before any stream capture.  All calls
+ * share the one array: each call resets what must start at zero and overwrites the rest, and calls whose
  * GPU work overlaps (other threads, other streams) race on it and must be serialised by the
  * caller.  Errors are readable with rd_last_error(NULL). */
 rd_status rd_apsp_noalloc(const uint8_t* A, int32_t n, double gamma, int32_t* D, void* stream);
@@ -321,15 +326,25 @@ typedef struct {
 
 typedef struct rd_server* rd_server_handle;
 
-/* Start a server on the current device with a device-memory budget (bytes) and 1..64 workers. */
+/* Start a server on the current device with a device-memory budget (bytes) and 1..64 workers.
+ * The server's handles allocate from one stream-ordered memory pool of the device (created here,
+ * keeping up to the budget mapped between requests), so admitting a graph or evicting one never
+ * synchronises the device. */
 rd_status rd_serve_create(int64_t hbm_budget_bytes, int32_t workers, rd_server_handle* out);
-/* Queue a request (its inputs are copied); *id identifies it for poll and wait. */
+/* Queue a request (its inputs are copied); *id identifies it for poll and wait.  RD_ERR_OOM when
+ * the request's estimated device footprint (its handle's workspace, the split digit planes in
+ * split precision, and staging for host outputs) exceeds the whole budget: such a request could
+ * never be admitted.  Requests that fit wait for memory while other requests run. */
 rd_status rd_serve_submit(rd_server_handle s, const rd_request* r, int64_t* id);
 /* *done = 1 once the request completed (its outputs are valid). */
 rd_status rd_serve_poll(rd_server_handle s, int64_t id, int32_t* done);
 /* Block until the request completed; its status and latency (ms) are returned and the id is
  * released. */
 rd_status rd_serve_wait(rd_server_handle s, int64_t id, rd_status* result, double* latency_ms);
+/* As rd_serve_wait, but wait at most timeout_ms (host wall clock; < 0: no limit).  Returns
+ * RD_ERR_TIMEOUT, with the request still running and its id still valid, when the time runs out. */
+rd_status rd_serve_wait_for(rd_server_handle s, int64_t id, double timeout_ms, rd_status* result,
+                            double* latency_ms);
 rd_status rd_serve_stats(rd_server_handle s, rd_serve_report* out);
 /* Finish the queued requests, then free every resident graph and the server. */
 void rd_serve_destroy(rd_server_handle s);

@@ -15,22 +15,29 @@ namespace {
 constexpr int B = RD_BF;
 
 __global__ void init_rhs_kernel(double* __restrict__ R, long long N, const int32_t* __restrict__ goals,
-                                int k) {
+                                int k, int n, int* status) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= RD_MAX_GOALS * N) return;
   const int c = (int)(t / N);
   const long long j = t % N;
-  R[t] = (c < k && goals[c] == j) ? 1.0 : 0.0;
+  const int g = c < k ? goals[c] : -1;
+  if (c < k && j == 0) rd_goal_ok(g, n, c, status);  // a goal outside [0, n) leaves its row zero
+  R[t] = (c < k && g == j && j < n) ? 1.0 : 0.0;
 }
 
 // next[c*n + i]: see rd_greedy_next in rd.h.  One thread per (goal, node).
 __global__ void greedy_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ succ, int n,
                               const int32_t* __restrict__ goals, int k, const double* __restrict__ Y,
-                              int32_t* __restrict__ next) {
+                              int32_t* __restrict__ next, int* status) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)k * n) return;
   const int c = (int)(t / n), i = (int)(t % n);
   const int g = goals[c];
+  if (!(g >= 0 && g < n)) {  // a goal outside [0, n): no next hops for it
+    if (i == 0) rd_goal_ok(g, n, c, status);
+    next[t] = -1;
+    return;
+  }
   const double* y = Y + (long long)c * n;
   int best = -1;
   if (i == g) {
@@ -70,7 +77,7 @@ cudaError_t rd_goal_f64(rd_ctx* h, const int32_t* dgoals, int k, double* out, cu
   const long long total = RD_MAX_GOALS * N;
   cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
-  init_rhs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(R, N, dgoals, k);
+  init_rhs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(R, N, dgoals, k, h->n, h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   const double fdiag_u = 2.0 * RD_MAX_GOALS * (B * (B + 1) / 2);
@@ -159,7 +166,7 @@ cudaError_t rd_greedy(rd_ctx* h, const int32_t* dgoals, int k, const double* yro
   cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   greedy_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ptr, h->dSucc, h->n, dgoals, k, yrows,
-                                                                next);
+                                                                next, h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }

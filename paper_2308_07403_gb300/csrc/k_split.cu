@@ -991,13 +991,13 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
     const size_t need = (size_t)ksplit * ma_pad * nb_pad * sizeof(double);
     if (P->part_bytes < need) {
       if (P->part) {
-        cudaFree(P->part);
+        rd_dev_free(h, P->part);
         h->bytes -= (int64_t)P->part_bytes;
         P->bytes -= (int64_t)P->part_bytes;
         P->part = nullptr;
         P->part_bytes = 0;
       }
-      if ((e = cudaMalloc((void**)&P->part, need)) != cudaSuccess) return e;
+      if ((e = rd_dev_alloc(h, (void**)&P->part, need)) != cudaSuccess) return e;
       P->part_bytes = need;
       P->bytes += (int64_t)need;
       h->bytes += (int64_t)need;
@@ -1151,15 +1151,21 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
 // rows goals[c] of U^-1 (upper part of T, zero left of the diagonal) into R (64 x N); with the
 // locality order, goal g sits at position pos[g]
 __global__ void gather_uinv_rows_kernel(const double* __restrict__ T, long long N, const int32_t* __restrict__ goals,
-                                        const int32_t* __restrict__ pos, int k, double* __restrict__ R) {
+                                        const int32_t* __restrict__ pos, int k, int n, int* status,
+                                        double* __restrict__ R) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)RD_MAX_GOALS * N) return;
   const int c = (int)(t / N);
   const long long j = t % N;
   double v = 0.0;
   if (c < k) {
-    const long long g = pos ? pos[goals[c]] : goals[c];
-    if (j >= g) v = T[g * N + j];
+    const int32_t gc = goals[c];
+    if (gc >= 0 && gc < n) {
+      const long long g = pos ? pos[gc] : gc;
+      if (j >= g) v = T[g * N + j];
+    } else if (j == 0) {
+      rd_goal_ok(gc, n, c, status);  // records the bad goal; its row stays zero
+    }
   }
   R[t] = v;
 }
@@ -1188,7 +1194,7 @@ rd_status rd_split_prepare(rd_ctx* h, int s) {
     const size_t ex = (NK / KAPPA_NARROW + 64) * sizeof(int);  // exponents of the narrowest chunks
     cudaError_t e = cudaSuccess;
     auto get = [&](void** ptr, size_t bytes) {
-      if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+      if (e == cudaSuccess) e = rd_dev_alloc(h, ptr, bytes);
       if (e == cudaSuccess) P->bytes += (int64_t)bytes;
     };
     get((void**)&P->digA, dig);
@@ -1212,7 +1218,7 @@ void rd_split_release(rd_ctx* h) {
   if (!P) return;
   void* ptrs[] = {P->digA, P->digB, P->eA, P->eB, P->part};
   for (void* q : ptrs)
-    if (q) cudaFree(q);
+    if (q) rd_dev_free(h, q);
   h->bytes -= (h->bytes >= P->bytes) ? P->bytes : 0;
   delete P;
   h->split = nullptr;
@@ -1271,8 +1277,8 @@ cudaError_t rd_goal_split(rd_ctx* h, const int32_t* dgoals, int k, double* out, 
   cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   const long long total = RD_MAX_GOALS * N;
-  gather_uinv_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->dT, N, dgoals,
-                                                                           h->ordered ? h->dPos : nullptr, k, h->dR);
+  gather_uinv_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+      h->dT, N, dgoals, h->ordered ? h->dPos : nullptr, k, h->n, h->dStatus, h->dR);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   const double Nd = (double)N;

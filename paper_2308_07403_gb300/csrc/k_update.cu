@@ -86,11 +86,17 @@ __global__ void set_edge_kernel(uint8_t* A, float* W, double* colsum, int32_t* d
 
 // Y rows goals[c] into out (k x n)
 __global__ void rows_from_y_kernel(const double* __restrict__ Y, int n, const int32_t* __restrict__ goals, int k,
-                                   double* __restrict__ out) {
+                                   double* __restrict__ out, int* status) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)k * n) return;
   const int c = (int)(t / n), col = (int)(t % n);
-  out[t] = Y[(long long)goals[c] * n + col];
+  const int32_t g = goals[c];
+  if (!(g >= 0 && g < n)) {  // a goal outside [0, n): recorded, its row left zero
+    if (col == 0) rd_goal_ok(g, n, c, status);
+    out[t] = 0.0;
+    return;
+  }
+  out[t] = Y[(long long)g * n + col];
 }
 
 }  // namespace
@@ -127,7 +133,7 @@ cudaError_t rd_rows_from_y(rd_ctx* h, const int32_t* dgoals, int k, double* out,
   const long long total = (long long)k * h->n;
   cudaError_t e = rd_prof_begin(h, s, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
-  rows_from_y_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->dYres, h->n, dgoals, k, out);
+  rows_from_y_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->dYres, h->n, dgoals, k, out, h->dStatus);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }

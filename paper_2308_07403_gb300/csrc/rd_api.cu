@@ -20,6 +20,22 @@ namespace {
 
 thread_local std::string g_create_err;
 
+}  // namespace
+
+cudaError_t rd_dev_alloc(rd_ctx* h, void** p, size_t bytes) {
+  if (h->pool) return cudaMallocFromPoolAsync(p, bytes, h->pool, h->stream);
+  return cudaMalloc(p, bytes);
+}
+
+void rd_dev_free(rd_ctx* h, void* p) {
+  if (h->pool)
+    cudaFreeAsync(p, h->stream);  // after the handle's work enqueued so far
+  else
+    cudaFree(p);
+}
+
+namespace {
+
 rd_status fail(rd_ctx* h, rd_status st, const std::string& msg) {
   if (h)
     h->err = msg;
@@ -64,7 +80,7 @@ template <class T>
 cudaError_t dalloc(rd_ctx* h, T** p, size_t count) {
   size_t bytes = count * sizeof(T);
   if (bytes == 0) bytes = sizeof(T);
-  cudaError_t e = cudaMalloc((void**)p, bytes);
+  cudaError_t e = rd_dev_alloc(h, (void**)p, bytes);
   if (e == cudaSuccess) h->bytes += (int64_t)bytes;
   return e;
 }
@@ -80,7 +96,7 @@ void free_all(rd_ctx* h) {
   void* ptrs[] = {h->dA, h->dW, h->dLU, h->dT, h->dS, h->dR, h->dStatus, h->dRed, h->dDeg, h->dColsum,
                   h->dSucc, h->dGoals, h->dNext, h->dYrows, h->dDout, h->dYout, h->dOrd, h->dPos, h->dCheckGoals, h->dYres, h->dSuccW};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) rd_dev_free(h, p);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
 }
@@ -100,6 +116,12 @@ rd_status check_device_status(rd_ctx* h) {
     return fail(h, RD_ERR_NUMERIC, buf);
   }
   if (st[0] == RD_DEV_TIMEOUT) return fail(h, RD_ERR_TIMEOUT, "a bounded device wait expired");
+  if (st[0] == RD_DEV_BADGOAL) {
+    // reported once: the factors are intact and the handle stays usable
+    snprintf(buf, sizeof buf, "goal index out of range at position %d of the device goal array", st[1]);
+    RD_CK(h, cudaMemsetAsync(h->dStatus, 0, 2 * sizeof(int), h->stream));
+    return fail(h, RD_ERR_ARG, buf);
+  }
   snprintf(buf, sizeof buf, "device status %d (detail %d)", st[0], st[1]);
   return fail(h, RD_ERR_ARG, buf);
 }
@@ -109,8 +131,8 @@ rd_status ensure_succ_capacity(rd_ctx* h, int64_t edges) {
   const bool need_w = h->weighted && !h->dSuccW;
   if (h->dSucc && edges <= h->succ_cap && !need_w) return RD_OK;  // (a graph without edges still gets lists)
   const int64_t cap = edges > h->succ_cap ? edges + edges / 8 + 1024 : h->succ_cap;
-  if (h->dSucc) cudaFree(h->dSucc);
-  if (h->dSuccW) cudaFree(h->dSuccW);
+  if (h->dSucc) rd_dev_free(h, h->dSucc);
+  if (h->dSuccW) rd_dev_free(h, h->dSuccW);
   h->bytes -= h->succ_cap * (int64_t)(sizeof(int32_t) + sizeof(float));
   h->dSucc = nullptr;
   h->dSuccW = nullptr;
@@ -172,7 +194,8 @@ rd_status load_impl(rd_ctx* h, const uint8_t* A, const float* W, double gamma) {
   return RD_OK;
 }
 
-rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma, rd_handle* out) {
+rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma, rd_handle* out,
+                      cudaMemPool_t pool = nullptr, cudaStream_t stream = nullptr) {
   if (!out) return fail(nullptr, RD_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!A) return fail(nullptr, RD_ERR_ARG, "A is NULL");
@@ -188,6 +211,8 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
     return fail_cuda(nullptr, e, "cudaGetDevice");
   }
   h->device = dev;
+  h->pool = pool;
+  h->stream = stream;
   h->n = n;
   h->N = (n + RD_PAD - 1) / RD_PAD * RD_PAD;
   const size_t N = (size_t)h->N;
@@ -421,6 +446,9 @@ rd_status ensure_factored(rd_ctx* h) {
   return RD_OK;
 }
 
+// Host goals are range-checked here; goals in device memory are checked by every kernel that reads
+// them (a goal outside [0, n) leaves its row zero and its next hops -1, and records RD_DEV_BADGOAL,
+// which the next synchronising call returns as RD_ERR_ARG).
 rd_status ensure_goals(rd_ctx* h, const int32_t* goals, int32_t k) {
   if (!goals) return fail(h, RD_ERR_ARG, "goals is NULL");
   if (k < 1 || k > RD_MAX_GOALS) return fail(h, RD_ERR_ARG, "k must lie in [1, 64]");
@@ -517,6 +545,15 @@ rd_status rd_set_profiling(rd_handle h, int32_t on) {
 rd_status rd_create(const uint8_t* A, int32_t n, double gamma, rd_handle* out) {
   return create_impl(A, nullptr, n, gamma, out);
 }
+
+}  // extern "C"
+
+rd_status rd_create_pooled(const uint8_t* A, int32_t n, double gamma, cudaMemPool_t pool, cudaStream_t stream,
+                           rd_handle* out) {
+  return create_impl(A, nullptr, n, gamma, out, pool, stream);
+}
+
+extern "C" {
 
 rd_status rd_create_weighted(const uint8_t* A, const float* W, int32_t n, double gamma, rd_handle* out) {
   if (!W) {
@@ -862,7 +899,9 @@ const char* rd_status_string(rd_status s) {
 void rd_destroy(rd_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
-  cudaStreamSynchronize(h->stream);
+  // a pooled handle's memory returns to its pool in stream order (no wait); otherwise wait for the
+  // handle's work before cudaFree
+  if (!h->pool) cudaStreamSynchronize(h->stream);
   free_all(h);
   delete h;
 }

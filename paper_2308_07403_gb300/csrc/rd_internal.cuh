@@ -27,6 +27,7 @@
 #define RD_DEV_PIVOT 1      // non-positive or non-finite pivot
 #define RD_DEV_NONFINITE 2  // non-finite entry of Y
 #define RD_DEV_TIMEOUT 3    // a bounded wait expired
+#define RD_DEV_BADGOAL 4    // a goal index in device memory outside [0, n) (detail: its position)
 #define RD_SPLIT_START 12   // digit count of an unscreened graph (weighted) when the caller leaves it open
 #define RD_SPLIT_MIN 8      // fewest digits the range screen picks
 #define RD_SPLIT_MAX 15     // largest digit count in the natural order (exact group sums, 256-wide chunks)
@@ -55,6 +56,9 @@ struct rd_split_plan;       // defined by the split path
 
 struct rd_ctx {
   int device = 0;
+  // device memory: cudaMalloc / cudaFree, or, for handles of a server, its stream-ordered pool
+  // (cudaMallocFromPoolAsync / cudaFreeAsync on the handle's stream: no device-wide synchronisation)
+  cudaMemPool_t pool = nullptr;
   int32_t n = 0, N = 0;
   double gamma = 0.0, tau = 1e-9, max_colsum = 0.0;
   int weighted = 0;
@@ -130,6 +134,13 @@ struct rd_ctx {
   int8_t prof_kind[kProfPairs] = {};           // RD_PROF_* of each pending event pair
   double prof_pair_flops[kProfPairs] = {};
 };
+
+// Device memory of a handle (see rd_ctx::pool); frees are stream-ordered for pooled handles.
+cudaError_t rd_dev_alloc(rd_ctx* h, void** p, size_t bytes);
+void rd_dev_free(rd_ctx* h, void* p);
+// rd_create with every allocation of the handle (now and later) from `pool` on `stream`
+rd_status rd_create_pooled(const uint8_t* A, int32_t n, double gamma, cudaMemPool_t pool, cudaStream_t stream,
+                           rd_handle* out);
 
 // Launch accounting around one kernel launch (see rd_ctx).  `kind` marks the dense GEMM kernels
 // whose time and algorithmic flops are profiled (RD_PROF_NONE for every other kernel).
@@ -261,4 +272,12 @@ __device__ __forceinline__ int32_t rd_decode_entry_fast(double y, float inv_log2
 
 __device__ __forceinline__ void rd_set_status(int* status, int code, int detail) {
   if (status && atomicCAS(status, 0, code) == 0) status[1] = detail;
+}
+
+// A goal read from the caller's device memory: valid when in [0, n); otherwise the status word
+// records RD_DEV_BADGOAL with its position c, and the caller's kernel must not index with it.
+__device__ __forceinline__ bool rd_goal_ok(int32_t g, int n, int c, int* status) {
+  if (g >= 0 && g < n) return true;
+  rd_set_status(status, RD_DEV_BADGOAL, c);
+  return false;
 }

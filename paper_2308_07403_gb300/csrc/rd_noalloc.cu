@@ -14,14 +14,15 @@
 // reductions -- 2.5 * 512^2 * 8 bytes + 16 KiB, about 5.3 MB.  Every GPU that loads the
 // library holds this array until the process exits.
 //
-// In host code the array's name is only a host-side stand-in, not a device address, so the
-// first call on each device (with that device current) asks the runtime for the array's
-// device address with cudaGetSymbolAddress and caches it; that first call should therefore
-// come before any stream capture.  Every call shares the one array: each call clears what
-// must start at zero (the status and reduction words) and overwrites everything else before
-// reading it, and two calls whose work overlaps on the GPU race on the array.
-#include <mutex>
-
+// In host code the array's name is only a host-side stand-in, not a device address, so every
+// call asks the runtime for the array's device address on the current device with
+// cudaGetSymbolAddress (it allocates nothing).  Asking on every call, rather than caching the
+// address per device, keeps the address right when the device's context is destroyed and made
+// again (cudaDeviceReset), which loads the module again, possibly at another address.  The first
+// call on a device also loads the library's module there (lazy loading), so make it before any
+// stream capture.  Every call shares the one array: each call clears what must start at zero (the
+// status and reduction words) and overwrites everything else before reading it, and two calls
+// whose work overlaps on the GPU race on the array.
 #include "rd_internal.cuh"
 
 namespace {
@@ -33,21 +34,12 @@ constexpr size_t kScratchDoubles = 2 * kMatDoubles + kMatDoubles / 2 + kIntWords
 
 static __device__ __align__(256) double g_rd_noalloc_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// device address of the scratch array on the current device (looked up once per device)
-cudaError_t scratch_address(int device, double** out) {
-  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_rd_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[device] = p;
-  }
-  *out = static_cast<double*>(g_addr[device]);
+// device address of the scratch array on the current device (asked for on every call)
+cudaError_t scratch_address(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_rd_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -88,7 +80,7 @@ extern "C" rd_status rd_apsp_noalloc(const uint8_t* A, int32_t n, double gamma, 
   if (!on_device(A, dev) || !on_device(D, dev))
     return fail(RD_ERR_ARG, "A and D must be device memory of the current device");
   double* base = nullptr;
-  NA_CK(scratch_address(dev, &base));
+  NA_CK(scratch_address(&base));
 
   rd_ctx h;  // a view of the scratch; owns nothing
   h.device = dev;
@@ -122,7 +114,11 @@ extern "C" rd_status rd_apsp_noalloc(const uint8_t* A, int32_t n, double gamma, 
   int st[2] = {0, 0};
   NA_CK(cudaMemcpyAsync(st, h.dStatus, sizeof(st), cudaMemcpyDeviceToHost, h.stream));
   NA_CK(cudaStreamSynchronize(h.stream));
-  if (st[0] == RD_DEV_PIVOT) return fail(RD_ERR_NUMERIC, "non-positive pivot");
-  if (st[0] != RD_DEV_OK) return fail(RD_ERR_NUMERIC, "non-finite entry of Y");
-  return RD_OK;
+  switch (st[0]) {
+    case RD_DEV_OK: return RD_OK;
+    case RD_DEV_PIVOT: return fail(RD_ERR_NUMERIC, "non-positive pivot at row " + std::to_string(st[1]));
+    case RD_DEV_NONFINITE: return fail(RD_ERR_NUMERIC, "non-finite entry of Y in row " + std::to_string(st[1]));
+    case RD_DEV_TIMEOUT: return fail(RD_ERR_TIMEOUT, "a bounded device wait expired");
+    default: return fail(RD_ERR_CUDA, "unexpected device status " + std::to_string(st[0]));
+  }
 }

@@ -10,6 +10,13 @@
 // the work of several requests overlaps on the device.  Requests for one graph never run at the
 // same time (a handle is not thread-safe); a later request for a busy graph waits while the queue
 // behind it moves on.
+//
+// Device memory: every handle of the server allocates from one stream-ordered memory pool
+// (cudaMallocFromPoolAsync on the worker's stream) and an evicted handle returns its memory with
+// cudaFreeAsync, so admission and eviction never synchronise the device or stall the other
+// workers' streams (cudaMalloc / cudaFree may).  The pool keeps up to the budget mapped for reuse.
+// A request whose estimated footprint exceeds the whole budget is refused at submit (RD_ERR_OOM):
+// every admitted request fits once the idle graphs are evicted.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -62,6 +69,7 @@ int64_t estimate_bytes(int32_t n, int32_t precision) {
 
 struct rd_server {
   int device = 0;
+  cudaMemPool_t pool = nullptr;  // the handles' device memory (see the file comment)
   int64_t budget = 0;
   int64_t used = 0;
   std::mutex mu;
@@ -83,6 +91,13 @@ struct rd_server {
 
 namespace {
 
+// drop an idle resident graph (caller holds the lock)
+void release(rd_server* s, std::unordered_map<int32_t, Resident>::iterator e) {
+  rd_destroy(e->second.h);
+  s->used -= e->second.bytes;
+  s->cache.erase(e);
+}
+
 // pick a runnable job (caller holds the lock); reserves memory / marks the graph busy
 Job* take_runnable(rd_server* s) {
   for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
@@ -95,26 +110,24 @@ Job* take_runnable(rd_server* s) {
       s->queue.erase(it);
       return j;
     }
+    if (c != s->cache.end()) {  // same id but another size or precision: replace it
+      if (c->second.busy) continue;  // (its running request keeps the handle until it ends)
+      release(s, c);
+      c = s->cache.end();
+    }
     const int64_t need = estimate_bytes(j->r.n, j->r.precision);
-    // evict least-recently-used idle handles until the job fits (other graphs only)
+    // evict least-recently-used idle handles until the job fits; a request never needs more than
+    // the budget (refused at submit), so an idle server always makes room
     while (s->used + need > s->budget) {
       auto victim = s->cache.end();
       for (auto e = s->cache.begin(); e != s->cache.end(); ++e)
         if (!e->second.busy && e->second.ready && (victim == s->cache.end() || e->second.last_use < victim->second.last_use))
           victim = e;
       if (victim == s->cache.end()) break;
-      rd_destroy(victim->second.h);
-      s->used -= victim->second.bytes;
-      s->cache.erase(victim);
+      release(s, victim);
       s->evictions++;
     }
-    if (s->used + need > s->budget && s->inflight > 0) continue;  // wait for memory (unless idle)
-    if (c != s->cache.end()) {  // same id but another size or precision: replace it
-      if (c->second.busy) continue;
-      rd_destroy(c->second.h);
-      s->used -= c->second.bytes;
-      s->cache.erase(c);
-    }
+    if (s->used + need > s->budget) continue;  // wait for running requests to free memory
     s->used += need;
     j->fresh = true;
     Resident rsd;
@@ -137,7 +150,7 @@ void run_job(rd_server* s, Job* j, cudaStream_t st) {
   }
   rd_status r = RD_OK;
   if (!h) {
-    r = rd_create(j->A.data(), j->r.n, j->r.gamma, &h);
+    r = rd_create_pooled(j->A.data(), j->r.n, j->r.gamma, s->pool, st, &h);
     if (r == RD_OK) r = rd_set_precision(h, j->r.precision, 0);
   }
   if (r == RD_OK) r = rd_set_stream(h, (void*)st);  // this worker's stream, whoever ran it before
@@ -236,10 +249,24 @@ rd_status rd_serve_create(int64_t hbm_budget_bytes, int32_t workers, rd_server_h
   }
   s->budget = hbm_budget_bytes;
   s->t0 = clock_type::now();
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = s->device;
+  if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    rd_record_error("rd_serve_create: cudaMemPoolCreate failed");
+    return RD_ERR_CUDA;
+  }
+  uint64_t keep = (uint64_t)hbm_budget_bytes;  // memory kept mapped in the pool between requests
+  cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   for (int w = 0; w < workers; ++w) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       for (cudaStream_t q : s->streams) cudaStreamDestroy(q);
+      cudaMemPoolDestroy(s->pool);
       delete s;
       rd_record_error("rd_serve_create: cudaStreamCreate failed");
       return RD_ERR_CUDA;
@@ -257,6 +284,11 @@ rd_status rd_serve_submit(rd_server_handle s, const rd_request* r, int64_t* id) 
   if (r->kind == RD_REQ_APSP && !r->D_out) return RD_ERR_ARG;
   if (r->kind == RD_REQ_GOALS && (!r->goals || !r->Y_out || r->k < 1 || r->k > RD_MAX_GOALS)) return RD_ERR_ARG;
   if (r->precision != RD_PREC_FP64 && r->precision != RD_PREC_SPLIT_BF16) return RD_ERR_ARG;
+  if (r->n > 65536) return RD_ERR_ARG;
+  if (estimate_bytes(r->n, r->precision) > s->budget) {
+    rd_record_error("rd_serve_submit: the request's device footprint exceeds the server's budget");
+    return RD_ERR_OOM;
+  }
   Job* j = new Job();
   j->r = *r;
   j->A.assign(r->A, r->A + (size_t)r->n * r->n);
@@ -287,12 +319,22 @@ rd_status rd_serve_poll(rd_server_handle s, int64_t id, int32_t* done) {
 }
 
 rd_status rd_serve_wait(rd_server_handle s, int64_t id, rd_status* result, double* latency_ms) {
+  return rd_serve_wait_for(s, id, -1.0, result, latency_ms);
+}
+
+rd_status rd_serve_wait_for(rd_server_handle s, int64_t id, double timeout_ms, rd_status* result,
+                            double* latency_ms) {
   if (!s) return RD_ERR_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->jobs.find(id);
   if (it == s->jobs.end()) return RD_ERR_ARG;
   Job* j = it->second;
-  s->cv_done.wait(lk, [&] { return j->done; });
+  if (timeout_ms < 0.0) {
+    s->cv_done.wait(lk, [&] { return j->done; });
+  } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms),
+                                  [&] { return j->done; })) {
+    return RD_ERR_TIMEOUT;  // still running: the id stays valid
+  }
   if (result) *result = j->result;
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
   s->jobs.erase(it);
@@ -330,7 +372,11 @@ void rd_serve_destroy(rd_server_handle s) {
   for (auto& e : s->cache)
     if (e.second.h) rd_destroy(e.second.h);
   for (auto& e : s->jobs) delete e.second;
-  for (cudaStream_t q : s->streams) cudaStreamDestroy(q);
+  for (cudaStream_t q : s->streams) {
+    cudaStreamSynchronize(q);  // the handles' stream-ordered frees
+    cudaStreamDestroy(q);
+  }
+  cudaMemPoolDestroy(s->pool);
   delete s;
 }
 

@@ -65,6 +65,8 @@ _SIGS = {
     "rd_serve_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
     "rd_serve_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double)]),
+    "rd_serve_wait_for": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double)]),
     "rd_serve_stats": (ctypes.c_int, [_P, _P]),
     "rd_serve_destroy": (None, [_P]),
 }
@@ -186,11 +188,27 @@ def rd_set_tau(h, tau: float):
     _check(load().rd_set_tau(h, float(tau)), h)
 
 
-def rd_greedy_walk(h, next_hops, start, max_len: int, path, length):
-    """Walks from start[c] along the next hops of goal c (next_hops: k x n), at most max_len steps."""
+def _shape_dtype(x):
+    return tuple(int(d) for d in x.shape), str(x.dtype).replace("torch.", "")
+
+
+def rd_greedy_walk(h, next_hops, start, max_len: int, path, length, n: int | None = None):
+    """Walks from start[c] along the next hops of goal c (next_hops: k x n), at most max_len steps.
+
+    Shapes and dtypes are checked before the call (the library copies k n next hops in and
+    k (max_len + 1) path entries out): next_hops int32 (k, n), start int32 (k,), path int32
+    (k, max_len + 1), length int32 (k,).  n defaults to the handle's graph size."""
     _np_out(path)
     _np_out(length)
-    k = int(start.shape[0])
+    if n is None:
+        n = rd_get_stats(h)["n"]
+    k = int(start.shape[0]) if len(start.shape) == 1 else -1
+    want = {"next_hops": (next_hops, (k, int(n))), "start": (start, (k,)),
+            "path": (path, (k, int(max_len) + 1)), "length": (length, (k,))}
+    for name, (x, shape) in want.items():
+        got, dt = _shape_dtype(x)
+        if k < 1 or got != shape or dt != "int32":
+            raise ValueError(f"{name} must be int32 of shape {shape}, got {dt} {got}")
     pn, kn = _ptr(next_hops)
     ps, ks = _ptr(start)
     pp, kp = _ptr(path)
@@ -308,7 +326,7 @@ class Handle:
         return rd_spectral_radius(self.h, iters)
 
     def greedy_walk(self, next_hops, start, max_len, path, length):
-        rd_greedy_walk(self.h, next_hops, start, max_len, path, length)
+        rd_greedy_walk(self.h, next_hops, start, max_len, path, length, n=self.n)
         return path, length
 
     def stats(self):
@@ -449,11 +467,16 @@ class Server:
         _check(load().rd_serve_poll(self.h, int(rid), ctypes.byref(d)))
         return bool(d.value)
 
-    def wait(self, rid):
-        """Returns (status, latency_ms)."""
+    def wait(self, rid, timeout_ms=None):
+        """Returns (status, latency_ms); with timeout_ms, raises RDError(RD_ERR_TIMEOUT) when the
+        request has not completed in time (it keeps running and can be waited for again)."""
         st = ctypes.c_int()
         lat = ctypes.c_double()
-        _check(load().rd_serve_wait(self.h, int(rid), ctypes.byref(st), ctypes.byref(lat)))
+        if timeout_ms is None:
+            _check(load().rd_serve_wait(self.h, int(rid), ctypes.byref(st), ctypes.byref(lat)))
+        else:
+            _check(load().rd_serve_wait_for(self.h, int(rid), float(timeout_ms), ctypes.byref(st),
+                                            ctypes.byref(lat)))
         self._live.pop(int(rid), None)
         return st.value, lat.value
 

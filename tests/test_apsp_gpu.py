@@ -200,6 +200,56 @@ def test_errors(rd):
         assert np.array_equal(D, oracle.rdistance(A, 0.5 / delta))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "split", "updated"])
+def test_device_goal_out_of_range(rd, precision):
+    """Goals in device memory are checked by the kernels that read them: a goal outside [0, n) is
+    never used as an index, its row of Y stays zero and its next hops -1, the other goals' rows
+    are the oracle's, and the next synchronising call returns RD_ERR_ARG naming the position.
+    The handle stays usable afterwards.  ("updated": goal rows read from the resident Y that
+    edge updates keep current.)"""
+    A = graphs.er(200, 0.05, 4)
+    n = A.shape[0]
+    g = graphs.gamma_frac(A, 0.5)
+    stream = torch.cuda.current_stream().cuda_stream
+    bad = torch.tensor([5, n, 199, -3], dtype=torch.int32, device="cuda")
+    ok_goals = np.array([5, 0, 199, 0], np.int32)
+    rows = torch.full((4, n), -1.0, dtype=torch.float64, device="cuda")
+    nxt = torch.full((4, n), -7, dtype=torch.int32, device="cuda")
+    with rd.Handle(torch.from_numpy(A).cuda(), g, stream=stream) as h:
+        if precision == "split":
+            h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
+        if precision == "updated":
+            Dd = torch.empty((n, n), dtype=torch.int32, device="cuda")
+            i, j = next((i, j) for i in range(3, n) for j in range(4, n) if i != j and A[i, j] == 0)
+            h.update_edge(i, j, True, Dd)   # a new edge j -> i
+            A = A.copy()
+            A[i, j] = 1
+        h.goal_solve(bad, rows)
+        with pytest.raises(rd.RDError) as ei:
+            h.sync()
+        assert ei.value.status == rd.RD_ERR_ARG
+        assert "position 1" in rd.rd_last_error(h.h)
+        h.greedy_next(bad, rows, nxt)
+        with pytest.raises(rd.RDError) as ei:
+            h.sync()
+        assert ei.value.status == rd.RD_ERR_ARG
+        h.sync()  # reported once: the handle is usable again
+        got, hops = rows.cpu().numpy(), nxt.cpu().numpy()
+        ref = oracle.goal_rows(A, g, ok_goals)
+        tol = YTOL if precision != "split" else 1e-10
+        for c in (0, 2):
+            nz = ref[c] != 0
+            assert np.array_equal(got[c] == 0, ~nz)
+            assert np.max(np.abs(got[c][nz] - ref[c][nz]) / ref[c][nz]) < tol
+        assert np.all(got[1] == 0) and np.all(got[3] == 0)
+        assert np.all(hops[1] == -1) and np.all(hops[3] == -1)
+        ref_next = oracle.greedy_next(A, ok_goals[[0, 2]], got[[0, 2]])
+        assert np.array_equal(hops[[0, 2]], ref_next)
+        good = np.empty((2, n))
+        h.goal_solve(np.array([5, 199], np.int32), good)
+        assert np.array_equal(good, got[[0, 2]])
+
+
 @pytest.mark.parametrize("precision", ["fp64", "split"])
 @pytest.mark.parametrize("n", [1, 2, 65, 300])
 def test_degenerate_graphs(rd, n, precision):

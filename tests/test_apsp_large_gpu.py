@@ -82,7 +82,8 @@ def test_full_size_fp64(rd, bufs, kind, frac):
     Dh = D.cpu().numpy()
     bad = check_against_golden(Dh, rec)
     assert bad == 0, f"{len(bad)} row blocks of D differ from the oracle's: {bad[:10]}"
-    rng = np.random.default_rng(hash((kind, frac)) % 2**32)
+    # a fixed seed per case (Python's str hash is salted per process): the same rows every run
+    rng = np.random.default_rng(2308_07403 + 10 * CASES.index((kind, frac)))
     for idx in rng.choice(n, size=3, replace=False):
         row, _ = oracle.series_vector(A, g, int(idx), transpose=True)
         col, _ = oracle.series_vector(A, g, int(idx), transpose=False)

@@ -403,3 +403,57 @@ def test_weighted_equals_subdivided_unweighted_graph(oracle_lib):
         assert rel_err(Yw[Yw != 0], Ys[:n, :n][Yw != 0]) < 1e-12
         assert np.array_equal(Yw == 0, Ys[:n, :n] == 0)
         assert np.array_equal(Dw, Ds[:n, :n])
+
+
+# ---- the gain check's quantity: the largest column sum of X ----------------------------------
+
+def _out_star(n):
+    """Node 0 -> every other node: out-degree n - 1 at node 0, in-degree at most 1."""
+    A = np.zeros((n, n), dtype=np.uint8)
+    A[1:, 0] = 1  # A[i, 0] = 1: the edge 0 -> i (Sec. 2's orientation)
+    return A
+
+
+@pytest.mark.parametrize("n,g", [(9, 0.1), (40, 0.02)])
+def test_max_column_sum_is_gamma_times_out_degree(oracle_lib, n, g):
+    """The gain check of Theorem 4 reads the largest column sum of X = gamma A, gamma times the
+    largest OUT-degree Delta (column j of A lists the successors of j, Sec. 2).  Closed forms:
+    the out-star (gamma (n - 1), against gamma for its transpose, the in-star, which a row sum
+    would swap), the directed path (gamma), K_n (gamma (n - 1)), the directed cycle (gamma)."""
+    star = _out_star(n)
+    assert oracle.max_column_sum(oracle.build_m(star, g)) == pytest.approx(g * (n - 1), rel=1e-15)
+    assert oracle.max_column_sum(oracle.build_m(np.ascontiguousarray(star.T), g)) == pytest.approx(g, rel=1e-15)
+    assert oracle.max_column_sum(oracle.build_m(graphs.directed_path(n), g)) == pytest.approx(g, rel=1e-15)
+    assert oracle.max_column_sum(oracle.build_m(graphs.directed_cycle(n), g)) == pytest.approx(g, rel=1e-15)
+    gk = 0.9 / (n - 1)
+    assert oracle.max_column_sum(oracle.build_m(graphs.complete(n), gk)) == pytest.approx(0.9, rel=1e-14)
+
+
+def test_max_column_sum_weighted_geometric(oracle_lib):
+    """Weighted (Sec. 3.2, X_ij = gamma^W_ij): node 0 -> node i with weight i (i = 1..m) gives a
+    column sum of gamma + gamma^2 + ... + gamma^m = gamma (1 - gamma^m) / (1 - gamma); the other
+    columns hold one edge i -> 0 of weight 7 (gamma^7)."""
+    m, g = 12, 0.4
+    n = m + 1
+    A = _out_star(n)
+    A[0, 1:] = 1
+    W = np.zeros((n, n), dtype=np.float32)
+    W[1:, 0] = np.arange(1, n, dtype=np.float32)
+    W[0, 1:] = 7.0
+    ref = g * (1 - g ** m) / (1 - g)
+    assert oracle.max_column_sum(oracle.build_m(A, g, W)) == pytest.approx(ref, rel=1e-14)
+
+
+def test_max_column_sum_er_and_the_gain_check(oracle_lib):
+    """On a seeded directed ER graph the largest column sum is gamma Delta with Delta counted by
+    hand from the edge list; at gamma = 1/Delta it reaches 1 (the boundary of Theorem 4's
+    condition) and the no-pivot LU still has positive pivots just below it."""
+    A = graphs.er(300, 0.03, 11)
+    src = np.nonzero(A)[1]  # A[i, j] != 0: edge j -> i, so j is the source
+    delta = int(np.bincount(src, minlength=300).max())
+    ins = int(np.bincount(np.nonzero(A)[0], minlength=300).max())
+    assert delta != ins  # the case separates out-degree from in-degree
+    g = 0.999 / delta
+    assert oracle.max_column_sum(oracle.build_m(A, g)) == pytest.approx(g * delta, rel=1e-14)
+    assert oracle.max_column_sum(oracle.build_m(A, 1.0 / delta)) == pytest.approx(1.0, rel=1e-14)
+    oracle.lu(A, g)  # raises on a non-positive pivot

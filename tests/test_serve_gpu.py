@@ -1,6 +1,8 @@
 """Serving (rd_serve_*): every result is the same alone and in a concurrent mix (bit-exact: the
-kernels are deterministic), eviction under a small memory budget keeps results, goal solves reuse
-resident factors, bad requests are refused on the host."""
+kernels are deterministic) and is the method's (D against the CPU oracle, goal rows against the
+oracle's rows of Y); eviction under a small memory budget keeps results; a graph id resubmitted
+at another size replaces its resident graph; goal solves reuse resident factors; bad and
+oversized requests are refused on the host; a bounded wait runs out with RD_ERR_TIMEOUT."""
 import numpy as np
 import pytest
 
@@ -9,6 +11,8 @@ from paper_2308_07403_gb300 import graphs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+YTOL = {0: 1e-11, 1: 1e-10}  # goal rows: FP64 path, split path (digit count chosen by the library)
 
 
 @pytest.fixture(scope="module")
@@ -24,6 +28,8 @@ def rd():
 
 
 def pool():
+    """Requests over 8 graphs (ER, grid, WS; n from 64 to 1500), half of the graphs in FP64 and
+    half in split precision, each graph with one full APSP and two goal-row requests, shuffled."""
     rng = np.random.default_rng(11)
     out = []
     for i, n in enumerate((64, 100, 200, 300, 513, 700, 1024, 1500)):
@@ -34,28 +40,52 @@ def pool():
             A = graphs.grid4(n, int(np.ceil(np.sqrt(n))))
         else:
             A = graphs.ws(n, 10, 0.1, 100 + i)
-        out.append((i, A, graphs.gamma_small(A)))
+        out.append((i, A, graphs.gamma_small(A), i % 2))   # precision 0 = FP64, 1 = split
     reqs = []
-    for gid, A, g in out:
-        reqs.append(("apsp", gid, A, g, None))
+    for gid, A, g, prec in out:
+        reqs.append(("apsp", gid, A, g, None, prec))
         for _ in range(2):
             k = int(rng.integers(1, 65))
-            reqs.append(("goals", gid, A, g, np.sort(rng.choice(A.shape[0], size=min(k, A.shape[0]), replace=False))))
+            goals = np.sort(rng.choice(A.shape[0], size=min(k, A.shape[0]), replace=False))
+            reqs.append(("goals", gid, A, g, goals, prec))
     order = rng.permutation(len(reqs))
     return [reqs[i] for i in order]
 
 
 def submit(srv, rd, req):
-    kind, gid, A, g, goals = req
+    kind, gid, A, g, goals, prec = req
     n = A.shape[0]
     if kind == "apsp":
         out = np.full((n, n), -7, np.int32)
-        return srv.submit_apsp(gid, A, g, out), out
+        return srv.submit_apsp(gid, A, g, out, precision=prec), out
     out = np.full((goals.size, n), -7.0)
-    return srv.submit_goals(gid, A, g, goals, out), out
+    return srv.submit_goals(gid, A, g, goals, out, precision=prec), out
 
 
-def test_serve_alone_equals_mix(rd):
+@pytest.fixture(scope="module")
+def oracle_results():
+    """Per graph id: the oracle's D and Y (one CPU inverse per graph)."""
+    res = {}
+    for kind, gid, A, g, goals, prec in pool():
+        if gid not in res:
+            res[gid] = oracle.rdistance(A, g, want_y=True)
+    return res
+
+
+def check_against_oracle(req, out, oracle_results):
+    kind, gid, A, g, goals, prec = req
+    D, Y = oracle_results[gid]
+    if kind == "apsp":
+        assert np.array_equal(out, D), (gid, prec)
+        return
+    ref = Y[goals]
+    assert np.array_equal(out == 0, ref == 0)
+    nz = ref != 0
+    err = np.max(np.abs(out[nz] - ref[nz]) / ref[nz])
+    assert err < YTOL[prec], (gid, prec, err)
+
+
+def test_serve_alone_equals_mix_and_the_oracle(rd, oracle_results):
     reqs = pool()
     alone = []
     with rd.Server(64 << 30, workers=1) as srv:
@@ -75,26 +105,62 @@ def test_serve_alone_equals_mix(rd):
     assert s["max_inflight"] > 1          # the work overlapped
     assert s["reused"] >= len(reqs) - 8   # goal solves on resident factors
     for req, out in zip(reqs, alone):     # and the results are the method's
-        kind, gid, A, g, goals = req
-        if kind == "apsp" and A.shape[0] <= 700:
-            assert np.array_equal(out, oracle.rdistance(A, g))
+        check_against_oracle(req, out, oracle_results)
 
 
-def test_serve_small_budget_evicts_and_keeps_results(rd):
+def test_serve_small_budget_evicts_and_keeps_results(rd, oracle_results):
     reqs = pool()
-    with rd.Server(64 << 30, workers=1) as srv:
-        ref = []
-        for req in reqs:
-            rid, out = submit(srv, rd, req)
-            assert srv.wait(rid)[0] == rd.RD_OK
-            ref.append(out)
-    with rd.Server(300 << 20, workers=3) as srv:   # room for about one large handle at a time
+    with rd.Server(300 << 20, workers=3) as srv:   # less than the pool's ~380 MB: graphs are evicted
         live = [submit(srv, rd, req) for req in reqs]
-        for (rid, out), r in zip(live, ref):
+        for (rid, out), req in zip(live, reqs):
             assert srv.wait(rid)[0] == rd.RD_OK
-            assert np.array_equal(out, r)
+            check_against_oracle(req, out, oracle_results)
         s = srv.stats()
     assert s["evictions"] > 0 and s["failed"] == 0
+
+
+def test_serve_graph_id_reused_at_another_size(rd):
+    """One graph id submitted with graphs of two sizes (and both precisions), beside another id's
+    resident graph, under a 200 MB budget: the resident graph of the id is replaced each time
+    (never evicted while in use, never freed twice), the other graph is evicted when room is
+    needed, and every result is the oracle's."""
+    small = graphs.er(300, 0.02, 5)
+    large = graphs.ws(900, 10, 0.1, 6)
+    cases = [(small, 0), (large, 1), (small, 1), (large, 0), (small, 0)]
+    refs = {id(A): oracle.rdistance(A, graphs.gamma_small(A)) for A, _ in cases}
+    other = graphs.grid4(1000, 32)
+    with rd.Server(200 << 20, workers=2) as srv:
+        Do = np.empty((1000, 1000), np.int32)
+        assert srv.wait(srv.submit_apsp(3, other, graphs.gamma_small(other), Do))[0] == rd.RD_OK
+        live = []
+        for A, prec in cases:
+            n = A.shape[0]
+            out = np.full((n, n), -7, np.int32)
+            live.append((srv.submit_apsp(7, A, graphs.gamma_small(A), out, precision=prec), out, A))
+        for rid, out, A in live:
+            assert srv.wait(rid)[0] == rd.RD_OK
+            assert np.array_equal(out, refs[id(A)])
+        s = srv.stats()
+    assert s["failed"] == 0 and s["resident_graphs"] <= 2 and s["evictions"] >= 1
+
+
+def test_serve_bounded_wait_times_out(rd):
+    """rd_serve_wait_for gives up after its limit with RD_ERR_TIMEOUT while the request keeps
+    running; a later wait returns its result.  One worker holds a large FP64 APSP, so a request
+    queued behind it cannot complete within 1 ms."""
+    big = graphs.er(4096, 4.0 / 4096, 9)
+    small = graphs.er(64, 0.05, 10)
+    with rd.Server(8 << 30, workers=1) as srv:
+        Db = np.empty((4096, 4096), np.int32)
+        Ds = np.empty((64, 64), np.int32)
+        rb = srv.submit_apsp(1, big, graphs.gamma_small(big), Db, precision=rd.RD_PREC_FP64)
+        rs = srv.submit_apsp(2, small, graphs.gamma_small(small), Ds, precision=rd.RD_PREC_FP64)
+        with pytest.raises(rd.RDError) as ei:
+            srv.wait(rs, timeout_ms=1.0)
+        assert ei.value.status == rd.RD_ERR_TIMEOUT
+        assert srv.wait(rb)[0] == rd.RD_OK
+        assert srv.wait(rs, timeout_ms=60_000.0)[0] == rd.RD_OK
+    assert np.array_equal(Ds, oracle.rdistance(small, graphs.gamma_small(small)))
 
 
 def test_serve_rejects_bad_requests(rd):
@@ -107,3 +173,8 @@ def test_serve_rejects_bad_requests(rd):
             assert ei.value.status == rd.RD_ERR_ARG
         with pytest.raises(ValueError):
             srv.submit_apsp(0, A, 0.01, np.empty((64, 64), np.int64))
+    big = graphs.er(2048, 2.0 / 2048, 2)
+    with rd.Server(64 << 20, workers=1) as srv:   # a 2048-node handle needs more than 64 MB
+        with pytest.raises(rd.RDError) as ei:
+            srv.submit_apsp(0, big, graphs.gamma_small(big), np.empty((2048, 2048), np.int32))
+        assert ei.value.status == rd.RD_ERR_OOM

@@ -73,3 +73,50 @@ def test_walks_match_oracle_next_hops(rd, kind, device_io):
     assert length[2] == 0   # started at the goal
     if kind == "dpath":
         assert length[0] == -1   # edges j -> j + 1 lead away from goal 0
+
+
+def _walk(rd, h, nxt, starts, max_len, device_start):
+    k = starts.size
+    path = np.empty((k, max_len + 1), np.int32)
+    length = np.empty(k, np.int32)
+    st = torch.from_numpy(starts).cuda() if device_start else starts
+    h.greedy_walk(torch.from_numpy(nxt).cuda(), st, max_len, path, length)
+    return path, length
+
+
+def test_walk_edge_cases_on_a_directed_path(rd):
+    """Hand-computed walks on the directed path 0 -> 1 -> ... -> 19 toward goal 12: from 3 the walk
+    is 3, 4, ..., 12 (9 steps).  max_len = 0 keeps the start only; a max_len shorter than the way
+    ends the walk with exactly max_len + 1 nodes and length -1; a start at the goal has length 0
+    even with max_len = 0; device starts outside [0, n) give an all -1 path and length -1."""
+    A = graphs.directed_path(20)
+    n, goal = 20, 12
+    goals = np.full(4, goal, np.int32)
+    with rd.Handle(A, 0.3) as h:
+        rows = np.empty((4, n))
+        nxt = np.empty((4, n), np.int32)
+        h.goal_solve(goals, rows)
+        h.greedy_next(goals, rows, nxt)
+        starts = np.array([3, goal, 3, 3], np.int32)
+        path, length = _walk(rd, h, nxt, starts, 0, device_start=False)
+        assert path[:, 0].tolist() == [3, goal, 3, 3] and length.tolist() == [-1, 0, -1, -1]
+        path, length = _walk(rd, h, nxt, starts, 4, device_start=True)
+        assert path[0].tolist() == [3, 4, 5, 6, 7] and length[0] == -1
+        assert path[1].tolist() == [goal, -1, -1, -1, -1] and length[1] == 0
+        path, length = _walk(rd, h, nxt, starts, 9, device_start=False)
+        assert path[0].tolist() == list(range(3, 13)) and length[0] == 9
+        path, length = _walk(rd, h, nxt, starts, n, device_start=False)
+        assert path[0].tolist() == list(range(3, 13)) + [-1] * (n + 1 - 10) and length[0] == 9
+        bad = np.array([-1, n, 3, goal], np.int32)
+        path, length = _walk(rd, h, nxt, bad, 6, device_start=True)
+        assert path[0].tolist() == [-1] * 7 and path[1].tolist() == [-1] * 7
+        assert length[:2].tolist() == [-1, -1] and length[3] == 0
+        assert path[2].tolist() == [3, 4, 5, 6, 7, 8, 9] and length[2] == -1
+        with pytest.raises(rd.RDError):  # host starts are checked on the host
+            _walk(rd, h, nxt, bad, 6, device_start=False)
+        with pytest.raises(ValueError):  # the binding checks shapes and dtypes
+            h.greedy_walk(nxt[:, :10], starts, 4, np.empty((4, 5), np.int32), np.empty(4, np.int32))
+        with pytest.raises(ValueError):
+            h.greedy_walk(nxt, starts.astype(np.int64), 4, np.empty((4, 5), np.int32), np.empty(4, np.int32))
+        with pytest.raises(ValueError):
+            h.greedy_walk(nxt, starts, 4, np.empty((4, 4), np.int32), np.empty(4, np.int32))

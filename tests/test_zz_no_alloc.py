@@ -1,16 +1,18 @@
 """rd_apsp_noalloc: the APSP entry point for callers that must not allocate device memory.
 
-Some callers cannot call cudaMalloc (their device memory is handed out up front by another
-runtime, or they run inside another system's time-critical loop).  rd_apsp_noalloc serves
-them from a fixed device array declared in the library.  This test calls it through the C ABI
-twice in a row on different graphs (so stale contents of the shared array would show) and
-checks each result against the handle-based rd_apsp: D must match exactly, the tolerance the
-other parity tests use for D.  It runs last (file name) and also passes alone in a fresh
-process.
+Some callers cannot call cudaMalloc: their device memory is handed out up front by another
+runtime, or they run inside another system's time-critical loop where the implicit device
+synchronisation of an allocation is not acceptable.  rd_apsp_noalloc serves them from a fixed
+device array declared in the library.  This test calls it through the C ABI twice in a row on
+different graphs (so stale contents of the shared array would show) and checks each D against
+the CPU oracle and against the handle-based rd_apsp: both must match exactly, the tolerance the
+other parity tests use for D (an integer result).  It runs last (file name) and also passes
+alone in a fresh process.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2308_07403_gb300 import graphs
 
 torch = pytest.importorskip("torch")
@@ -29,7 +31,7 @@ def rd():
     return _rd
 
 
-def reference_D(rd, A, g):
+def handle_D(rd, A, g):
     n = A.shape[0]
     D = torch.empty((n, n), dtype=torch.int32, device="cuda")
     with rd.Handle(torch.from_numpy(A).cuda(), g, stream=torch.cuda.current_stream().cuda_stream) as h:
@@ -39,7 +41,7 @@ def reference_D(rd, A, g):
     return D.cpu().numpy()
 
 
-def test_noalloc_matches_rd_apsp_twice(rd):
+def test_noalloc_matches_oracle_and_rd_apsp_twice(rd):
     cases = [graphs.workload_small(), (graphs.grid4(300, 17), None)]
     stream = torch.cuda.current_stream().cuda_stream
     for A, g in cases:
@@ -50,7 +52,9 @@ def test_noalloc_matches_rd_apsp_twice(rd):
         D = torch.full((n, n), -7, dtype=torch.int32, device="cuda")
         rd.rd_apsp_noalloc(At, n, g, D, stream)
         torch.cuda.synchronize()
-        assert np.array_equal(D.cpu().numpy(), reference_D(rd, A, g))
+        got = D.cpu().numpy()
+        assert np.array_equal(got, oracle.rdistance(A, g))
+        assert np.array_equal(got, handle_D(rd, A, g))
 
 
 def test_noalloc_rejects_what_it_cannot_hold(rd):
