@@ -339,9 +339,45 @@ def pct(xs, q):
 BATCH_METRIC = "batched R-distance APSP, 4096 graphs n~U[32,512] (ER/grid/WS), graphs/s"
 
 
+def time_batch(b, A_dev, D_dev, steps, warmup, dev, local, world, dist):
+    """Capture one rd_batch_apsp in a CUDA graph, replay it warmup times, then time `steps`
+    replays with CUDA events (max over ranks); returns per-step ms, total ms and the clock record."""
+    import torch
+
+    stream = torch.cuda.Stream(dev)
+    b.apsp(A_dev, D_dev, stream.cuda_stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        b.apsp(A_dev, D_dev, stream.cuda_stream)
+    for _ in range(warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    cur = torch.cuda.current_stream(dev)
+    ev[0].record(cur)
+    for i in range(steps):
+        graph.replay()
+        ev[i + 1].record(cur)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    tot = reduce_max(ev[0].elapsed_time(ev[-1]), dist, world, f"cuda:{local}")
+    return per, tot, clk
+
+
 def run_batched(args):
-    """The batched workload: every graph of the batch through the whole method in one persistent
-    launch (rd_batch_apsp), captured once in a CUDA graph and replayed per step."""
+    """The batched workload: every graph of the batch through the whole method (rd_batch_apsp),
+    captured once in a CUDA graph and replayed per step, in two variants: the split variant with
+    the per-size-class choice of the library's autotuner (the headline) and the FP64 Gauss-Jordan
+    kernel alone (compare); D of both is compared graph by graph."""
     import torch
     import torch.distributed as dist
 
@@ -372,34 +408,20 @@ def run_batched(args):
         A_np[off[g]:off[g + 1]] = A.ravel()
     A_dev = A_host.to(dev)
     D_dev = torch.empty(total, dtype=torch.int32, device=dev)
-    stream = torch.cuda.Stream(dev)
-    # capture the launch once (a memset and one kernel); steps replay the graph
-    b.apsp(A_dev, D_dev, stream.cuda_stream)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        b.apsp(A_dev, D_dev, stream.cuda_stream)
-    for _ in range(args.warmup):
-        graph.replay()
-    torch.cuda.synchronize()
+    # the FP64 variant: one memset and the persistent Gauss-Jordan kernel per step
+    per64, tot64, clk64 = time_batch(b, A_dev, D_dev, args.steps, args.warmup, dev, local, world, dist)
+    st64 = b.status()
+    D64 = D_dev.cpu()
+    ms64 = tot64 / args.steps
+    # the split variant, size classes chosen by the autotuner (timed on probe graphs at set-up)
+    t_tune = time.perf_counter()
+    b.set_precision(rd.RD_PREC_SPLIT_BF16, True)
+    t_tune = time.perf_counter() - t_tune
+    tune = b.tuning()
+    per, tot, clk = time_batch(b, A_dev, D_dev, args.steps, args.warmup, dev, local, world, dist)
     st = b.status()
-    clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    cur = torch.cuda.current_stream(dev)
-    ev[0].record(cur)
-    for i in range(args.steps):
-        graph.replay()
-        ev[i + 1].record(cur)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    tot = reduce_max(ev[0].elapsed_time(ev[-1]), dist, world, f"cuda:{local}")
+    routes = b.routes()
+    same_as_fp64 = bool(torch.equal(D_dev.cpu(), D64))
     ms = tot / args.steps
     value = world * len(ns) * args.steps / (tot * 1e-3)
     # end to end through the C ABI: A from pinned host memory in, D out to pinned host memory
@@ -411,8 +433,9 @@ def run_batched(args):
         D_host.copy_(D_dev, non_blocking=True)
         torch.cuda.synchronize()
     te = reduce_max((time.perf_counter() - te0) / max(1, args.e2e_steps), dist, world, f"cuda:{local}")
-    sm_mhz = clk.get("sm_mhz") or 2070.0
+    sm_mhz = clk64.get("sm_mhz") or 2070.0
     peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    achieved64 = flop / (ms64 * 1e-3) / 1e12
     achieved = flop / (ms * 1e-3) / 1e12
     b.close()
     if rank != 0:
@@ -433,22 +456,36 @@ def run_batched(args):
         cpu = {"value": len(ns) / (tcpu * scale), "unit": "graphs/s", "cores": 1, "kind": "oracle",
                "sample": f"CPU oracle (1 thread, FP64) on {len(sample)} evenly spaced graphs of the batch, "
                          f"{tcpu:.2f} s, scaled to the batch by sum 2 n^3"}
+    rh = {name: int((routes == k).sum()) for k, name in
+          enumerate(["fp64_class", "split", "split_redone_fp64", "screened_to_fp64", "gain_failed"])}
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16-digits+f64", "data": "synthetic",
         "config": {"workload": f"{len(ns)} graphs, n uniform in [32, 512], kind uniform over ER p=4/n, "
                                f"grid ceil(sqrt n) columns, WS k=10 beta=0.1; gain 0.5/(Delta+1)",
                    "graphs": len(ns), "sum_2n3_flop": flop, "sum_n2": total,
-                   "launch": "one persistent kernel per step, replayed from a CUDA graph",
+                   "variant": "split (size classes chosen by the autotuner), FP64 Gauss-Jordan for the rest",
+                   "launch": "one CUDA graph per step (split stacks, then the persistent FP64 kernel)",
                    "l2": "no flush: FP64 workspace 8 sum n^2 = %.2f GB > 129 MB L2" % (8 * total / 1e9),
                    "parallelism": f"replicas x{world}"},
-        "p50_ms": pct(per, 0.5), "p99_ms": pct(per, 0.99), "tflops": achieved,
+        "p50_ms": pct(per, 0.5), "p99_ms": pct(per, 0.99), "tflops_2n3": achieved,
         "graphs_ok": int((st == rd.RD_OK).sum()), "graphs": len(ns),
-        "clocks": clk, "gpu_launches": 1,
-        "roofline": {"kernel": "batch_kernel", "bound": "alu",
+        "routes": rh, "D_identical_to_fp64_variant": same_as_fp64,
+        "autotuner": dict(tune, seconds=round(t_tune, 2),
+                          class_n_range=["(0,128]", "(128,256]", "(256,384]", "(384,512]"]),
+        "compare": {"variant": "fp64 Gauss-Jordan, one persistent kernel", "value": world * len(ns) * args.steps /
+                    (tot64 * 1e-3), "unit": "graphs/s", "ms_per_step": ms64, "p50_ms": pct(per64, 0.5),
+                    "p99_ms": pct(per64, 0.99), "graphs_ok": int((st64 == rd.RD_OK).sum()),
+                    "tflops": achieved64, "clocks": clk64,
+                    "roofline": {"kernel": "batch_kernel", "bound": "alu",
+                                 "peak_source": f"FP64 pipe: 152 SMs x 4 flop/clk x {sm_mhz:.0f} MHz (unit counts)",
+                                 "achieved": achieved64, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": achieved64 / peak}},
+        "clocks": clk, "gpu_launches": tune["launches_last_run"],
+        "roofline": {"kernel": "batch_kernel (FP64 variant)", "bound": "alu",
                      "peak_source": f"FP64 pipe: 152 SMs x 4 flop/clk x {sm_mhz:.0f} MHz (unit counts)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "achieved": achieved64, "peak": peak, "unit": "TFLOP/s", "frac": achieved64 / peak,
                      "traffic": None},
         "e2e": {"value": world * len(ns) / te, "unit": "graphs/s", "ms_per_step": te * 1e3,
                 "h2d_bytes_per_step": total, "d2h_bytes_per_step": 4 * total},

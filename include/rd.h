@@ -289,6 +289,39 @@ rd_status rd_batch_status(rd_batch_handle b, int32_t* status);
 /* Free a batch (NULL is ignored). */
 void rd_batch_destroy(rd_batch_handle b);
 
+/* Size classes of a batch: n in (128 c, 128 (c + 1)], c = 0..RD_BATCH_CLASSES-1. */
+#define RD_BATCH_CLASSES 4
+
+/* Precision of a batch's inverses.  RD_PREC_FP64 (the default): every graph by the FP64
+ * Gauss-Jordan kernel above.  RD_PREC_SPLIT_BF16: the graphs of chosen size classes run the split
+ * path (the single-graph method's recursive LU and triangular inverses with exact BF16 digit
+ * products on the tensor cores, FP64 leaves and decode) with graphs of one class stacked, so that
+ * every launch covers all of them; per graph, on the device, a range screen (BFS from 8 sources,
+ * as rd_set_precision's) picks the digit count and a residual check of every entry of M Y - I
+ * (the single-graph self-check's limit) keeps the result, and graphs that fail either (or fail the
+ * gain check) are redone by the FP64 kernel in the same run.  A run stays one fixed sequence of
+ * launches on the stream (no host synchronisation: capturable in a CUDA graph).  With autotune = 1
+ * each size class runs on the split path only when it measured faster there, by timing both
+ * variants on up to 152 seeded random graphs of the class's sizes (directed ER, p = 4/n); with 0
+ * every class with graphs runs on the split path.  Allocates the split workspace (for up to 512
+ * graphs of one class per stack, about 2 * 15 * 2 * N (N + 256) bytes of digit planes per graph of
+ * the largest stack, shared by the stacks) and synchronises.  Extends the paper's method to many
+ * graphs at once (no counterpart in the paper). */
+rd_status rd_batch_set_precision(rd_batch_handle b, int32_t mode, int32_t autotune);
+
+/* Per-graph route of the last run (host array of G): 0 FP64 kernel (its class is not on the split
+ * path), 1 split path, 2 split path failed the residual check and was redone in FP64, 3 screened
+ * off the split path (more than 15 digits, or too many edges to screen) and computed in FP64,
+ * 4 failed the gain check (status RD_ERR_GAMMA).  Synchronises the device. */
+rd_status rd_batch_routes(rd_batch_handle b, int32_t* routes);
+
+/* The autotuner's record per size class (host arrays of RD_BATCH_CLASSES): graphs of the batch in
+ * the class, 1 if the class runs on the split path, and the measured device ms per graph of the
+ * FP64 and split variants on the probe graphs (0 when not measured); *launches receives the kernel
+ * launches of the last rd_batch_apsp. */
+rd_status rd_batch_tuning(rd_batch_handle b, int32_t* graphs, int32_t* split, double* ms_fp64, double* ms_split,
+                          int64_t* launches);
+
 /* ---- Serving (continuous batching of requests over resident graphs) --------------------------
  * A server runs requests -- the full R-distance of a graph, or goal rows (the local mode of
  * Sec. 4.2) -- on `workers` threads, each with its own CUDA stream, one request per worker at a

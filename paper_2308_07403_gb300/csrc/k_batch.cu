@@ -39,6 +39,7 @@ struct BatchArgs {
   int* counter;          // work queue head (zeroed before the launch)
   int32_t* status;       // per graph: RD_OK, RD_ERR_GAMMA, RD_ERR_NUMERIC
   double tau;
+  const int32_t* done;   // per graph: 1 = already computed (the split variant kept its result); may be null
 };
 
 // C (rows x cols tile at global (r0, c0) of an n x n matrix) -= A (rows x kb) B (kb x cols), with
@@ -104,6 +105,10 @@ __global__ void __launch_bounds__(BT) batch_kernel(const BatchArgs p) {
     __syncthreads();
     const int g = s_graph;
     if (g < 0) return;
+    if (p.done && p.done[g]) {  // (uniform: every thread reads the same flag)
+      __syncthreads();            // every thread has read s_graph before thread 0 takes the next
+      continue;
+    }
     const int n = p.n[g];
     const double gamma = p.gamma[g];
     const uint8_t* A = p.A + p.off[g];
@@ -275,15 +280,76 @@ struct rd_batch {
   double* d_W = nullptr;
   int blocks = 0;
   std::string err;
+  std::vector<int32_t> n;      // node counts (host)
+  std::vector<double> gamma;   // gains (host)
+  // split precision (rd_batch_set_precision): the split plan of the size classes that run on it
+  int precision = RD_PREC_FP64;
+  rd_batch_split* split = nullptr;
+  int32_t* d_done = nullptr;    // per graph: 1 = the split variant kept its result
+  int32_t* d_routes = nullptr;  // per graph: the route of its last run (rd_batch_routes)
+  double tune_ms_fp64[RD_BATCH_CLASSES] = {}, tune_ms_split[RD_BATCH_CLASSES] = {};
+  int32_t tune_split[RD_BATCH_CLASSES] = {};
+  int32_t tune_graphs[RD_BATCH_CLASSES] = {};
+  int64_t launches = 0;  // kernel launches of the last run
 };
 
 namespace {
 constexpr size_t BATCH_SMEM = 3 * BB * LDS * sizeof(double);
 
 void batch_free(rd_batch* b) {
-  void* ptrs[] = {b->d_off, b->d_n, b->d_gamma, b->d_order, b->d_status, b->d_counter, b->d_W};
+  rd_bsplit_destroy(b->split);
+  b->split = nullptr;
+  void* ptrs[] = {b->d_off, b->d_n, b->d_gamma, b->d_order, b->d_status, b->d_counter, b->d_W, b->d_done, b->d_routes};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+}
+
+// size class of a graph: n rounded up to a multiple of 128, as an index 0..RD_BATCH_CLASSES-1
+int size_class(int n) { return (n + RD_PAD - 1) / RD_PAD - 1; }
+
+// Seeded directed Erdos-Renyi graphs (p = 4/n, no self-loops) for the autotuner's probes: A packed
+// as a batch (A_ij != 0 iff edge j -> i), gain 0.5 / (Delta + 1).  SplitMix64 per entry.
+uint64_t splitmix(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+void probe_graphs(const std::vector<int32_t>& n, std::vector<uint8_t>& A, std::vector<double>& gamma,
+                  std::vector<int64_t>& off) {
+  off.assign(n.size() + 1, 0);
+  for (size_t g = 0; g < n.size(); ++g) off[g + 1] = off[g] + (int64_t)n[g] * n[g];
+  A.assign((size_t)off.back(), 0);
+  gamma.resize(n.size());
+  for (size_t g = 0; g < n.size(); ++g) {
+    const int m = n[g];
+    const uint64_t thr = (uint64_t)((4.0 / m) * 18446744073709551615.0);
+    std::vector<int> deg(m, 0);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        if (i != j && splitmix(((uint64_t)g << 40) ^ ((uint64_t)i << 20) ^ (uint64_t)j) < thr) {
+          A[off[g] + (int64_t)i * m + j] = 1;
+          deg[j]++;
+        }
+    gamma[g] = 0.5 / (*std::max_element(deg.begin(), deg.end()) + 1);
+  }
+}
+
+// Device time (ms) of the second of two runs of a batch on `st` (CUDA events).
+double time_runs(rd_batch* b, const uint8_t* A, int32_t* D, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  rd_batch_apsp(b, A, D, st);
+  cudaEventRecord(e0, st);
+  rd_batch_apsp(b, A, D, st);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
 }
 }  // namespace
 
@@ -310,6 +376,8 @@ rd_status rd_batch_create(const int32_t* n, const double* gamma, int32_t G, rd_b
     b->max_n = std::max(b->max_n, (int)n[g]);
   }
   b->total = b->off[G];
+  b->n.assign(n, n + G);
+  b->gamma.assign(gamma, gamma + G);
   std::vector<int32_t> order(G);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return n[a] > n[c]; });
@@ -324,11 +392,14 @@ rd_status rd_batch_create(const int32_t* n, const double* gamma, int32_t G, rd_b
   get((void**)&b->d_status, G * sizeof(int32_t));
   get((void**)&b->d_counter, sizeof(int));
   get((void**)&b->d_W, (size_t)b->total * sizeof(double));
+  get((void**)&b->d_done, G * sizeof(int32_t));
+  get((void**)&b->d_routes, G * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_off, b->off.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_n, n, G * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_gamma, gamma, G * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_order, order.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0xff, G * sizeof(int32_t));  // -1: not run yet
+  if (e == cudaSuccess) e = cudaMemset(b->d_routes, 0, G * sizeof(int32_t));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_SMEM);
   int per_sm = 0, sms = 0;
@@ -355,6 +426,15 @@ rd_status rd_batch_apsp(rd_batch_handle b, const uint8_t* A, int32_t* D, void* s
   if (!b || !A || !D) return RD_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+  b->launches = 1;
+  if (e == cudaSuccess && b->split) {
+    // the split variant first (its stacks decide on the device which graphs it keeps), then the
+    // FP64 kernel for every other graph
+    e = cudaMemsetAsync(b->d_done, 0, b->G * sizeof(int32_t), s);
+    int64_t n_split = 0;
+    if (e == cudaSuccess) e = rd_bsplit_run(b->split, A, D, b->d_status, b->d_done, b->d_routes, s, &n_split);
+    b->launches += n_split;
+  }
   if (e != cudaSuccess) {
     b->err = cudaGetErrorString(e);
     return RD_ERR_CUDA;
@@ -371,6 +451,7 @@ rd_status rd_batch_apsp(rd_batch_handle b, const uint8_t* A, int32_t* D, void* s
   a.counter = b->d_counter;
   a.status = b->d_status;
   a.tau = b->tau;
+  a.done = b->split ? b->d_done : nullptr;
   batch_kernel<<<b->blocks, BT, BATCH_SMEM, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) {
     b->err = cudaGetErrorString(e);
@@ -394,6 +475,107 @@ void rd_batch_destroy(rd_batch_handle b) {
   if (!b) return;
   batch_free(b);
   delete b;
+}
+
+rd_status rd_batch_set_precision(rd_batch_handle b, int32_t mode, int32_t autotune) {
+  if (!b) return RD_ERR_ARG;
+  if (mode != RD_PREC_FP64 && mode != RD_PREC_SPLIT_BF16) {
+    rd_record_error("rd_batch_set_precision: unknown precision mode");
+    return RD_ERR_ARG;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  rd_bsplit_destroy(b->split);
+  b->split = nullptr;
+  b->precision = mode;
+  for (int c = 0; c < RD_BATCH_CLASSES; ++c) {
+    b->tune_ms_fp64[c] = b->tune_ms_split[c] = 0.0;
+    b->tune_split[c] = 0;
+    b->tune_graphs[c] = 0;
+  }
+  if (e == cudaSuccess) e = cudaMemset(b->d_routes, 0, b->G * sizeof(int32_t));
+  if (e != cudaSuccess) {
+    rd_record_error(std::string("rd_batch_set_precision: ") + cudaGetErrorString(e));
+    return RD_ERR_CUDA;
+  }
+  if (mode == RD_PREC_FP64) return RD_OK;
+  std::vector<std::vector<int32_t>> cls(RD_BATCH_CLASSES);
+  for (int g = 0; g < b->G; ++g) cls[size_class(b->n[g])].push_back(g);
+  std::string err;
+  cudaStream_t st = nullptr;
+  for (int c = 0; c < RD_BATCH_CLASSES; ++c) {
+    b->tune_graphs[c] = (int32_t)cls[c].size();
+    if (cls[c].empty()) continue;
+    if (!autotune) {
+      b->tune_split[c] = 1;
+      continue;
+    }
+    // The autotuner: time both variants on up to 152 seeded random graphs of this class's sizes (a
+    // full wave of the FP64 kernel) and keep the faster per graph
+    const size_t P = std::min<size_t>(cls[c].size(), 152);
+    std::vector<int32_t> pn(P), pid(P);
+    for (size_t q = 0; q < P; ++q) {
+      pn[q] = b->n[cls[c][q]];
+      pid[q] = (int32_t)q;
+    }
+    std::vector<uint8_t> pA;
+    std::vector<double> pg;
+    std::vector<int64_t> poff;
+    probe_graphs(pn, pA, pg, poff);
+    rd_batch* pb = nullptr;
+    rd_status rs = rd_batch_create(pn.data(), pg.data(), (int32_t)P, &pb);
+    uint8_t* dA = nullptr;
+    int32_t* dD = nullptr;
+    if (rs == RD_OK) {
+      e = cudaMalloc((void**)&dA, pA.size());
+      if (e == cudaSuccess) e = cudaMalloc((void**)&dD, pA.size() * sizeof(int32_t));
+      if (e == cudaSuccess) e = cudaMemcpy(dA, pA.data(), pA.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) b->tune_ms_fp64[c] = time_runs(pb, dA, dD, st) / P;
+      if (e == cudaSuccess) rs = rd_bsplit_create(pn.data(), pg.data(), poff.data(), pid.data(), (int)P, b->tau,
+                                                  &pb->split, &err);
+      if (e == cudaSuccess && rs == RD_OK) b->tune_ms_split[c] = time_runs(pb, dA, dD, st) / P;
+      if (e == cudaSuccess && rs == RD_OK) e = cudaDeviceSynchronize();
+    }
+    if (dA) cudaFree(dA);
+    if (dD) cudaFree(dD);
+    rd_batch_destroy(pb);
+    if (rs != RD_OK || e != cudaSuccess) {
+      rd_record_error("rd_batch_set_precision: autotuner: " + (e != cudaSuccess ? std::string(cudaGetErrorString(e)) : err));
+      return rs != RD_OK ? rs : RD_ERR_CUDA;
+    }
+    b->tune_split[c] = b->tune_ms_split[c] < b->tune_ms_fp64[c] ? 1 : 0;
+  }
+  std::vector<int32_t> gids;
+  for (int c = 0; c < RD_BATCH_CLASSES; ++c)
+    if (b->tune_split[c]) gids.insert(gids.end(), cls[c].begin(), cls[c].end());
+  if (gids.empty()) return RD_OK;
+  const rd_status rs = rd_bsplit_create(b->n.data(), b->gamma.data(), b->off.data(), gids.data(), (int)gids.size(),
+                                        b->tau, &b->split, &err);
+  if (rs != RD_OK) rd_record_error("rd_batch_set_precision: " + err);
+  return rs;
+}
+
+rd_status rd_batch_routes(rd_batch_handle b, int32_t* routes) {
+  if (!b || !routes) return RD_ERR_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(routes, b->d_routes, b->G * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    b->err = cudaGetErrorString(e);
+    return RD_ERR_CUDA;
+  }
+  return RD_OK;
+}
+
+rd_status rd_batch_tuning(rd_batch_handle b, int32_t* graphs, int32_t* split, double* ms_fp64, double* ms_split,
+                          int64_t* launches) {
+  if (!b || !graphs || !split || !ms_fp64 || !ms_split || !launches) return RD_ERR_ARG;
+  *launches = b->launches;
+  for (int c = 0; c < RD_BATCH_CLASSES; ++c) {
+    graphs[c] = b->tune_graphs[c];
+    split[c] = b->tune_split[c];
+    ms_fp64[c] = b->tune_ms_fp64[c];
+    ms_split[c] = b->tune_ms_split[c];
+  }
+  return RD_OK;
 }
 
 }  // extern "C"

@@ -48,6 +48,10 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(rd_gemm_f64_args p0, rd_ge
   constexpr int R = T / 16;           // micro-tile edge
   constexpr int LA = T * BK / NT;     // elements of A (and of B) each thread stages per K step
   const rd_gemm_f64_args& p = (blockIdx.z == 0) ? p0 : p1;
+  // graph blockIdx.y of a stacked batch (strides 0 for one graph)
+  const double* __restrict__ pA = p.A + (long long)blockIdx.y * p.a_gs;
+  const double* __restrict__ pB = p.B + (long long)blockIdx.y * p.b_gs;
+  double* pC = p.C + (long long)blockIdx.y * p.c_gs;
   const int tiles_n = p.N / T;
   const int tiles = (p.M / T) * tiles_n;
   const int tile = blockIdx.x;
@@ -81,8 +85,8 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(rd_gemm_f64_args p0, rd_ge
   auto load_regs = [&](int k0) {
 #pragma unroll
     for (int e = 0; e < LA; ++e) {
-      ra[e] = tri_load(p.A, p.lda, r0 + a_r, k0 + a_k + e, p.a_tri);
-      rb[e] = tri_load(p.B, p.ldb, k0 + b_k, c0 + b_c + e, p.b_tri);
+      ra[e] = tri_load(pA, p.lda, r0 + a_r, k0 + a_k + e, p.a_tri);
+      rb[e] = tri_load(pB, p.ldb, k0 + b_k, c0 + b_c + e, p.b_tri);
     }
   };
   auto store_regs = [&](int buf) {
@@ -131,8 +135,8 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(rd_gemm_f64_args p0, rd_ge
     for (int j = 0; j < R; ++j) {
       const int c = c0 + tx + 16 * j;
       double v = p.alpha * acc[i][j];
-      if (p.beta != 0.0) v = fma(p.beta, p.C[(long long)r * p.ldc + c], v);
-      if (p.store_c && r < p.c_rows && c < p.c_cols) p.C[(long long)r * p.ldc + c] = v;
+      if (p.beta != 0.0) v = fma(p.beta, pC[(long long)r * p.ldc + c], v);
+      if (p.store_c && r < p.c_rows && c < p.c_cols) pC[(long long)r * p.ldc + c] = v;
       if (p.D && r < p.d_rows && c < p.d_cols) {
         int32_t d;
         if (!isfinite(v)) {
@@ -156,6 +160,21 @@ cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cud
   int T = 64;
   long long work = 0;
   bool aliased = false;
+  // a stacked batch: every problem for every graph (graph 0's pointers, per-graph strides)
+  rd_gemm_f64_args q[2];
+  const int nb = h->nbatch > 1 ? h->nbatch : 1;
+  for (int i = 0; i < nprob; ++i) {
+    q[i] = probs[i];
+    if (nb > 1) {
+      if (q[i].D) return cudaErrorInvalidValue;  // no fused decode in stacked batches
+      q[i].a_gs = rd_batch_stride(h, q[i].A);
+      q[i].b_gs = rd_batch_stride(h, q[i].B);
+      q[i].c_gs = rd_batch_stride(h, q[i].C);
+    } else {
+      q[i].a_gs = q[i].b_gs = q[i].c_gs = 0;
+    }
+  }
+  probs = q;
   for (int i = 0; i < nprob; ++i) {
     const rd_gemm_f64_args& p = probs[i];
     if (p.M % 16 || p.N % 16 || p.K % BK || p.M < 0 || p.N < 0 || p.K < 0) return cudaErrorInvalidValue;
@@ -164,7 +183,7 @@ cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cud
       aliased = true;
       if (p.beta != 0.0 || (p.M != 64 && p.N != 64)) return cudaErrorInvalidValue;
     }
-    work += (long long)p.M * p.N;
+    work += (long long)p.M * p.N * nb;
   }
   if (aliased && T != 64) return cudaErrorInvalidValue;
   while (!aliased && T > 16 && work / ((long long)T * T) < 2 * 152) T /= 2;
@@ -174,7 +193,7 @@ cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cud
     if (t > maxtiles) maxtiles = t;
   }
   if (maxtiles == 0) return cudaSuccess;
-  dim3 grid(maxtiles, 1, nprob);
+  dim3 grid(maxtiles, nb, nprob);
   cudaError_t e = rd_prof_begin(h, s, RD_PROF_F64);
   if (e != cudaSuccess) return e;
   const rd_gemm_f64_args& q1 = nprob > 1 ? probs[1] : probs[0];

@@ -77,12 +77,14 @@ __device__ __forceinline__ void leaf_lu_chunk(double (&a)[4][4], LeafLuShared& s
   }
 }
 
+// (a stacked batch: graph blockIdx.x, its matrix gs doubles further, its status in bg)
 __global__ void __launch_bounds__(256) leaf_lu_kernel(double* __restrict__ LU, long long ld, int k0,
-                                                      int* status) {
+                                                      int* status, long long gs, rd_batch_graph* bg) {
   static_assert(B == 64, "the leaf kernels are laid out for 64 x 64 blocks");
   __shared__ LeafLuShared sm;
   const int t = threadIdx.x, r = t >> 4, c = t & 15, w = t >> 5;
-  double* blk = LU + (long long)k0 * ld + k0;
+  if (bg) status = bg[blockIdx.x].status;
+  double* blk = LU + (long long)blockIdx.x * gs + (long long)k0 * ld + k0;
   double a[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -105,11 +107,14 @@ __global__ void __launch_bounds__(256) leaf_lu_kernel(double* __restrict__ LU, l
 // step's pivot entry reaches the warp by shuffle and the factor is read from shared memory
 // (padded rows: column reads are conflict-free).  32 CTAs of 4 warps: CTAs 0..15 take the
 // columns of L^-1, 16..31 those of U^-1, so the FP64 work is spread over 32 SMs.
+// (a stacked batch: graph blockIdx.y, its matrices gs doubles further)
 __global__ void __launch_bounds__(128) leaf_inv_kernel(const double* __restrict__ LU,
-                                                       double* __restrict__ T, long long ld, int k0) {
+                                                       double* __restrict__ T, long long ld, int k0, long long gs) {
   __shared__ double f[B][B + 1];
   __shared__ double rcp[B];
   const int t = threadIdx.x, lane = t & 31;
+  LU += (long long)blockIdx.y * gs;
+  T += (long long)blockIdx.y * gs;
   const double* blk = LU + (long long)k0 * ld + k0;
   for (int e = t; e < B * B; e += blockDim.x) f[e / B][e % B] = blk[(long long)(e / B) * ld + e % B];
   const bool lower = blockIdx.x < 16;
@@ -155,11 +160,13 @@ rd_gemm_f64_args blank() {
 cudaError_t rd_lu_diag(rd_ctx* h, int k0, cudaStream_t s) {
   cudaError_t e;
   if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
-  leaf_lu_kernel<<<1, 256, 0, s>>>(h->dLU, h->N, k0, h->dStatus);
+  const int nb = h->nbatch > 1 ? h->nbatch : 1;
+  const long long gs = nb > 1 ? (long long)h->N * h->N : 0;
+  leaf_lu_kernel<<<nb, 256, 0, s>>>(h->dLU, h->N, k0, h->dStatus, gs, nb > 1 ? h->dBatch : nullptr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
-  leaf_inv_kernel<<<32, 128, 0, s>>>(h->dLU, h->dT, h->N, k0);
+  leaf_inv_kernel<<<dim3(32, nb), 128, 0, s>>>(h->dLU, h->dT, h->N, k0, gs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }

@@ -23,9 +23,11 @@
 // The operands of every product of the inverse are sign-definite, so the accumulated value is
 // accurate relative to itself; the digit count s sets the precision.
 //
-// Kernel structure (one CTA per 128 x 128 output tile, 320 threads, 512 tensor-memory columns):
-//   warp 0      TMA producer: digit tiles A_p[128 x 64] and B_q[128 x 64] into a 3-stage ring,
-//               two (pair, K step) items per stage
+// Kernel structure (one CTA per 128 x 128 output tile, 320 threads, 512 tensor-memory columns; with
+// 256-wide chunks a cluster of two CTAs per 256 x 128 tile, tcgen05 cta_group::2, see Ring):
+//   warp 0      TMA producer: digit tiles A_p[128 x 64] and B_q[128 x 64] (a pair: each CTA its
+//               half of B, 64 x 64) into a 3-stage ring of two (pair, K step) items per stage (a
+//               pair: 2 stages of four)
 //   warp 1      TMEM allocator and MMA issuer (one thread): tcgen05.mma.kind::f16, M=N=128,
 //               K=16, 8 MMAs per wait; group accumulators double-buffered in tensor memory
 //               (columns 0..255)
@@ -58,9 +60,6 @@ constexpr int SIGMA = 7;          // bits per digit (balanced base 2^SIGMA)
 constexpr int KAPPA_WIDE = 256;   // exponent / read-out chunk along K (natural order)
 constexpr int KAPPA_NARROW = 64;  // the same with the locality order (compact 64-node parts)
 constexpr int TM = 128, TN = 128, TK = 64;
-constexpr int STAGES = 3;          // ring stages; each holds ITEMS (A, B) tile pairs of one digit group
-constexpr int ITEMS = 2;           // (pair, K step) items per stage: 8 MMAs per wait of the MMA thread
-constexpr int SLOTS = STAGES * ITEMS;  // 16 KiB tile slots per operand
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr int TILE_BYTES = TM * TK * 2;            // one 128 x 64 BF16 tile: 16 KiB
@@ -79,21 +78,52 @@ static_assert((long long)KAPPA_WIDE * MAX_SLICES_WIDE * 4096 < (1 << 24) &&
 static_assert(ACC_OFF - SIGMA * (MAX_SLICES_NARROW + 1) >= -126 && ACC_OFF - 2 * SIGMA + 24 + 17 < 127,
               "group scales normal, accumulators finite");
 
-constexpr uint32_t IDESC = (1u << 4)               // D: FP32
-                           | (1u << 7)             // A: BF16
-                           | (1u << 10)            // B: BF16
-                           | ((uint32_t)(TN >> 3) << 17)  // N
-                           | ((uint32_t)(TM >> 4) << 24); // M  (A and B K-major)
+// instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator, BF16 A and B (both K-major),
+// N = TN, and M = 128 (one CTA) or 256 (a CTA pair, 128 rows in each CTA's tensor memory)
+constexpr uint32_t idesc(int m) {
+  return (1u << 4)                        // D: FP32
+         | (1u << 7)                      // A: BF16
+         | (1u << 10)                     // B: BF16
+         | ((uint32_t)(TN >> 3) << 17)    // N
+         | ((uint32_t)(m >> 4) << 24);    // M
+}
 
-constexpr int REF_OFFSET = 2 * SLOTS * TILE_BYTES + 256 + 2 * TN * 4;  // per-entry reference exponents
+// Shared-memory layout of the two kernel variants.  One CTA per 128 x 128 tile (PAIR = false): a
+// ring of 3 stages, each holding 2 items of (A, B) 16 KiB tiles.  A CTA pair per 256 x 128 tile
+// (PAIR = true, tcgen05 cta_group::2): each CTA holds its own 128 rows of A (16 KiB) and half of
+// the B tile (64 rows, 8 KiB) per item, so an item costs each CTA 24 KiB of L2 reads instead of
+// 32 KiB and one MMA instruction does twice the work; the same 192 KiB then hold 2 stages of 4
+// items.  Measured on the inverse product (256-wide chunks): 4 items x 2 stages 5 % faster than the
+// one-CTA kernel (n = 4096 and 8192), 2 items x 4 stages and 3 x 2 slower; with 64-wide chunks,
+// whose groups fill few items, the pair kernel is 2 % slower, so it runs for 256-wide chunks only.
+// After the ring: the barriers (256 B), the chunk exponents of the tile's columns (2 x TN ints)
+// and the per-entry reference exponents (TM x TN int16).
+template <bool PAIR>
+struct Ring {
+  // (digit pair, K step) items per stage: each item is TK / 16 = 4 MMAs, and the MMA thread waits
+  // once per stage (a wait costs the tensor pipe about as much whatever the MMA size, so the pair
+  // kernel's 4 items of M = 256 MMAs give 1024 tensor cycles per wait against 512)
+  static constexpr int ITEMS = PAIR ? 4 : 2;
+  static constexpr int STAGES = PAIR ? 2 : 3;
+  static constexpr int SLOTS = STAGES * ITEMS;
+  static constexpr int A_BYTES = TILE_BYTES;
+  static constexpr int B_BYTES = PAIR ? TILE_BYTES / 2 : TILE_BYTES;
+  static constexpr int BAR_OFFSET = SLOTS * (A_BYTES + B_BYTES);
+  static constexpr int ECOL_OFFSET = BAR_OFFSET + 256;
+  static constexpr int REF_OFFSET = ECOL_OFFSET + 2 * TN * 4;
+  static constexpr size_t SMEM = 1024 + REF_OFFSET + TM * TN * 2;
+  static constexpr uint32_t IDESC = idesc(PAIR ? 2 * TM : TM);
+};
+static_assert((2 * 4 + 2 * 2 + 1) * 8 + 8 <= 256, "barriers, tensor-memory slot and abort flag");
+static_assert(Ring<false>::SMEM <= 232448 && Ring<true>::SMEM <= 232448, "shared memory of one CTA");
+static_assert(Ring<true>::A_BYTES % 1024 == 0 && Ring<true>::B_BYTES % 1024 == 0, "128-byte swizzle atoms");
+
 constexpr int16_t REF_NONE = -32768;                                    // no chunk with digits yet
-constexpr size_t SMEM_BYTES = 1024 + REF_OFFSET + TM * TN * 2;
 // tensor memory: two accumulator buffers, the low words of the float-float accumulators, and the
 // per-entry scale of the current chunk (one 32-bit column per tile column each)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t TMEM_LO = 2 * TN;
 constexpr uint32_t TMEM_SCALE = 3 * TN;
-static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
 
 // ---- PTX wrappers -----------------------------------------------------------------------
 
@@ -122,11 +152,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // NOSLEEP: a zero suspend-time hint, for the MMA thread: every wait of the thread that issues the
 // MMAs delays its next MMA (the tensor pipe's instruction queue is shallow), and a plain try_wait
-// costs it more (measured: 56 % against 67 % of the tensor peak with one wait per 4 MMAs)
-template <bool NOSLEEP = false>
+// costs it more (measured: 56 % against 67 % of the tensor peak with one wait per 4 MMAs).
+// CLUSTER: acquire at cluster scope, for barriers that the other CTA of a pair arrives on (its
+// epilogue's release of an accumulator, its TMA copies, the pair's MMA commits).
+template <bool NOSLEEP = false, bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
-  if (NOSLEEP)
+  if (CLUSTER && NOSLEEP)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  else if (CLUSTER)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  else if (NOSLEEP)
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 0;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
@@ -142,11 +188,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase of `parity` to complete; false when the CTA aborted or the deadline passed.
-template <bool NOSLEEP = false>
+template <bool NOSLEEP = false, bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           unsigned long long deadline) {
   uint32_t spins = 0;
-  while (!mbar_try_wait<NOSLEEP>(bar, parity)) {
+  while (!mbar_try_wait<NOSLEEP, CLUSTER>(bar, parity)) {
     if ((++spins & 1023u) == 0) {
       if (*abort_flag) return false;
       if (globaltimer() > deadline) {
@@ -156,6 +202,40 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     }
   }
   return true;
+}
+
+// ---- CTA pairs (a cluster of two CTAs sharing each MMA: tcgen05 cta_group::2) ------------------
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// the shared::cluster address of this CTA's shared-memory word `p` as seen in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa_shared(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+// every thread of both CTAs (a full barrier across the cluster, with release/acquire ordering)
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// arrive on an mbarrier of either CTA of the pair (shared::cluster address)
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+// TMA tile load into this CTA's shared memory whose completion (bytes) is signalled on the pair
+// leader's barrier (bar_cluster: a shared::cluster address, possibly in the peer CTA)
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(bar_cluster), "r"(x), "r"(y)
+      : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -181,17 +261,39 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
   return d;
 }
 
+// D (tensor memory) (+)= A B^T for one K = 16 step.  PAIR: M = 256 issued by the leader CTA of a
+// pair; A's rows 0..127 come from the leader's shared memory and 128..255 from the peer's, B's rows
+// (the N = 128 columns) 0..63 from the leader's and 64..127 from the peer's (same offsets in both),
+// and each CTA's tensor memory receives its 128 rows.
+template <bool PAIR>
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
-      : "memory");
+  if (PAIR)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(Ring<true>::IDESC), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(Ring<false>::IDESC), "r"(accumulate)
+        : "memory");
 }
 
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
+// Arrive (once) on `bar` when every MMA issued so far has completed.  PAIR: on the barrier at the
+// same offset in each CTA of the pair named by `mask` (bit r = CTA rank r).
+template <bool PAIR>
+__device__ __forceinline__ void umma_commit(uint64_t* bar, uint16_t mask = 3) {
+  if (PAIR)
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
 }
 
 // tcgen05.ld of 8 columns without the wait; tmem_wait_ld(r) then waits for every prior load of this
@@ -309,6 +411,14 @@ __device__ __forceinline__ void write_digits2(double x0, double x1, int e, int s
   *reinterpret_cast<__nv_bfloat162*>(out) = __floats2bfloat162_rn((float)(a.neg ? -ta : ta), (float)(b.neg ? -tb : tb));
 }
 
+// A stacked batch (both slicing kernels): graph b = blockIdx.y (rows) or blockIdx.z (columns)
+// reads its operand x_gs doubles further, writes its s_b = bg[b].s digit planes from plane b * s
+// on (s is then the planes per graph) and its exponents e_gs ints further; s_b = 0 skips it.
+struct SliceBatch {
+  const rd_batch_graph* bg;  // nullptr: one graph
+  long long x_gs, e_gs;
+};
+
 // Role A (row chunks contiguous in memory): one warp per (row, chunk), each lane taking pairs of
 // adjacent K positions c0 + 2 lane + 64 t.  digits[p][row][k] (plane = rows_pad * k_pad),
 // exps[chunk][row].
@@ -316,7 +426,15 @@ template <int KP>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, long long ld, int tri,
                                                          int rows, int cols, int rows_pad, int k_pad, int s,
                                                          __nv_bfloat16* __restrict__ dig, int* __restrict__ exps,
-                                                         int* status) {
+                                                         int* status, SliceBatch sb) {
+  if (sb.bg) {
+    const int b = blockIdx.y;
+    X += (long long)b * sb.x_gs;
+    dig += (long long)b * s * rows_pad * k_pad;
+    exps += (long long)b * sb.e_gs;
+    s = sb.bg[b].s;
+    if (s == 0) return;
+  }
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   const int nch = k_pad / KP;
@@ -351,8 +469,16 @@ template <int KP>
 __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ X, long long ld, int tri,
                                                          int krows, int cols, int cols_pad, int k_pad, int s,
                                                          __nv_bfloat16* __restrict__ dig, int* __restrict__ exps,
-                                                         int* status) {
+                                                         int* status, SliceBatch sb) {
   __shared__ double tile[KP][17];
+  if (sb.bg) {
+    const int b = blockIdx.z;
+    X += (long long)b * sb.x_gs;
+    dig += (long long)b * s * cols_pad * k_pad;
+    exps += (long long)b * sb.e_gs;
+    s = sb.bg[b].s;
+    if (s == 0) return;
+  }
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n0 = blockIdx.x * 16;
   const int c0 = blockIdx.y * KP;
@@ -414,52 +540,137 @@ struct SplitArgs {
   // kernel then applies alpha, beta, the bounds and the maps.  ksplit = 1: no partials.
   int ksplit;
   double* partial;
+  // a stacked batch (nbatch > 1): the CTAs of graph b come after those of graphs 0..b-1; graph b
+  // uses bg[b].s digits (0: skipped), its digit planes start at plane b * s_max of each operand's
+  // buffer, its exponents ea_gs / eb_gs ints and its C c_gs doubles further; its D sits at
+  // D + bg[b].off with leading dimension bg[b].n, and the C and D bounds are bg[b].n
+  int nbatch;
+  const rd_batch_graph* bg;
+  int s_max;
+  long long ea_gs, eb_gs, c_gs;
 };
 
-template <int KP>
+// Tile (row pair P of 256 rows, column J of 128) of CTA pair t, longest K range first, as the
+// one-CTA order below: the inverse product (K from max(row, column) on) by increasing
+// s = max(2P, J) (the row pair P = s / 2 for even s, then column J = s); a K range set by the
+// column alone column-major (the last columns first for an upper-triangular B); by the row alone
+// the last row pairs first for a lower-triangular A; otherwise row-major.
+__device__ __forceinline__ void pair_tile(int t, int tp, int tn, int a_tri, int b_tri, int& P, int& J) {
+  if (a_tri == RD_TRI_UPPER && b_tri == RD_TRI_LOWER_UNIT && tn == 2 * tp) {
+    int rem = t;
+    P = J = 0;
+    for (int s = 0; s < tn; ++s) {
+      if ((s & 1) == 0) {
+        if (rem <= s) {  // row pair s / 2, columns 0..s
+          P = s >> 1;
+          J = rem;
+          return;
+        }
+        rem -= s + 1;
+        if (rem < (s >> 1)) {  // column s, row pairs 0 .. s/2 - 1
+          P = rem;
+          J = s;
+          return;
+        }
+        rem -= s >> 1;
+      } else {
+        if (rem < ((s + 1) >> 1)) {  // column s, row pairs 0 .. (s - 1)/2
+          P = rem;
+          J = s;
+          return;
+        }
+        rem -= (s + 1) >> 1;
+      }
+    }
+    return;
+  }
+  if (a_tri == RD_TRI_FULL && b_tri != RD_TRI_FULL) {
+    P = t % tp;
+    J = t / tp;
+    if (b_tri == RD_TRI_UPPER) J = tn - 1 - J;
+    return;
+  }
+  P = t / tn;
+  J = t % tn;
+  if (a_tri == RD_TRI_LOWER_UNIT) P = tp - 1 - P;
+}
+
+// One CTA per 128 x 128 output tile (PAIR = false), or a cluster of two CTAs per 256 x 128 tile
+// (PAIR = true: CTA rank r owns rows 128 r .. 128 r + 127 of the tile and half of the B tile; the
+// leader, rank 0, issues the MMAs for both; every CTA runs its own producer and epilogue).
+template <int KP, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const SplitArgs p) {
+  using R = Ring<PAIR>;
+  constexpr int STAGES = R::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
-  uint8_t* sB = smem + SLOTS * TILE_BYTES;
-  uint64_t* full = (uint64_t*)(sB + SLOTS * TILE_BYTES);
+  uint8_t* sB = smem + R::SLOTS * R::A_BYTES;
+  uint64_t* full = (uint64_t*)(smem + R::BAR_OFFSET);
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;
   uint64_t* acc_empty = acc_full + 2;
-  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  int* ecol_s = (int*)(smem + 2 * SLOTS * TILE_BYTES + 256);   // [2][TN]
-  int16_t* ref_s = (int16_t*)(smem + REF_OFFSET);                // [TN][TM], column-major
+  int* ecol_s = (int*)(smem + R::ECOL_OFFSET);    // [2][TN]
+  int16_t* ref_s = (int16_t*)(smem + R::REF_OFFSET);  // [TN][TM], column-major
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
   const int tiles_n = (p.N + TN - 1) / TN, tiles_m = (p.M + TM - 1) / TM;
-  const int ks_idx = (int)(blockIdx.x % (unsigned)p.ksplit);
-  const int tile = (int)(blockIdx.x / (unsigned)p.ksplit);
+  unsigned unit = PAIR ? blockIdx.x / 2 : blockIdx.x;  // the CTA pair (or CTA) index
+  // a stacked batch: the graph of this CTA, and its share of the launch
+  int gb = 0;
+  if (p.nbatch > 1) {
+    const unsigned per_graph = (unsigned)(PAIR ? tiles_m / 2 : tiles_m) * (unsigned)tiles_n * (unsigned)p.ksplit;
+    gb = (int)(unit / per_graph);
+    unit %= per_graph;
+  }
+  const rd_batch_graph* bgr = p.nbatch > 1 ? p.bg + gb : nullptr;
+  const int* eA = p.eA + (long long)gb * p.ea_gs;
+  const int* eB = p.eB + (long long)gb * p.eb_gs;
+  const int a_plane0 = gb * p.s_max, b_plane0 = gb * p.s_max;  // first digit plane of this graph
+  const int ks_idx = (int)(unit % (unsigned)p.ksplit);
+  const int tile = (int)(unit / (unsigned)p.ksplit);
   // Longest tiles first (the block scheduler starts CTAs in index order, so the last wave then
   // holds the short ones): with a triangular operand the K range of a tile depends on its row or
   // column (see kbeg / kend below).
-  int tr = tile / tiles_n, tc = tile % tiles_n;
-  if (p.a_tri == RD_TRI_UPPER && p.b_tri == RD_TRI_LOWER_UNIT && tiles_m == tiles_n) {
-    // K from max(row, col) on: shells of equal max(tr, tc), the outermost (shortest) last
-    const int sh = (int)sqrtf((float)tile);
-    const int shell = (sh + 1) * (sh + 1) <= tile ? sh + 1 : (sh * sh > tile ? sh - 1 : sh);
-    const int o = tile - shell * shell;  // 0 .. 2 shell
-    tr = o <= shell ? o : shell;
-    tc = o <= shell ? shell : o - shell - 1;
-  } else if (p.a_tri == RD_TRI_FULL && p.b_tri != RD_TRI_FULL) {
-    // K depends on the tile column alone: column-major, so that a wave takes whole columns
-    tr = tile % tiles_m;
-    tc = tile / tiles_m;
-    if (p.b_tri == RD_TRI_UPPER) tc = tiles_n - 1 - tc;  // K up to the column's end: the last columns first
-  } else if (p.a_tri == RD_TRI_LOWER_UNIT) {
-    tr = tiles_m - 1 - tr;  // K up to the tile row's end
+  int m0, n0;  // the tile (of the pair: 256 rows) and this CTA's first row
+  constexpr int ROWS = PAIR ? 2 * TM : TM;
+  if (PAIR) {
+    int P, J;
+    pair_tile(tile, p.ma_pad / ROWS, p.nb_pad / TN, p.a_tri, p.b_tri, P, J);
+    m0 = P * ROWS;
+    n0 = J * TN;
+  } else {
+    int tr = tile / tiles_n, tc = tile % tiles_n;
+    if (p.a_tri == RD_TRI_UPPER && p.b_tri == RD_TRI_LOWER_UNIT && tiles_m == tiles_n) {
+      // K from max(row, col) on: shells of equal max(tr, tc), the outermost (shortest) last
+      const int sh = (int)sqrtf((float)tile);
+      const int shell = (sh + 1) * (sh + 1) <= tile ? sh + 1 : (sh * sh > tile ? sh - 1 : sh);
+      const int o = tile - shell * shell;  // 0 .. 2 shell
+      tr = o <= shell ? o : shell;
+      tc = o <= shell ? shell : o - shell - 1;
+    } else if (p.a_tri == RD_TRI_FULL && p.b_tri != RD_TRI_FULL) {
+      // K depends on the tile column alone: column-major, so that a wave takes whole columns
+      tr = tile % tiles_m;
+      tc = tile / tiles_m;
+      if (p.b_tri == RD_TRI_UPPER) tc = tiles_n - 1 - tc;  // K up to the column's end: the last columns first
+    } else if (p.a_tri == RD_TRI_LOWER_UNIT) {
+      tr = tiles_m - 1 - tr;  // K up to the tile row's end
+    }
+    m0 = tr * TM;
+    n0 = tc * TN;
   }
-  const int m0 = tr * TM;
-  const int n0 = tc * TN;
+  const int m_cta = m0 + (int)rank * TM;  // this CTA's rows of A and of the output
+  // K range of the tile (of both CTAs of a pair: the union of their rows' ranges; the extra K steps
+  // of one CTA's rows meet zeros of its triangular operand and add exact zeros)
   int kbeg = 0, kend = p.K;
-  if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, m0 + TM);
+  if (p.a_tri == RD_TRI_LOWER_UNIT) kend = min(kend, m0 + ROWS);
   if (p.a_tri == RD_TRI_UPPER) kbeg = max(kbeg, m0);
   if (p.b_tri == RD_TRI_LOWER_UNIT) kbeg = max(kbeg, n0);
   if (p.b_tri == RD_TRI_UPPER) kend = min(kend, n0 + TN);
@@ -475,7 +686,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   const int cbeg = kbeg / KP;
   const int nchunks = (kbeg < kend) ? (kend + KP - 1) / KP - cbeg : 0;
-  const int s = p.s;
+  const int s = bgr ? bgr->s : p.s;  // (0: a graph of the batch that is not on the split path)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
@@ -484,54 +695,72 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], EPI_WARPS);
+      mbar_init(&acc_empty[i], PAIR ? 2 * EPI_WARPS : EPI_WARPS);  // (a pair: both CTAs' epilogues)
     }
+    mbar_init(drain, 1);
     // a CTA that timed out earlier leaves its mark in the status word: skip the work
     *abort_flag = (p.status && *(volatile int*)p.status == RD_DEV_TIMEOUT) ? 1 : 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  if (warp == 1) {  // both CTAs of a pair allocate (the same columns of each CTA's tensor memory)
+    if (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // the peer's barriers are initialised before any remote arrive
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const unsigned long long deadline = globaltimer() + WAIT_NS;
   const int nloop = *abort_flag ? 0 : nchunks;
 
   if (warp == 0) {
-    if (lane == 0) {  // TMA producer
+    if (lane == 0) {  // TMA producer (in each CTA of a pair: its own A rows and half of B)
       int it = 0;
       bool ok = true;
       for (int c = 0; c < nloop && ok; ++c) {
         const int kc0 = max(kbeg, (cbeg + c) * KP);
         const int ksteps = (min(kend, (cbeg + c + 1) * KP) - kc0) / TK;
         for (int g = 0; g < s && ok; ++g) {
-          // the group's items (pair pa, K step ks) in order, ITEMS to a stage
+          // the group's items (pair pa, K step ks) in order, R::ITEMS to a stage
           const int items = (g + 1) * ksteps;
-          for (int i0 = 0; i0 < items; i0 += ITEMS, ++it) {
+          for (int i0 = 0; i0 < items; i0 += R::ITEMS, ++it) {
             const int st = it % STAGES;
             const uint32_t round = (uint32_t)(it / STAGES);
-            if (!mbar_wait(&empty[st], (round + 1) & 1u, abort_flag, deadline)) {
+            if (!mbar_wait<false, PAIR>(&empty[st], (round + 1) & 1u, abort_flag, deadline)) {
               ok = false;
               break;
             }
-            const int cnt = min(ITEMS, items - i0);
-            mbar_arrive_expect_tx(&full[st], cnt * 2 * TILE_BYTES);
+            const int cnt = min(R::ITEMS, items - i0);
+            // the leader's barrier counts the bytes of both CTAs (a peer's copies may land first:
+            // the transaction count goes negative until the leader's expect)
+            if (leader) mbar_arrive_expect_tx(&full[st], cnt * (PAIR ? 2 : 1) * (R::A_BYTES + R::B_BYTES));
             for (int u = 0; u < cnt; ++u) {
-              const int pa = (i0 + u) / ksteps, ks = (i0 + u) % ksteps, slot = st * ITEMS + u;
-              tma_load_2d(sA + slot * TILE_BYTES, &tmA, &full[st], kc0 + ks * TK, pa * p.ma_pad + m0);
-              tma_load_2d(sB + slot * TILE_BYTES, &tmB, &full[st], kc0 + ks * TK, (g - pa) * p.nb_pad + n0);
+              const int pa = (i0 + u) / ksteps, ks = (i0 + u) % ksteps, slot = st * R::ITEMS + u;
+              const int ka = kc0 + ks * TK;
+              if (PAIR) {
+                const uint32_t bar = mapa_shared(&full[st], 0);
+                tma_load_2d_pair(sA + slot * R::A_BYTES, &tmA, bar, ka, (a_plane0 + pa) * p.ma_pad + m_cta);
+                tma_load_2d_pair(sB + slot * R::B_BYTES, &tmB, bar, ka,
+                                 (b_plane0 + g - pa) * p.nb_pad + n0 + (int)rank * (TN / 2));
+              } else {
+                tma_load_2d(sA + slot * R::A_BYTES, &tmA, &full[st], ka, (a_plane0 + pa) * p.ma_pad + m0);
+                tma_load_2d(sB + slot * R::B_BYTES, &tmB, &full[st], ka, (b_plane0 + g - pa) * p.nb_pad + n0);
+              }
             }
           }
         }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {  // MMA issuer
+    if (lane == 0 && leader) {  // MMA issuer (a pair's leader issues for both CTAs)
       int it = 0, gi = 0;
       bool ok = true;
       for (int c = 0; c < nloop && ok; ++c) {
@@ -540,7 +769,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int g = 0; g < s && ok; ++g, ++gi) {
           const int buf = gi & 1;
           const uint32_t use = (uint32_t)(gi >> 1);
-          if (!mbar_wait<true>(&acc_empty[buf], (use + 1) & 1u, abort_flag, deadline)) {
+          if (!mbar_wait<true, PAIR>(&acc_empty[buf], (use + 1) & 1u, abort_flag, deadline)) {
             ok = false;
             break;
           }
@@ -548,36 +777,40 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t dt = tmem + (uint32_t)(buf * TN);
           uint32_t acc = 0;
           const int items = (g + 1) * ksteps;
-          for (int i0 = 0; i0 < items; i0 += ITEMS, ++it) {
+          for (int i0 = 0; i0 < items; i0 += R::ITEMS, ++it) {
             const int st = it % STAGES;
             const uint32_t round = (uint32_t)(it / STAGES);
-            if (!mbar_wait<true>(&full[st], round & 1u, abort_flag, deadline)) {
+            if (!mbar_wait<true, PAIR>(&full[st], round & 1u, abort_flag, deadline)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const int cnt = min(ITEMS, items - i0);
+            const int cnt = min(R::ITEMS, items - i0);
             for (int u = 0; u < cnt; ++u) {
-              const uint32_t a_addr = smem_u32(sA + (st * ITEMS + u) * TILE_BYTES);
-              const uint32_t b_addr = smem_u32(sB + (st * ITEMS + u) * TILE_BYTES);
+              const uint32_t a_addr = smem_u32(sA + (st * R::ITEMS + u) * R::A_BYTES);
+              const uint32_t b_addr = smem_u32(sB + (st * R::ITEMS + u) * R::B_BYTES);
 #pragma unroll
               for (int k16 = 0; k16 < TK / 16; ++k16) {
-                umma_bf16(dt, sdesc_sw128(a_addr + k16 * 32), sdesc_sw128(b_addr + k16 * 32), acc);
+                umma_bf16<PAIR>(dt, sdesc_sw128(a_addr + k16 * 32), sdesc_sw128(b_addr + k16 * 32), acc);
                 acc = 1;
               }
             }
-            umma_commit(&empty[st]);
+            umma_commit<PAIR>(&empty[st]);  // (a pair: both CTAs' stage barriers)
           }
-          if (ok) umma_commit(&acc_full[buf]);
+          if (ok) umma_commit<PAIR>(&acc_full[buf]);
         }
       }
+      // every MMA issued has completed before the tensor memory can be freed (bounded: a second)
+      umma_commit<PAIR>(drain, 1);
+      volatile int no_abort = 0;
+      mbar_wait<false, false>(drain, 0, &no_abort, globaltimer() + 1000000000ull);
     }
   } else {  // epilogue warps 2..9
     const int ew = warp - 2;
     const int quarter = warp & 3;      // tensor-memory lane quarter this warp may access
     const int half = ew >> 2;          // column half of the tile
     const int lrow = quarter * 32 + lane;
-    const int row = m0 + lrow;
+    const int row = m_cta + lrow;
     // float-float accumulators: high words in registers, low words in tensor memory, both relative
     // to a per-entry reference exponent (shared memory, int16) that follows the largest chunk scale
     // eA[c][row] + eB[c][col] met so far.  When a chunk's scale exceeds it, the accumulator is
@@ -612,11 +845,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int cb = c & 1;
       if (ew < 4) {
         const int t = ew * 32 + lane;  // 0..127: one column each
-        ecol_s[cb * TN + t] = p.eB[(long long)kc * p.nb_pad + n0 + t];
+        ecol_s[cb * TN + t] = eB[(long long)kc * p.nb_pad + n0 + t];
       }
       asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
       if (!ok) continue;
-      const int erow = p.eA[(long long)kc * p.ma_pad + row];
+      const int erow = eA[(long long)kc * p.ma_pad + row];
       // renormalise the previous chunk's sums, rebase where this chunk's scale exceeds the
       // reference, and set this chunk's per-entry scale
 #pragma unroll
@@ -655,7 +888,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int buf = gi & 1;
         const uint32_t use = (uint32_t)(gi >> 1);
         // warp-uniform outcome: the tensor-memory loads below are warp-wide
-        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], use & 1u, abort_flag, deadline))) {
+        if (!__all_sync(0xffffffffu, mbar_wait<false, PAIR>(&acc_full[buf], use & 1u, abort_flag, deadline))) {
           ok = false;
           break;
         }
@@ -673,7 +906,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (t == 7) {  // all reads of the accumulator done: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            if (lane == 0) {
+              if (PAIR)
+                mbar_arrive_cluster(mapa_shared(&acc_empty[buf], 0));  // the leader's MMA thread
+              else
+                mbar_arrive(&acc_empty[buf]);
+            }
           }
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
@@ -692,7 +930,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     // final values, 16 columns at a time (the tensor-memory loads are warp-wide: outside any
     // per-lane condition)
-    const bool store = ok && !*abort_flag;
+    const bool store = ok && !*abort_flag && s > 0;
+    // this graph's stores (a stacked batch: its own C, D, bounds, gain and status)
+    double* Cg = p.C ? p.C + (long long)gb * p.c_gs : nullptr;
+    int32_t* Dg = (p.D && bgr) ? p.D + bgr->off : p.D;
+    const long long ldd = bgr ? bgr->n : p.ldd;
+    const int c_rows = bgr ? min(p.c_rows, bgr->n) : p.c_rows, c_cols = bgr ? min(p.c_cols, bgr->n) : p.c_cols;
+    const int d_rows = bgr ? bgr->n : p.d_rows, d_cols = bgr ? bgr->n : p.d_cols;
+    const double log_gamma = bgr ? bgr->log_gamma : p.log_gamma;
+    const float inv_log2_gamma = bgr ? bgr->inv_log2_gamma : p.inv_log2_gamma;
+    int* status_g = bgr ? const_cast<int*>(bgr->status) : p.status;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       uint32_t lr[8];
@@ -712,30 +959,38 @@ __global__ void __launch_bounds__(THREADS, 1)
         v = p.alpha * v;
         const long long orow = p.row_map ? p.row_map[row] : row;
         const long long ocol = p.col_map ? p.col_map[col] : col;
-        if (p.C && row < p.c_rows && col < p.c_cols) {
-          double* cp = p.C + orow * p.ldc + ocol;
+        if (Cg && row < c_rows && col < c_cols) {
+          double* cp = Cg + orow * p.ldc + ocol;
           if (p.beta != 0.0) v = fma(p.beta, *cp, v);
           if (p.store_c) *cp = v;
         }
-        if (p.D && row < p.d_rows && col < p.d_cols) {
+        if (Dg && row < d_rows && col < d_cols) {
           int32_t d;
           if (!isfinite(v)) {
-            rd_set_status(p.status, RD_DEV_NONFINITE, (int)orow);
+            rd_set_status(status_g, RD_DEV_NONFINITE, (int)orow);
             d = RD_UNREACHABLE;
           } else {
-            d = (row == col) ? 0 : rd_decode_entry_fast(v, p.inv_log2_gamma, p.log_gamma, p.tau);
+            d = (row == col) ? 0 : rd_decode_entry_fast(v, inv_log2_gamma, log_gamma, p.tau);
           }
-          p.D[orow * p.ldd + ocol] = d;
+          Dg[orow * ldd + ocol] = d;
         }
       }
     }
   }
+  tc_fence_before();
   __syncthreads();
+  // a pair: neither CTA frees its tensor memory or leaves while the other's work (the leader's
+  // MMAs into both, the peer's arrivals on the leader's barriers) may still touch it; every loop
+  // above ends (bounded waits), so both CTAs arrive here
+  if (PAIR) cluster_sync();
   if (*abort_flag && threadIdx.x == 0) rd_set_status(p.status, RD_DEV_TIMEOUT, blockIdx.x);
   // (the status word is only read at the start of a CTA: a stale value merely skips work)
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    if (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
 }
 
@@ -802,13 +1057,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D map over digit planes: inner dim k_pad (contiguous), outer dim s * rows_pad
-cudaError_t make_map(CUtensorMap* m, const void* base, int k_pad, long long rows) {
+// 2D map over digit planes: inner dim k_pad (contiguous), outer dim s * rows_pad; boxes of TK x box_rows
+cudaError_t make_map(CUtensorMap* m, const void* base, int k_pad, long long rows, int box_rows = TM) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
-  cuuint32_t box[2] = {TK, TM};
+  cuuint32_t box[2] = {TK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -843,9 +1098,22 @@ struct rd_split_plan {
   int* eA = nullptr;
   int* eB = nullptr;
   int64_t bytes = 0;
+  bool borrowed = false;  // digA, digB, eA, eB belong to a batch (rd_split_prepare_borrowed)
 };
 
 namespace {
+
+// the batch part of a slicing launch: per-graph strides of the operand and of the exponents
+// (exponent arrays hold k_pad / kappa chunks of rows_pad entries per graph)
+SliceBatch slice_batch(const rd_ctx* h, const void* x, int rows_pad, int k_pad) {
+  SliceBatch sb{};
+  if (h->nbatch > 1) {
+    sb.bg = h->dBatch;
+    sb.x_gs = rd_batch_stride(h, x);
+    sb.e_gs = (long long)(k_pad / h->kappa) * rows_pad;
+  }
+  return sb;
+}
 
 // Slice the A operand (rows x k) into digA/eA (chunks of h->kappa along k).
 cudaError_t slice_a(rd_ctx* h, const View& v, int rows_pad, int k_pad, cudaStream_t st) {
@@ -854,12 +1122,14 @@ cudaError_t slice_a(rd_ctx* h, const View& v, int rows_pad, int k_pad, cudaStrea
   if (e != cudaSuccess) return e;
   const long long warps = (long long)rows_pad * (k_pad / h->kappa);
   const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+  const SliceBatch sb = slice_batch(h, v.p, rows_pad, k_pad);
+  const dim3 grid(blocks, h->nbatch > 1 ? h->nbatch : 1);
   if (h->kappa == KAPPA_NARROW)
-    slice_rows_kernel<KAPPA_NARROW><<<blocks, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, rows_pad, k_pad, P->s,
-                                                            P->digA, P->eA, h->dStatus);
+    slice_rows_kernel<KAPPA_NARROW><<<grid, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, rows_pad, k_pad, P->s,
+                                                          P->digA, P->eA, h->dStatus, sb);
   else
-    slice_rows_kernel<KAPPA_WIDE><<<blocks, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, rows_pad, k_pad, P->s,
-                                                          P->digA, P->eA, h->dStatus);
+    slice_rows_kernel<KAPPA_WIDE><<<grid, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, rows_pad, k_pad, P->s,
+                                                        P->digA, P->eA, h->dStatus, sb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, st, RD_PROF_NONE, 0.0);
 }
@@ -903,28 +1173,45 @@ cudaError_t slice_b(rd_ctx* h, const View& v, int cols_pad, int k_pad, cudaStrea
   P->b_gen = h->factor_gen;
   cudaError_t e = rd_prof_begin(h, st, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
-  const dim3 grid(cols_pad / 16, k_pad / h->kappa);
+  const dim3 grid(cols_pad / 16, k_pad / h->kappa, h->nbatch > 1 ? h->nbatch : 1);
+  const SliceBatch sb = slice_batch(h, v.p, cols_pad, k_pad);
   if (h->kappa == KAPPA_NARROW)
     slice_cols_kernel<KAPPA_NARROW><<<grid, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, cols_pad, k_pad, P->s,
-                                                          P->digB, P->eB, h->dStatus);
+                                                          P->digB, P->eB, h->dStatus, sb);
   else
     slice_cols_kernel<KAPPA_WIDE><<<grid, 256, 0, st>>>(v.p, v.ld, v.tri, v.rows, v.cols, cols_pad, k_pad, P->s,
-                                                        P->digB, P->eB, h->dStatus);
+                                                        P->digB, P->eB, h->dStatus, sb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, st, RD_PROF_NONE, 0.0);
 }
 
-template <int KP>
-cudaError_t launch_split(const CUtensorMap& ta, const CUtensorMap& tb, const SplitArgs& a, int tiles, cudaStream_t st) {
+// ctas: one per 128 x 128 tile (times ksplit); a pair kernel runs them as clusters of two
+template <int KP, bool PAIR>
+cudaError_t launch_split(const CUtensorMap& ta, const CUtensorMap& tb, const SplitArgs& a, int ctas, cudaStream_t st) {
   static bool attr = false;
+  const int smem = (int)Ring<PAIR>::SMEM;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<KP, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  split_gemm_kernel<KP><<<tiles, THREADS, SMEM_BYTES, st>>>(ta, tb, a);
-  return cudaGetLastError();
+  if (!PAIR) {
+    split_gemm_kernel<KP, false><<<ctas, THREADS, smem, st>>>(ta, tb, a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas, 1, 1);
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, split_gemm_kernel<KP, true>, ta, tb, a);
 }
 
 // C (c_rows x c_cols, ldc) = alpha * A (M x K) * B (K x N) + beta * C; with D != nullptr the product is
@@ -942,9 +1229,13 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   cudaError_t e;
   if ((e = slice_a(h, A, ma_pad, k_pad, st)) != cudaSuccess) return e;
   if ((e = slice_b(h, B, nb_pad, k_pad, st, b_is_final_linv)) != cudaSuccess) return e;
+  // CTA pairs (256 x 128 per cluster of two, half of each B tile per CTA) with 256-wide chunks when
+  // the rows fill whole pairs, unless the handle asks for single CTAs
+  const bool pair = h->split_pairs && h->kappa == KAPPA_WIDE && ma_pad % (2 * TM) == 0;
+  const int nb = h->nbatch > 1 ? h->nbatch : 1;  // a stacked batch: the digit planes of every graph
   CUtensorMap ta, tb;
-  if ((e = make_map(&ta, P->digA, k_pad, (long long)P->s * ma_pad)) != cudaSuccess) return e;
-  if ((e = make_map(&tb, P->digB, k_pad, (long long)P->s * nb_pad)) != cudaSuccess) return e;
+  if ((e = make_map(&ta, P->digA, k_pad, (long long)nb * P->s * ma_pad)) != cudaSuccess) return e;
+  if ((e = make_map(&tb, P->digB, k_pad, (long long)nb * P->s * nb_pad, pair ? TN / 2 : TN)) != cudaSuccess) return e;
   SplitArgs a{};
   a.eA = P->eA;
   a.eB = P->eB;
@@ -959,7 +1250,7 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   a.alpha = alpha;
   a.beta = beta;
   a.C = D ? Ystore : C;
-  a.ldc = D ? h->n : ldc;
+  a.ldc = D ? (nb > 1 ? h->N : h->n) : ldc;  // (a stacked batch keeps Y in its N x N matrices)
   a.store_c = (a.C != nullptr);
   a.c_rows = D ? h->n : c_rows;
   a.c_cols = D ? h->n : c_cols;
@@ -973,13 +1264,19 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
   a.status = h->dStatus;
   a.row_map = row_map;
   a.col_map = col_map;
+  a.nbatch = nb;
+  a.bg = nb > 1 ? h->dBatch : nullptr;
+  a.s_max = P->s;
+  a.ea_gs = (long long)(k_pad / h->kappa) * ma_pad;
+  a.eb_gs = (long long)(k_pad / h->kappa) * nb_pad;
+  a.c_gs = rd_batch_stride(h, a.C);
   const int tiles = (ma_pad / TM) * (nb_pad / TN);
   // split K when the tiles leave SMs idle (products of a few tiles: the goal and self-check rows,
   // the middle of the recursion), up to two CTAs per SM and 8 per tile, at least one K step
   // (64) each; not with the fused decode
   int ksplit = 1;
   const int ksteps = K / TK, sms = num_sms();
-  if (!D && a.store_c && tiles < sms) {
+  if (!D && a.store_c && tiles < sms && nb == 1) {  // (a batch has tiles enough)
     ksplit = (2 * sms) / tiles;
     if (ksplit > 8) ksplit = 8;
     if (ksplit > ksteps) ksplit = ksteps;
@@ -1005,10 +1302,15 @@ cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, in
     a.partial = P->part;
   }
   if ((e = rd_prof_begin(h, st, RD_PROF_SPLIT)) != cudaSuccess) return e;
-  e = (h->kappa == KAPPA_NARROW) ? launch_split<KAPPA_NARROW>(ta, tb, a, tiles * ksplit, st)
-                                 : launch_split<KAPPA_WIDE>(ta, tb, a, tiles * ksplit, st);
+  const int ctas = tiles * ksplit * nb;
+  if (pair)
+    e = (h->kappa == KAPPA_NARROW) ? launch_split<KAPPA_NARROW, true>(ta, tb, a, ctas, st)
+                                   : launch_split<KAPPA_WIDE, true>(ta, tb, a, ctas, st);
+  else
+    e = (h->kappa == KAPPA_NARROW) ? launch_split<KAPPA_NARROW, false>(ta, tb, a, ctas, st)
+                                   : launch_split<KAPPA_WIDE, false>(ta, tb, a, ctas, st);
   if (e != cudaSuccess) return e;
-  if ((e = rd_prof_end(h, st, RD_PROF_SPLIT, flops * (double)P->s * (P->s + 1) / 2.0)) != cudaSuccess) return e;
+  if ((e = rd_prof_end(h, st, RD_PROF_SPLIT, flops * nb * (double)P->s * (P->s + 1) / 2.0)) != cudaSuccess) return e;
   if (ksplit > 1) {
     if ((e = rd_prof_begin(h, st, RD_PROF_NONE)) != cudaSuccess) return e;
     const long long total = (long long)a.c_rows * a.c_cols;
@@ -1028,7 +1330,7 @@ inline View tri(const double* p, long long ld, int n, int mode) { return View{p,
 // 4 tiles of 128 x 128, too few for the tensor cores even with split K, while an FP64 product on
 // 16 x 16 tiles spreads over every SM.  At n = 8192 the 512^3 products of the 1024-row nodes took
 // 167 us each in FP64; with split K over 64-wide K steps they fill the SMs on the tensor cores.
-constexpr int FP64_NODE = 512;
+// (rd_ctx::fp64_node; 512 for one graph, smaller for a stacked batch, whose products have tiles enough)
 
 rd_gemm_f64_args f64_args(const View& A, const View& B, int M, int N, int K, double alpha, double beta, double* C,
                           long long ldc) {
@@ -1079,7 +1381,7 @@ cudaError_t product(rd_ctx* h, bool fp64, const View& A, const View& B, int M, i
 cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
   const int m = hi - lo;
   if (m <= LEAF) return rd_lu_diag(h, lo, st);
-  const bool f64 = m <= FP64_NODE;
+  const bool f64 = m <= h->fp64_node;
   const int mid = lo + ((m / 2 + LEAF - 1) / LEAF) * LEAF;
   const int m1 = mid - lo, m2 = hi - mid;
   const long long N = h->N;
@@ -1189,9 +1491,10 @@ rd_status rd_split_prepare(rd_ctx* h, int s) {
     h->split = P;
     P->N = h->N;
     P->cap_s = s;  // digit planes sized for this count; a later escalation reallocates
-    const size_t NK = (size_t)h->N * ((size_t)h->N + KAPPA_WIDE);  // rows x K padded to whole chunks
+    // rows x K padded to whole chunks, for each graph of a stacked batch
+    const size_t NK = (size_t)(h->nbatch > 1 ? h->nbatch : 1) * h->N * ((size_t)h->N + KAPPA_WIDE);
     const size_t dig = (size_t)s * NK * sizeof(__nv_bfloat16);
-    const size_t ex = (NK / KAPPA_NARROW + 64) * sizeof(int);  // exponents of the narrowest chunks
+    const size_t ex = (NK / KAPPA_NARROW + 64) * sizeof(int);  // exponents of the narrowest chunks (every graph)
     cudaError_t e = cudaSuccess;
     auto get = [&](void** ptr, size_t bytes) {
       if (e == cudaSuccess) e = rd_dev_alloc(h, ptr, bytes);
@@ -1213,9 +1516,36 @@ rd_status rd_split_prepare(rd_ctx* h, int s) {
   return RD_OK;
 }
 
+void rd_split_workspace(int N, int nbatch, int s, size_t* dig_bytes, size_t* exp_bytes) {
+  const size_t NK = (size_t)(nbatch > 1 ? nbatch : 1) * N * ((size_t)N + KAPPA_WIDE);
+  *dig_bytes = (size_t)s * NK * sizeof(__nv_bfloat16);
+  *exp_bytes = (NK / KAPPA_NARROW + 64) * sizeof(int);
+}
+
+rd_status rd_split_prepare_borrowed(rd_ctx* h, int s, void* digA, void* digB, int* eA, int* eB) {
+  if (s < 2 || s > MAX_SLICES_WIDE) return RD_ERR_ARG;
+  if (!encode_fn()) {
+    h->err = "cuTensorMapEncodeTiled is not available from the driver";
+    return RD_ERR_UNSUPPORTED;
+  }
+  rd_split_release(h);
+  rd_split_plan* P = new rd_split_plan();
+  P->N = h->N;
+  P->s = P->cap_s = s;
+  P->borrowed = true;
+  P->digA = static_cast<__nv_bfloat16*>(digA);
+  P->digB = static_cast<__nv_bfloat16*>(digB);
+  P->eA = eA;
+  P->eB = eB;
+  h->split = P;
+  h->slices = s;
+  return RD_OK;
+}
+
 void rd_split_release(rd_ctx* h) {
   rd_split_plan* P = h->split;
   if (!P) return;
+  if (P->borrowed) P->digA = P->digB = nullptr, P->eA = P->eB = nullptr;
   void* ptrs[] = {P->digA, P->digB, P->eA, P->eB, P->part};
   for (void* q : ptrs)
     if (q) rd_dev_free(h, q);

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -211,6 +212,10 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
     return fail_cuda(nullptr, e, "cudaGetDevice");
   }
   h->device = dev;
+  {
+    const char* pairs = getenv("RD_SPLIT_CTA_PAIRS");
+    h->split_pairs = (pairs && pairs[0] == '0') ? 0 : 1;
+  }
   h->pool = pool;
   h->stream = stream;
   h->n = n;

@@ -54,6 +54,21 @@
 
 struct rd_split_plan;       // defined by the split path
 
+// One graph of a stacked batch (device array, see rd_ctx::nbatch): the batched split path's
+// per-graph parameters and outcome.
+struct rd_batch_graph {
+  double gamma;          // its gain
+  int32_t n;             // nodes (at most the batch's padded size N)
+  int32_t s;             // digits of its split products; 0: not on the split path (launches skip it)
+  int64_t off;           // element offset of its packed D (n x n, leading dimension n)
+  double log_gamma;      // the decode's log(gamma) and 1 / log2(gamma)
+  float inv_log2_gamma;
+  int32_t status[2];     // RD_DEV_* of this graph and its detail
+  int32_t route;         // 0: split result kept; 1: FP64 (screened out or failed the self-check)
+  double residual;       // largest entrywise relative residual of its split Y (the self-check)
+  double screen_bits;    // its range screen: chunk spread x log2(1 / gamma)
+};
+
 struct rd_ctx {
   int device = 0;
   // device memory: cudaMalloc / cudaFree, or, for handles of a server, its stream-ordered pool
@@ -106,6 +121,15 @@ struct rd_ctx {
   double screen_per_hop = 1.0; // weight factor of a hop in that estimate (largest W; 1 unweighted)
   int ordered = 0;             // the split path runs on P M P^T with the locality order (dOrd)
   int kappa = 256;             // chunk width of the split digits: 256, or 64 with the locality order
+  int split_pairs = 1;         // split GEMM as CTA pairs (tcgen05 cta_group::2) where the rows allow;
+                               // 0: one CTA per tile (environment RD_SPLIT_CTA_PAIRS=0 at rd_create)
+  int fp64_node = 512;         // recursion nodes of at most this many rows run their products in FP64
+  // A stacked batch of nbatch graphs of one padded size N (the batched split path): graph b's
+  // matrices start b * N * N doubles into dLU and dT and b * N * N / 2 into dS, and every launch
+  // of the factorisation covers all of them (the CTA index or blockIdx.y/z picks the graph).
+  // Pointers handed to the launchers are graph 0's; rd_batch_stride maps them to a stride.
+  int nbatch = 1;
+  rd_batch_graph* dBatch = nullptr;  // device, nbatch entries (nbatch > 1)
   int fallbacks = 0;           // split results redone (more digits or FP64) after the self-check
   double last_residual = 0.0;  // largest sampled-row residual of the last split result
 
@@ -134,6 +158,17 @@ struct rd_ctx {
   int8_t prof_kind[kProfPairs] = {};           // RD_PROF_* of each pending event pair
   double prof_pair_flops[kProfPairs] = {};
 };
+
+// Per-graph element stride of a matrix pointer of graph 0 of a stacked batch (0 for one graph):
+// N * N inside dLU or dT, N * N / 2 inside dS.
+inline long long rd_batch_stride(const rd_ctx* h, const void* p) {
+  if (h->nbatch <= 1 || !p) return 0;
+  const long long NN = (long long)h->N * h->N;
+  const double* q = static_cast<const double*>(p);
+  if ((q >= h->dLU && q < h->dLU + NN) || (q >= h->dT && q < h->dT + NN)) return NN;
+  if (q >= h->dS && q < h->dS + NN / 2) return NN / 2;
+  return 0;
+}
 
 // Device memory of a handle (see rd_ctx::pool); frees are stream-ordered for pooled handles.
 cudaError_t rd_dev_alloc(rd_ctx* h, void** p, size_t bytes);
@@ -177,6 +212,8 @@ struct rd_gemm_f64_args {
   // CTA must then own the whole strip it reads, so the 64 x 64 tile is kept and the aliased
   // extent (N when C aliases A, M when C aliases B) must be 64
   int aliased;
+  // stacked batches: per-graph element strides of A, B and C (blockIdx.y is the graph)
+  long long a_gs, b_gs, c_gs;
 };
 
 // flops: algorithmic flop count of the launch (for the profile), computed by the caller
@@ -229,11 +266,29 @@ cudaError_t rd_walk(rd_ctx* h, const int32_t* dnext, int k, const int32_t* dstar
 // ---- split path (k_split.cu) -----------------------------------------------------------------
 rd_status rd_split_prepare(rd_ctx* h, int slices);
 void rd_split_release(rd_ctx* h);
+// digit-plane bytes (each operand) and exponent bytes of a split plan for nbatch graphs of size N
+void rd_split_workspace(int N, int nbatch, int s, size_t* dig_bytes, size_t* exp_bytes);
+// a plan whose digit planes and exponents are caller-owned buffers of rd_split_workspace's sizes
+rd_status rd_split_prepare_borrowed(rd_ctx* h, int s, void* digA, void* digB, int* eA, int* eB);
 cudaError_t rd_lu_split(rd_ctx* h, cudaStream_t s);
 cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s);
 cudaError_t rd_goal_split(rd_ctx* h, const int32_t* dgoals, int k, double* out, cudaStream_t s);
 cudaError_t rd_split_row_check(rd_ctx* h, double* worst, cudaStream_t s);
 #define RD_SPLIT_RESIDUAL 1e-9  // largest accepted entrywise relative residual of the sampled rows
+
+// ---- the batched split path (k_batch_split.cu) ------------------------------------------------
+struct rd_batch_split;
+// Plan the split path for the graphs gid[0..count) of a batch (node counts n[], gains gamma[],
+// packed offsets off[] of every graph of the batch): stacks of at most 512 graphs of one padded
+// size, their workspaces and one shared digit workspace, allocated on the current device.
+rd_status rd_bsplit_create(const int32_t* n, const double* gamma, const int64_t* off, const int32_t* gid,
+                           int count, double tau, rd_batch_split** out, std::string* err);
+// Enqueue a run on stream s: every planned graph's screen, factorisation, product with the decode
+// into D, and self-check; done[g] = 1 (device) for graphs whose split result is kept (their
+// status[g] set), 0 for graphs the FP64 kernel must redo; routes[g] (device) records why.
+cudaError_t rd_bsplit_run(rd_batch_split* b, const uint8_t* A, int32_t* D, int32_t* status, int32_t* done,
+                          int32_t* routes, cudaStream_t s, int64_t* launches);
+void rd_bsplit_destroy(rd_batch_split* b);
 
 // ---- errors of calls without a handle (read back through rd_last_error(NULL)) -----------------
 void rd_record_error(const std::string& msg);

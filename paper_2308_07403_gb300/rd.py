@@ -32,6 +32,7 @@ RD_UNREACHABLE = 2**31 - 1
 MAX_GOALS = 64
 NOALLOC_MAX_N = 512
 BATCH_MAX_N = 512
+BATCH_CLASSES = 4
 
 # every symbol declared in include/rd.h, with its ctypes signature
 _P = ctypes.c_void_p
@@ -60,6 +61,9 @@ _SIGS = {
     "rd_batch_apsp": (ctypes.c_int, [_P, _P, _P, _P]),
     "rd_batch_status": (ctypes.c_int, [_P, _P]),
     "rd_batch_destroy": (None, [_P]),
+    "rd_batch_set_precision": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "rd_batch_routes": (ctypes.c_int, [_P, _P]),
+    "rd_batch_tuning": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "rd_serve_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_P)]),
     "rd_serve_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
     "rd_serve_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
@@ -382,6 +386,26 @@ class Batch:
         st = np.empty(self.G, dtype=np.int32)
         _check(load().rd_batch_status(self.h, st.ctypes.data_as(_P)))
         return st
+
+    def set_precision(self, mode, autotune=True):
+        _check(load().rd_batch_set_precision(self.h, int(mode), 1 if autotune else 0))
+
+    def routes(self):
+        """Per graph: 0 FP64 kernel, 1 split, 2 split redone in FP64, 3 screened to FP64, 4 gain failed."""
+        r = np.empty(self.G, dtype=np.int32)
+        _check(load().rd_batch_routes(self.h, r.ctypes.data_as(_P)))
+        return r
+
+    def tuning(self):
+        """Per size class (n in (128 c, 128 (c + 1)]): graphs, on the split path, ms per graph of both variants."""
+        g = np.empty(BATCH_CLASSES, np.int32)
+        sp = np.empty(BATCH_CLASSES, np.int32)
+        mf = np.empty(BATCH_CLASSES)
+        ms = np.empty(BATCH_CLASSES)
+        nl = np.zeros(1, np.int64)
+        _check(load().rd_batch_tuning(self.h, *(x.ctypes.data_as(_P) for x in (g, sp, mf, ms, nl))))
+        return {"graphs": g.tolist(), "split": sp.tolist(), "ms_per_graph_fp64": mf.tolist(),
+                "ms_per_graph_split": ms.tolist(), "launches_last_run": int(nl[0])}
 
     def close(self):
         if self.h:

@@ -82,3 +82,72 @@ def test_batch_rejects_bad_sizes(rd):
         with pytest.raises(rd.RDError) as ei:
             rd.Batch(np.array(ns), np.array([0.1, 0.1]))
         assert ei.value.status == rd.RD_ERR_ARG
+
+
+# ---- the split variant (rd_batch_set_precision) ------------------------------------------------
+
+def run_split(rd, ns, As, gs, autotune, fill=-7, graph_capture=False):
+    """Pack, run in split mode (optionally as a captured CUDA graph, replayed twice), and return
+    offsets, D, status, routes and the tuning record."""
+    with rd.Batch(ns, gs) as b:
+        b.set_precision(rd.RD_PREC_SPLIT_BF16, autotune)
+        off = b.offsets()
+        packed = np.zeros(int(off[-1]), dtype=np.uint8)
+        for g, A in enumerate(As):
+            packed[off[g]:off[g + 1]] = np.ascontiguousarray(A).ravel()
+        A_dev = torch.from_numpy(packed).cuda()
+        D_dev = torch.full((int(off[-1]),), fill, dtype=torch.int32, device="cuda")
+        if graph_capture:
+            s = torch.cuda.Stream()
+            b.apsp(A_dev, D_dev, s.cuda_stream)   # warm-up outside the capture
+            s.synchronize()
+            D_dev.fill_(fill)
+            cg = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(cg, stream=s):
+                b.apsp(A_dev, D_dev, torch.cuda.current_stream().cuda_stream)
+            D_dev.fill_(fill)
+            cg.replay()
+            cg.replay()
+            torch.cuda.synchronize()
+        else:
+            b.apsp(A_dev, D_dev, torch.cuda.current_stream().cuda_stream)
+        st = b.status()
+        routes = b.routes()
+        tune = b.tuning()
+    return off, D_dev.cpu().numpy(), st, routes, tune
+
+
+def test_batch_split_matches_oracle(rd):
+    """Every size class forced onto the split path: D of every graph bit-exact against the oracle,
+    whatever route it took (split kept, redone in FP64 after the residual check, screened to FP64);
+    the gain-breaking graph is refused and its D left untouched; the ER and WS graphs of the larger
+    classes stay on the split path, the wide grid is screened off it."""
+    ns, As, gs, bad = mixed_batch()
+    off, D, st, routes, tune = run_split(rd, ns, As, gs, autotune=False)
+    for g, A in enumerate(As):
+        n = int(ns[g])
+        Dg = D[off[g]:off[g + 1]].reshape(n, n)
+        if g == bad:
+            assert st[g] == rd.RD_ERR_GAMMA and routes[g] == 4
+            assert (Dg == -7).all()
+            continue
+        assert st[g] == rd.RD_OK, (g, n, st[g], routes[g])
+        assert routes[g] in (1, 2, 3), (g, routes[g])
+        assert np.array_equal(Dg, oracle.rdistance(A, float(gs[g]))), (g, n, routes[g])
+    assert (routes == 1).sum() >= len(As) // 2, routes
+    assert tune["split"] == [1 if c else 0 for c in tune["graphs"]]
+
+
+def test_batch_split_autotune_and_graph_capture(rd):
+    """The autotuned split variant captured in a CUDA graph and replayed twice: every graph equals
+    the oracle; the tuning record has a measured time for both variants in every class present."""
+    kinds, ns, As, gs = graphs.workload_batched(48, 200, 512, replica=7)
+    off, D, st, routes, tune = run_split(rd, ns, As, gs, autotune=True, graph_capture=True)
+    assert (st == rd.RD_OK).all()
+    for g, A in enumerate(As):
+        n = int(ns[g])
+        assert np.array_equal(D[off[g]:off[g + 1]].reshape(n, n), oracle.rdistance(A, float(gs[g]))), (g, n)
+    for c, cnt in enumerate(tune["graphs"]):
+        if cnt:
+            assert tune["ms_per_graph_fp64"][c] > 0 and tune["ms_per_graph_split"][c] > 0
+            assert tune["split"][c] == int(tune["ms_per_graph_split"][c] < tune["ms_per_graph_fp64"][c])
