@@ -421,6 +421,8 @@ def run_batched(args):
     per, tot, clk = time_batch(b, A_dev, D_dev, args.steps, args.warmup, dev, local, world, dist)
     st = b.status()
     routes = b.routes()
+    info = b.split_info()
+    launches = b.tuning()["launches_last_run"]
     same_as_fp64 = bool(torch.equal(D_dev.cpu(), D64))
     ms = tot / args.steps
     value = world * len(ns) * args.steps / (tot * 1e-3)
@@ -472,6 +474,8 @@ def run_batched(args):
         "p50_ms": pct(per, 0.5), "p99_ms": pct(per, 0.99), "tflops_2n3": achieved,
         "graphs_ok": int((st == rd.RD_OK).sum()), "graphs": len(ns),
         "routes": rh, "D_identical_to_fp64_variant": same_as_fp64,
+        "split_digits_histogram": {int(d): int(c) for d, c in enumerate(np.bincount(info["digits"])) if c and d},
+        "split_second_pass": int((info["passes"] == 2).sum()),
         "autotuner": dict(tune, seconds=round(t_tune, 2),
                           class_n_range=["(0,128]", "(128,256]", "(256,384]", "(384,512]"]),
         "compare": {"variant": "fp64 Gauss-Jordan, one persistent kernel", "value": world * len(ns) * args.steps /
@@ -482,7 +486,7 @@ def run_batched(args):
                                  "peak_source": f"FP64 pipe: 152 SMs x 4 flop/clk x {sm_mhz:.0f} MHz (unit counts)",
                                  "achieved": achieved64, "peak": peak, "unit": "TFLOP/s",
                                  "frac": achieved64 / peak}},
-        "clocks": clk, "gpu_launches": tune["launches_last_run"],
+        "clocks": clk, "gpu_launches": launches,
         "roofline": {"kernel": "batch_kernel (FP64 variant)", "bound": "alu",
                      "peak_source": f"FP64 pipe: 152 SMs x 4 flop/clk x {sm_mhz:.0f} MHz (unit counts)",
                      "achieved": achieved64, "peak": peak, "unit": "TFLOP/s", "frac": achieved64 / peak,

@@ -315,6 +315,13 @@ rd_status rd_batch_set_precision(rd_batch_handle b, int32_t mode, int32_t autotu
  * 4 failed the gain check (status RD_ERR_GAMMA).  Synchronises the device. */
 rd_status rd_batch_routes(rd_batch_handle b, int32_t* routes);
 
+/* Per graph of the split variant's last run (host arrays of G): the digit count of its kept split
+ * result (0: not kept), the split passes it took (2: redone with more digits after the residual
+ * check), its last residual, and its range-screen estimate in bits (-1: not screened).
+ * Synchronises the device. */
+rd_status rd_batch_split_info(rd_batch_handle b, int32_t* digits, int32_t* passes, double* residual,
+                              double* screen_bits);
+
 /* The autotuner's record per size class (host arrays of RD_BATCH_CLASSES): graphs of the batch in
  * the class, 1 if the class runs on the split path, and the measured device ms per graph of the
  * FP64 and split variants on the probe graphs (0 when not measured); *launches receives the kernel

@@ -554,6 +554,13 @@ rd_status rd_batch_set_precision(rd_batch_handle b, int32_t mode, int32_t autotu
   return rs;
 }
 
+rd_status rd_batch_split_info(rd_batch_handle b, int32_t* digits, int32_t* passes, double* residual,
+                              double* screen_bits) {
+  if (!b || !digits || !passes || !residual || !screen_bits) return RD_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return RD_ERR_CUDA;
+  return rd_bsplit_info(b->split, b->G, digits, passes, residual, screen_bits);
+}
+
 rd_status rd_batch_routes(rd_batch_handle b, int32_t* routes) {
   if (!b || !routes) return RD_ERR_ARG;
   cudaError_t e = cudaDeviceSynchronize();

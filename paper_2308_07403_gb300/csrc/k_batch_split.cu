@@ -10,21 +10,25 @@
 // is a handful of 128 x 128 tiles, too few for the tensor cores alone, but a stack of hundreds
 // fills the GPU.  Every decision is taken on the device, so a run is a fixed sequence of launches
 // that a CUDA graph can capture:
-//   build     M = I - gamma A per graph (Sec. 2), the identity on the padding
 //   screen    per graph: the gain check (Theorem 4's condition, gamma times the largest out-degree
-//             below 1), successor lists in shared memory, BFS from 8 sampled sources, and the
+//             below 1), successor lists in shared memory, BFS from 16 sampled sources, and the
 //             largest hop spread within a 256-node chunk times log2(1/gamma): the digit count is
 //             the fewest (at least 8) whose 7 bits each cover that plus 40 bits of result (the
-//             single-graph range screen); beyond 15 digits, or with too many edges to screen, the
-//             graph leaves the split path
+//             single-graph range screen, with twice its sources: a few hundred nodes make them
+//             cheap); beyond 15 digits, or with too many edges to screen, the graph leaves the
+//             split path
+//   build     M = I - gamma A per graph on the split path (Sec. 2), the identity on the padding
 //   factor    LU and both triangular inverses of every graph (rd_lu_split), then
 //   product   Y = U^-1 L^-1 with D decoded in the epilogue into the caller's packed D; Y is kept
 //             in the stack's LU matrices for the check
 //   check     every entry of M Y - I against (|M| |Y|) entrywise (the componentwise backward
-//             error): a graph above min(1e-9, tau |ln gamma| / 16), at least 1e-12, leaves the
-//             split path (the single-graph self-check's limit)
-//   finalize  a graph that left the split path is redone by the FP64 Gauss-Jordan kernel
-//             (k_batch.cu), which runs after the stacks; the others keep their split D
+//             error), limit min(1e-9, tau |ln gamma| / 16), at least 1e-12 (the single-graph
+//             self-check's)
+//   finalize  a graph within the limit keeps its split D; one above it takes a second pass of
+//             build / factor / product / check with the digits its residual r asks for (about
+//             log2(r / 2^-40) / 7 more, as the single-graph escalation), and one that fails again,
+//             or would need more than 15, is redone by the FP64 Gauss-Jordan kernel (k_batch.cu),
+//             which runs after the stacks.  Every launch skips the graphs without work in its pass.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -40,6 +44,7 @@ constexpr int BS_THREADS = 256;
 constexpr int BS_MAX_N = RD_BATCH_MAX_N;
 constexpr int BS_EDGES = 12288;  // successor entries a screen holds in shared memory
 constexpr int BS_CHUNKS = (BS_MAX_N + RD_SCREEN_CHUNK - 1) / RD_SCREEN_CHUNK;
+constexpr int BS_SRC = 2 * RD_SCREEN_SOURCES;  // BFS sources of the batch screen
 static_assert(BS_MAX_N <= 512, "one screen thread per node");
 
 // a run's per-graph outcome starts clean (n, gamma, off and the decode constants stay)
@@ -51,6 +56,8 @@ __global__ void bs_reset_kernel(rd_batch_graph* bg, int nb) {
   bg[b].route = 0;
   bg[b].residual = 0.0;
   bg[b].screen_bits = -1.0;
+  bg[b].digits = 0;
+  bg[b].passes = 0;
 }
 
 // M = I - gamma A of graph blockIdx.y (n x n bytes at A + off, A_ij != 0 iff edge j -> i) into its
@@ -58,6 +65,7 @@ __global__ void bs_reset_kernel(rd_batch_graph* bg, int nb) {
 __global__ void __launch_bounds__(BS_THREADS) bs_build_kernel(const uint8_t* __restrict__ A, double* __restrict__ LU,
                                                               int N, const rd_batch_graph* __restrict__ bg) {
   const int b = blockIdx.y;
+  if (bg[b].s == 0) return;  // not on the split path in this pass
   const int n = bg[b].n;
   const double g = bg[b].gamma;
   const uint8_t* Ag = A + bg[b].off;
@@ -72,12 +80,12 @@ __global__ void __launch_bounds__(BS_THREADS) bs_build_kernel(const uint8_t* __r
 }
 
 // The gain check and the range screen of graph blockIdx.x (one thread per node; see the file
-// comment).  Sources: nodes q n / 8 + n / 16, as the single-graph screen.
+// comment).  Sources: nodes q n / 16 + n / 32.
 __global__ void __launch_bounds__(BS_MAX_N) bs_screen_kernel(const uint8_t* __restrict__ A, rd_batch_graph* bg) {
   __shared__ int ptr_s[BS_MAX_N + 1];
   __shared__ int16_t succ_s[BS_EDGES];
-  __shared__ int16_t dist_s[RD_SCREEN_SOURCES][BS_MAX_N];
-  __shared__ int lo_s[RD_SCREEN_SOURCES][BS_CHUNKS], hi_s[RD_SCREEN_SOURCES][BS_CHUNKS];
+  __shared__ int16_t dist_s[BS_SRC][BS_MAX_N];
+  __shared__ int lo_s[BS_SRC][BS_CHUNKS], hi_s[BS_SRC][BS_CHUNKS];
   __shared__ int maxdeg_s, total_s, flag_s;
   const int b = blockIdx.x, v = threadIdx.x;
   const int n = bg[b].n;
@@ -111,11 +119,11 @@ __global__ void __launch_bounds__(BS_MAX_N) bs_screen_kernel(const uint8_t* __re
     for (int i = 0; i < n; ++i)
       if (Ag[(long long)i * n + v]) succ_s[w++] = (int16_t)i;
   }
-  for (int q = 0; q < RD_SCREEN_SOURCES; ++q) {
-    const int src = q * n / RD_SCREEN_SOURCES + n / (2 * RD_SCREEN_SOURCES);
+  for (int q = 0; q < BS_SRC; ++q) {
+    const int src = q * n / BS_SRC + n / (2 * BS_SRC);
     if (v < n) dist_s[q][v] = (v == src) ? 0 : -1;
   }
-  if (v < RD_SCREEN_SOURCES * BS_CHUNKS) {
+  if (v < BS_SRC * BS_CHUNKS) {
     lo_s[v / BS_CHUNKS][v % BS_CHUNKS] = 1 << 30;
     hi_s[v / BS_CHUNKS][v % BS_CHUNKS] = -1;
   }
@@ -126,7 +134,7 @@ __global__ void __launch_bounds__(BS_MAX_N) bs_screen_kernel(const uint8_t* __re
     if (v == 0) flag_s = 0;
     __syncthreads();
     if (v < n)
-      for (int q = 0; q < RD_SCREEN_SOURCES; ++q)
+      for (int q = 0; q < BS_SRC; ++q)
         if (dist_s[q][v] == level)
           for (int e = ptr_s[v]; e < ptr_s[v + 1]; ++e) {
             const int u = succ_s[e];
@@ -142,7 +150,7 @@ __global__ void __launch_bounds__(BS_MAX_N) bs_screen_kernel(const uint8_t* __re
   }
   if (v < n) {
     const int c = v / RD_SCREEN_CHUNK;
-    for (int q = 0; q < RD_SCREEN_SOURCES; ++q) {
+    for (int q = 0; q < BS_SRC; ++q) {
       const int d = dist_s[q][v];
       if (d >= 0) {
         atomicMin(&lo_s[q][c], d);
@@ -153,7 +161,7 @@ __global__ void __launch_bounds__(BS_MAX_N) bs_screen_kernel(const uint8_t* __re
   __syncthreads();
   if (v == 0) {
     int spread = 0;
-    for (int q = 0; q < RD_SCREEN_SOURCES; ++q)
+    for (int q = 0; q < BS_SRC; ++q)
       for (int c = 0; c < BS_CHUNKS; ++c)
         if (hi_s[q][c] >= 0) spread = max(spread, hi_s[q][c] - lo_s[q][c]);
     const double bits = spread * log2(1.0 / gamma);
@@ -217,26 +225,46 @@ __global__ void __launch_bounds__(BS_THREADS) bs_residual_kernel(const uint8_t* 
   }
 }
 
-// The outcome of each graph of a stack: kept (route 0 -> done, status RD_OK) when it was screened
-// onto the split path, its Y finite and its residual within the limit; otherwise left for the
-// FP64 kernel (route 1: failed the check, 2: failed the gain check, 3: screened out).
-// routes[gid] (what rd_batch_routes reports): 1 split, 2 split redone in FP64, 3 screened out to
-// FP64, 4 gain check failed.
-__global__ void bs_finalize_kernel(rd_batch_graph* bg, int nb, const int32_t* __restrict__ gids, double tau,
+// The outcome of each graph of a stack after split pass `pass` (1 or 2).  A graph on the split path
+// whose Y is finite and whose residual is within the limit keeps its D (done, status RD_OK, no work
+// in later passes).  One above it takes pass 2 with the digits its residual asks for (at most 15);
+// after pass 2, or beyond 15 digits, it goes to the FP64 kernel (route 1), as do graphs that
+// failed the gain check (2) or were screened out (3).  routes[gid] (what rd_batch_routes reports):
+// 1 split, 2 split redone in FP64, 3 screened out to FP64, 4 gain check failed.
+__global__ void bs_finalize_kernel(rd_batch_graph* bg, int nb, const int32_t* __restrict__ gids, double tau, int pass,
                                    int32_t* status, int32_t* done, int32_t* routes) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
   rd_batch_graph& G = bg[b];
-  int route = G.route;
-  if (route == 0) {
-    const double lim = fmin(RD_SPLIT_RESIDUAL, fmax(tau * fabs(G.log_gamma) / 16.0, 1e-12));
-    if (G.s == 0 || !(G.residual <= lim) || G.status[0] != 0) route = 1;
-  }
-  G.route = route;
+  if (G.digits > 0) return;  // kept in pass 1
   const int gid = gids[b];
-  done[gid] = route == 0 ? 1 : 0;
-  if (route == 0) status[gid] = RD_OK;
-  routes[gid] = route == 0 ? 1 : (route == 1 ? 2 : (route == 3 ? 3 : 4));
+  if (G.route == 0 && G.s > 0) {
+    const double lim = fmin(RD_SPLIT_RESIDUAL, fmax(tau * fabs(G.log_gamma) / 16.0, 1e-12));
+    if (G.residual <= lim && G.status[0] == 0) {
+      done[gid] = 1;
+      status[gid] = RD_OK;
+      routes[gid] = 1;
+      G.digits = G.s;
+      G.passes = pass;
+      G.s = 0;
+      return;
+    }
+    int add = (G.residual <= 1.0 && G.status[0] == 0)
+                  ? (int)ceil((log2(fmax(G.residual, 1e-300)) + RD_SCREEN_RESULT_BITS) / RD_SPLIT_DIGIT_BITS)
+                  : RD_SPLIT_MAX;  // entries lost altogether (or not finite): no digit count will do
+    const int next = G.s + max(1, add);
+    if (pass == 1 && next <= RD_SPLIT_MAX) {  // pass 2 with more digits
+      G.s = next;
+      G.residual = 0.0;
+      G.status[0] = G.status[1] = 0;
+      done[gid] = 0;
+      return;
+    }
+    G.route = 1;
+  }
+  G.s = 0;
+  done[gid] = 0;
+  routes[gid] = G.route == 1 ? 2 : (G.route == 3 ? 3 : 4);
 }
 
 }  // namespace
@@ -366,20 +394,49 @@ cudaError_t rd_bsplit_run(rd_batch_split* b, const uint8_t* A, int32_t* D, int32
     const int64_t l0 = h->launches;
     const int nb = h->nbatch, N = h->N;
     h->stream = s;
-    h->factor_gen++;  // fresh factors: no digits of an earlier run are reused
     bs_reset_kernel<<<(nb + 127) / 128, 128, 0, s>>>(h->dBatch, nb);
     if ((e = cudaMemsetAsync(h->dStatus, 0, 4 * sizeof(int), s)) != cudaSuccess) return e;
-    bs_build_kernel<<<dim3((unsigned)(N / 8), (unsigned)nb), BS_THREADS, 0, s>>>(A, h->dLU, N, h->dBatch);
     bs_screen_kernel<<<nb, BS_MAX_N, 0, s>>>(A, h->dBatch);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = rd_lu_split(h, s)) != cudaSuccess) return e;
-    // Y = U^-1 L^-1 with D decoded into the caller's packed D (graph b at its offset, leading
-    // dimension n_b); Y itself into the stack's LU matrices (free after the factorisation)
-    if ((e = rd_trmm_decode_split(h, D, h->dLU, s)) != cudaSuccess) return e;
-    bs_residual_kernel<<<dim3((unsigned)N, (unsigned)nb), BS_THREADS, 0, s>>>(A, h->dLU, N, h->dBatch);
-    bs_finalize_kernel<<<(nb + 127) / 128, 128, 0, s>>>(h->dBatch, nb, p.d_gids, b->tau, status, done, routes);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *launches += (h->launches - l0) + 5;  // the recursion's and the product's, and the five above
+    for (int pass = 1; pass <= 2; ++pass) {
+      h->factor_gen++;  // fresh factors: no digits of an earlier pass are reused
+      bs_build_kernel<<<dim3((unsigned)(N / 8), (unsigned)nb), BS_THREADS, 0, s>>>(A, h->dLU, N, h->dBatch);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = rd_lu_split(h, s)) != cudaSuccess) return e;
+      // Y = U^-1 L^-1 with D decoded into the caller's packed D (graph b at its offset, leading
+      // dimension n_b); Y itself into the stack's LU matrices (free after the factorisation)
+      if ((e = rd_trmm_decode_split(h, D, h->dLU, s)) != cudaSuccess) return e;
+      bs_residual_kernel<<<dim3((unsigned)N, (unsigned)nb), BS_THREADS, 0, s>>>(A, h->dLU, N, h->dBatch);
+      bs_finalize_kernel<<<(nb + 127) / 128, 128, 0, s>>>(h->dBatch, nb, p.d_gids, b->tau, pass, status, done,
+                                                          routes);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    *launches += (h->launches - l0) + 9;  // the recursion's and the products', and the nine above
   }
   return cudaSuccess;
+}
+
+rd_status rd_bsplit_info(rd_batch_split* b, int G, int32_t* digits, int32_t* passes, double* residual,
+                         double* screen_bits) {
+  for (int g = 0; g < G; ++g) {
+    digits[g] = passes[g] = 0;
+    residual[g] = 0.0;
+    screen_bits[g] = -1.0;
+  }
+  if (!b) return RD_OK;
+  for (auto& p : b->parts) {
+    const int nb = p.h->nbatch;
+    std::vector<rd_batch_graph> hb(nb);
+    std::vector<int32_t> gid(nb);
+    if (cudaMemcpy(hb.data(), p.h->dBatch, nb * sizeof(rd_batch_graph), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(gid.data(), p.d_gids, nb * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return RD_ERR_CUDA;
+    for (int q = 0; q < nb; ++q) {
+      digits[gid[q]] = hb[q].digits;
+      passes[gid[q]] = hb[q].passes;
+      residual[gid[q]] = hb[q].residual;
+      screen_bits[gid[q]] = hb[q].screen_bits;
+    }
+  }
+  return RD_OK;
 }

@@ -564,9 +564,11 @@ __global__ void permute_m_kernel(const double* __restrict__ M, const int32_t* __
 
 // (a stacked batch: graph blockIdx.y, R and out r_gs and o_gs doubles further)
 __global__ void copy_rows_kernel(const double* __restrict__ R, long long ldr, int rows, int cols,
-                                 double* __restrict__ out, long long ldo, long long r_gs, long long o_gs) {
+                                 double* __restrict__ out, long long ldo, long long r_gs, long long o_gs,
+                                 const rd_batch_graph* bg) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)rows * cols) return;
+  if (bg && bg[blockIdx.y].s == 0) return;
   R += (long long)blockIdx.y * r_gs;
   out += (long long)blockIdx.y * o_gs;
   const int r = (int)(t / cols), c = (int)(t % cols);
@@ -660,7 +662,7 @@ cudaError_t rd_copy_rows_out(rd_ctx* h, const double* R, long long ldr, int rows
   if (e != cudaSuccess) return e;
   const unsigned nb = h->nbatch > 1 ? (unsigned)h->nbatch : 1u;
   copy_rows_kernel<<<dim3((unsigned)((total + threads - 1) / threads), nb), threads, 0, s>>>(
-      R, ldr, rows, cols, out, ldo, rd_batch_stride(h, R), rd_batch_stride(h, out));
+      R, ldr, rows, cols, out, ldo, rd_batch_stride(h, R), rd_batch_stride(h, out), nb > 1 ? h->dBatch : nullptr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(rd_gemm_f64_args p0, rd_ge
   constexpr int R = T / 16;           // micro-tile edge
   constexpr int LA = T * BK / NT;     // elements of A (and of B) each thread stages per K step
   const rd_gemm_f64_args& p = (blockIdx.z == 0) ? p0 : p1;
+  if (p.bg && p.bg[blockIdx.y].s == 0) return;  // a graph of a stacked batch without work in this pass
   // graph blockIdx.y of a stacked batch (strides 0 for one graph)
   const double* __restrict__ pA = p.A + (long long)blockIdx.y * p.a_gs;
   const double* __restrict__ pB = p.B + (long long)blockIdx.y * p.b_gs;
@@ -170,8 +171,10 @@ cudaError_t rd_gemm_f64(rd_ctx* h, const rd_gemm_f64_args* probs, int nprob, cud
       q[i].a_gs = rd_batch_stride(h, q[i].A);
       q[i].b_gs = rd_batch_stride(h, q[i].B);
       q[i].c_gs = rd_batch_stride(h, q[i].C);
+      q[i].bg = h->dBatch;
     } else {
       q[i].a_gs = q[i].b_gs = q[i].c_gs = 0;
+      q[i].bg = nullptr;
     }
   }
   probs = q;

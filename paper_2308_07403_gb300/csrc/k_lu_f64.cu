@@ -83,7 +83,10 @@ __global__ void __launch_bounds__(256) leaf_lu_kernel(double* __restrict__ LU, l
   static_assert(B == 64, "the leaf kernels are laid out for 64 x 64 blocks");
   __shared__ LeafLuShared sm;
   const int t = threadIdx.x, r = t >> 4, c = t & 15, w = t >> 5;
-  if (bg) status = bg[blockIdx.x].status;
+  if (bg) {
+    if (bg[blockIdx.x].s == 0) return;  // no split work for this graph in this pass
+    status = bg[blockIdx.x].status;
+  }
   double* blk = LU + (long long)blockIdx.x * gs + (long long)k0 * ld + k0;
   double a[4][4];
 #pragma unroll
@@ -109,10 +112,12 @@ __global__ void __launch_bounds__(256) leaf_lu_kernel(double* __restrict__ LU, l
 // columns of L^-1, 16..31 those of U^-1, so the FP64 work is spread over 32 SMs.
 // (a stacked batch: graph blockIdx.y, its matrices gs doubles further)
 __global__ void __launch_bounds__(128) leaf_inv_kernel(const double* __restrict__ LU,
-                                                       double* __restrict__ T, long long ld, int k0, long long gs) {
+                                                       double* __restrict__ T, long long ld, int k0, long long gs,
+                                                       const rd_batch_graph* bg) {
   __shared__ double f[B][B + 1];
   __shared__ double rcp[B];
   const int t = threadIdx.x, lane = t & 31;
+  if (bg && bg[blockIdx.y].s == 0) return;
   LU += (long long)blockIdx.y * gs;
   T += (long long)blockIdx.y * gs;
   const double* blk = LU + (long long)k0 * ld + k0;
@@ -166,7 +171,7 @@ cudaError_t rd_lu_diag(rd_ctx* h, int k0, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rd_prof_end(h, s, RD_PROF_NONE, 0.0)) != cudaSuccess) return e;
   if ((e = rd_prof_begin(h, s, RD_PROF_NONE)) != cudaSuccess) return e;
-  leaf_inv_kernel<<<dim3(32, nb), 128, 0, s>>>(h->dLU, h->dT, h->N, k0, gs);
+  leaf_inv_kernel<<<dim3(32, nb), 128, 0, s>>>(h->dLU, h->dT, h->N, k0, gs, nb > 1 ? h->dBatch : nullptr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return rd_prof_end(h, s, RD_PROF_NONE, 0.0);
 }

@@ -631,6 +631,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     unit %= per_graph;
   }
   const rd_batch_graph* bgr = p.nbatch > 1 ? p.bg + gb : nullptr;
+  // a graph of a stacked batch without split work in this pass: nothing to do (both CTAs of a pair
+  // belong to one graph, so a pair leaves together, before any barrier)
+  if (bgr && bgr->s == 0) return;
   const int* eA = p.eA + (long long)gb * p.ea_gs;
   const int* eB = p.eB + (long long)gb * p.eb_gs;
   const int a_plane0 = gb * p.s_max, b_plane0 = gb * p.s_max;  // first digit plane of this graph

@@ -64,9 +64,12 @@ struct rd_batch_graph {
   double log_gamma;      // the decode's log(gamma) and 1 / log2(gamma)
   float inv_log2_gamma;
   int32_t status[2];     // RD_DEV_* of this graph and its detail
-  int32_t route;         // 0: split result kept; 1: FP64 (screened out or failed the self-check)
+  int32_t route;         // 0: on the split path; 1: failed the residual check; 2: failed the gain
+                         // check; 3: screened out (these three go to the FP64 kernel)
   double residual;       // largest entrywise relative residual of its split Y (the self-check)
   double screen_bits;    // its range screen: chunk spread x log2(1 / gamma)
+  int32_t digits;        // the digit count of its kept split result (0: none)
+  int32_t passes;        // split passes it took (2: redone with more digits after the check)
 };
 
 struct rd_ctx {
@@ -212,8 +215,10 @@ struct rd_gemm_f64_args {
   // CTA must then own the whole strip it reads, so the 64 x 64 tile is kept and the aliased
   // extent (N when C aliases A, M when C aliases B) must be 64
   int aliased;
-  // stacked batches: per-graph element strides of A, B and C (blockIdx.y is the graph)
+  // stacked batches: per-graph element strides of A, B and C (blockIdx.y is the graph), and the
+  // graphs (bg[b].s == 0: no split work in this pass, skipped)
   long long a_gs, b_gs, c_gs;
+  const rd_batch_graph* bg;
 };
 
 // flops: algorithmic flop count of the launch (for the profile), computed by the caller
@@ -289,6 +294,10 @@ rd_status rd_bsplit_create(const int32_t* n, const double* gamma, const int64_t*
 cudaError_t rd_bsplit_run(rd_batch_split* b, const uint8_t* A, int32_t* D, int32_t* status, int32_t* done,
                           int32_t* routes, cudaStream_t s, int64_t* launches);
 void rd_bsplit_destroy(rd_batch_split* b);
+// per graph of the batch (host arrays of G): digits of its kept split result (0: none), split
+// passes it took, its last residual and its screen estimate (-1: not screened); synchronous
+rd_status rd_bsplit_info(rd_batch_split* b, int G, int32_t* digits, int32_t* passes, double* residual,
+                         double* screen_bits);
 
 // ---- errors of calls without a handle (read back through rd_last_error(NULL)) -----------------
 void rd_record_error(const std::string& msg);

@@ -63,6 +63,7 @@ _SIGS = {
     "rd_batch_destroy": (None, [_P]),
     "rd_batch_set_precision": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "rd_batch_routes": (ctypes.c_int, [_P, _P]),
+    "rd_batch_split_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "rd_batch_tuning": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "rd_serve_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_P)]),
     "rd_serve_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
@@ -395,6 +396,15 @@ class Batch:
         r = np.empty(self.G, dtype=np.int32)
         _check(load().rd_batch_routes(self.h, r.ctypes.data_as(_P)))
         return r
+
+    def split_info(self):
+        """Per graph: digits of its kept split result, split passes, last residual, screen bits."""
+        d = np.empty(self.G, np.int32)
+        p = np.empty(self.G, np.int32)
+        r = np.empty(self.G)
+        sb = np.empty(self.G)
+        _check(load().rd_batch_split_info(self.h, *(x.ctypes.data_as(_P) for x in (d, p, r, sb))))
+        return {"digits": d, "passes": p, "residual": r, "screen_bits": sb}
 
     def tuning(self):
         """Per size class (n in (128 c, 128 (c + 1)]): graphs, on the split path, ms per graph of both variants."""

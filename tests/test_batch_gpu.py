@@ -114,6 +114,13 @@ def run_split(rd, ns, As, gs, autotune, fill=-7, graph_capture=False):
         st = b.status()
         routes = b.routes()
         tune = b.tuning()
+        info = b.split_info()
+    # the record agrees with the routes: a kept split result has its digit count (8..15) and one or
+    # two passes; nothing else has digits
+    kept = routes == 1
+    assert ((info["digits"] >= 8) & (info["digits"] <= 15))[kept].all()
+    assert np.isin(info["passes"][kept], (1, 2)).all()
+    assert (info["digits"][~kept] == 0).all()
     return off, D_dev.cpu().numpy(), st, routes, tune
 
 
