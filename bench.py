@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--weighted-cols", type=int, default=256)
     p.add_argument("--weighted-frac", type=float, default=0.9, help="weighted: gain as a fraction of the weighted bound")
     p.add_argument("--batch-graphs", type=int, default=4096)
-    p.add_argument("--serve-seconds", type=float, default=20.0, help="serving: length of the arrival stream")
+    p.add_argument("--serve-seconds", type=float, default=60.0, help="serving: length of the arrival stream")
     p.add_argument("--serve-rate", type=float, default=200.0, help="serving: Poisson arrival rate (req/s)")
     return p.parse_args()
 
@@ -570,10 +570,22 @@ def run_serving(args):
             statuses.append(srv.wait(rid))
 
     srv = rd.Server(128 << 30, workers=8)
+    # outputs in pinned host memory, one D and one row block per graph (a latency-sensitive client's
+    # buffers: the 64 MB D of a 4096-node graph copies from the device in about a millisecond instead
+    # of the several a pageable buffer takes); requests for one graph run one after another
+    pinned = os.environ.get("RD_BENCH_PAGEABLE_OUTPUTS", "0") != "1"
+    outD, outY = [], []
+    for A, _ in pool:
+        n = A.shape[0]
+        if pinned:
+            outD.append(torch.empty((n, n), dtype=torch.int32).pin_memory().numpy())
+            outY.append(torch.empty((64, n), dtype=torch.float64).pin_memory().numpy())
+        else:
+            outD.append(np.empty((n, n), np.int32))
+            outY.append(np.empty((64, n)))
     # warm-up: factor every graph once (what a server holds after its first minutes), untimed
     for gid, (A, g) in enumerate(pool):
-        out = np.empty((1, A.shape[0]))
-        srv.wait(srv.submit_goals(gid, A, g, np.array([0], np.int32), out))
+        srv.wait(srv.submit_goals(gid, A, g, np.array([0], np.int32), outY[gid][:1]))
     th = threading.Thread(target=waiter, daemon=True)
     th.start()
     s0 = srv.stats()
@@ -587,9 +599,9 @@ def run_serving(args):
         A, g = pool[gid]
         n = A.shape[0]
         if goals is None:
-            rid = srv.submit_apsp(gid, A, g, np.empty((n, n), np.int32))
+            rid = srv.submit_apsp(gid, A, g, outD[gid])
         else:
-            rid = srv.submit_goals(gid, A, g, goals, np.empty((goals.size, n)))
+            rid = srv.submit_goals(gid, A, g, goals, outY[gid][:goals.size])
         done_q.put(rid)
     done_q.put(None)
     th.join()
@@ -604,12 +616,16 @@ def run_serving(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16-digits+f64", "data": "synthetic",
         "config": {"workload": f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s over 128 graphs, "
                                f"n log-uniform [64, 4096] (ER p=4/n, grid, WS k=10), gain 0.5/(Delta+1); "
-                               f"25% APSP, 75% goal rows (k ~ U[1,64]); split precision, 8 workers, 128 GB budget",
+                               f"25% APSP, 75% goal rows (k ~ U[1,64]); split precision, 8 workers, 128 GB budget; "
+                               f"outputs in {'pinned' if pinned else 'pageable'} host buffers, one per graph",
                    "requests": n_req, "parallelism": "one GPU, 8 streams"},
         "p50_ms": pct([lat for _, lat in statuses], 0.5), "p99_ms": pct([lat for _, lat in statuses], 0.99),
         "latency_note": "submit-to-completion, measured by the library, over the stream's requests",
         "requests_ok": int(sum(1 for st, _ in statuses if st == rd.RD_OK)),
         "max_inflight": s1["max_inflight"], "evictions": s1["evictions"] - s0["evictions"],
+        "device_loop_requests": s1["loop_requests"] - s0["loop_requests"],
+        "device_loop": "goal requests on graphs of at most %s nodes on the device-resident loop" %
+                       os.environ.get("RD_SERVE_LOOP_MAX_N", "1024"),
         "resident_graphs": s1["resident_graphs"], "clocks": clk,
         "e2e": {"value": n_req / wall, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
         "gpu_launches": s1["launches"] - s0["launches"],

@@ -333,7 +333,11 @@ rd_status rd_batch_tuning(rd_batch_handle b, int32_t* graphs, int32_t* split, do
  * A server runs requests -- the full R-distance of a graph, or goal rows (the local mode of
  * Sec. 4.2) -- on `workers` threads, each with its own CUDA stream, one request per worker at a
  * time, so requests that arrive while others run start as soon as a worker and device memory are
- * free and their work overlaps on the device.  Each graph's handle (its LU factors and inverses)
+ * free and their work overlaps on the device.  Goal requests on graphs of at most 1024 nodes run on
+ * a device-resident loop: a persistent kernel (16 CTAs, while requests flow; every wait bounded)
+ * takes request descriptors from a ring in mapped host memory and computes the rows of Y from the
+ * graph's resident triangular inverses (row g of U^-1 times L^-1, FP64), so no kernel is launched
+ * per request; larger goal requests run on the tensor-core path through the worker's stream.  Each graph's handle (its LU factors and inverses)
  * stays resident under the caller's graph id, so later goal solves on the same graph skip the
  * factorisation; when a new handle does not fit the device-memory budget, the least recently used
  * idle graphs are evicted.  Requests for one graph run one after another (a handle is not
@@ -361,7 +365,8 @@ typedef struct {
   int64_t bytes_used, evictions, reused;
   double p50_ms, p99_ms;  /* submit-to-completion latency over all completed requests           */
   double seconds;         /* since rd_serve_create                                              */
-  int64_t launches;       /* kernel launches of all requests so far                             */
+  int64_t launches;       /* kernel launches of all requests so far (not counting the loop)      */
+  int64_t loop_requests;  /* goal requests served by the device-resident loop                    */
 } rd_serve_report;
 
 typedef struct rd_server* rd_server_handle;
@@ -386,6 +391,12 @@ rd_status rd_serve_wait(rd_server_handle s, int64_t id, rd_status* result, doubl
 rd_status rd_serve_wait_for(rd_server_handle s, int64_t id, double timeout_ms, rd_status* result,
                             double* latency_ms);
 rd_status rd_serve_stats(rd_server_handle s, rd_serve_report* out);
+/* The failure path of the device-resident goal loop: posts a request to the loop whose descriptor is
+ * never marked ready, so that the loop's bounded wait for it (0.2 s per work unit) runs out;
+ * *result receives what the loop reported: RD_ERR_TIMEOUT when the wait ran out and the loop
+ * recovered (it goes on serving), RD_ERR_STATE if it never reported.  A check for tests; it holds
+ * one ring slot for about half a second. */
+rd_status rd_serve_loop_check(rd_server_handle s, rd_status* result);
 /* Finish the queued requests, then free every resident graph and the server. */
 void rd_serve_destroy(rd_server_handle s);
 

@@ -526,6 +526,20 @@ cudaError_t rd_prof_collect(rd_ctx* h) {
   return cudaSuccess;
 }
 
+// The factors and both triangular inverses of the handle's graph resident in dT (the serving loop
+// reads rows of U^-1 and columns of L^-1 there); waits for the handle's stream.
+rd_status rd_prepare_inverses(rd_ctx* h) {
+  RD_CK(h, cudaSetDevice(h->device));
+  if (h->factored && h->inverted && !h->updated) return RD_OK;  // resident since an earlier request
+  rd_status st = ensure_factored(h);
+  if (st != RD_OK) return st;
+  if (h->used_precision != RD_PREC_SPLIT_BF16 && !h->inverted) {
+    RD_CK(h, rd_trtri_f64(h, h->stream));
+    h->inverted = 1;
+  }
+  return check_device_status(h);
+}
+
 extern "C" {
 
 rd_status rd_set_profiling(rd_handle h, int32_t on) {

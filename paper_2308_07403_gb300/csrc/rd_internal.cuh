@@ -176,6 +176,8 @@ inline long long rd_batch_stride(const rd_ctx* h, const void* p) {
 // Device memory of a handle (see rd_ctx::pool); frees are stream-ordered for pooled handles.
 cudaError_t rd_dev_alloc(rd_ctx* h, void** p, size_t bytes);
 void rd_dev_free(rd_ctx* h, void* p);
+// factors and both triangular inverses of the handle's graph resident (dT complete); synchronises
+rd_status rd_prepare_inverses(rd_ctx* h);
 // rd_create with every allocation of the handle (now and later) from `pool` on `stream`
 rd_status rd_create_pooled(const uint8_t* A, int32_t n, double gamma, cudaMemPool_t pool, cudaStream_t stream,
                            rd_handle* out);
@@ -298,6 +300,20 @@ void rd_bsplit_destroy(rd_batch_split* b);
 // passes it took, its last residual and its screen estimate (-1: not screened); synchronous
 rd_status rd_bsplit_info(rd_batch_split* b, int G, int32_t* digits, int32_t* passes, double* residual,
                          double* screen_bits);
+
+// ---- the serving runtime's device-resident goal loop (rd_serve_loop.cu) ------------------------
+#define RD_LOOP_MAX_N 4096  // the loop's staging rows hold graphs of at most this many nodes
+#define RD_LOOP_DEFAULT_N 1024  // goal requests on graphs of at most this many nodes run on the loop
+struct rd_serve_loop;
+rd_status rd_loop_create(int device, rd_serve_loop** out, std::string* err);
+void rd_loop_destroy(rd_serve_loop* L);
+// rows of Y for goals[0..k) of a resident graph whose inverses are complete (rd_prepare_inverses),
+// computed by the loop; Y: host, k x n.  Blocks until done, at most timeout_ms (RD_ERR_TIMEOUT).
+rd_status rd_loop_goals(rd_serve_loop* L, rd_ctx* h, const int32_t* goals, int k, double* Y, double timeout_ms);
+// post a request whose descriptor is never marked ready: the loop's bounded wait runs out and it
+// reports RD_ERR_TIMEOUT (the loop's failure path)
+rd_status rd_loop_unready(rd_serve_loop* L, double timeout_ms);
+int64_t rd_loop_requests(rd_serve_loop* L);
 
 // ---- errors of calls without a handle (read back through rd_last_error(NULL)) -----------------
 void rd_record_error(const std::string& msg);

@@ -11,6 +11,16 @@
 // same time (a handle is not thread-safe); a later request for a busy graph waits while the queue
 // behind it moves on.
 //
+// Goal requests on graphs of at most RD_LOOP_DEFAULT_N nodes run on the device-resident loop
+// (rd_serve_loop.cu): the worker makes the graph resident with its factors and both triangular
+// inverses (the first request of a graph), then posts the request to the loop's ring and waits for
+// it; no kernel is launched per request.  Full APSP requests, and goal requests on larger graphs,
+// run through rd_apsp / rd_goal_solve on the worker's stream: the loop computes rows in FP64 on a
+// few SMs, and a 4096-node request (4.5 ms there) queued behind the split kernels of concurrent
+// APSP requests, which hold every SM, made the stream fall behind its arrivals, while the same
+// request takes about half a millisecond on the tensor cores.  RD_SERVE_LOOP_MAX_N (0..4096) at
+// rd_serve_create moves the limit (0: no loop requests).
+//
 // Device memory: every handle of the server allocates from one stream-ordered memory pool
 // (cudaMallocFromPoolAsync on the worker's stream) and an evicted handle returns its memory with
 // cudaFreeAsync, so admission and eviction never synchronise the device or stall the other
@@ -19,6 +29,7 @@
 // every admitted request fits once the idle graphs are evicted.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -70,6 +81,8 @@ int64_t estimate_bytes(int32_t n, int32_t precision) {
 struct rd_server {
   int device = 0;
   cudaMemPool_t pool = nullptr;  // the handles' device memory (see the file comment)
+  rd_serve_loop* loop = nullptr;  // the device-resident goal loop
+  int loop_max_n = RD_LOOP_DEFAULT_N;  // goal requests on graphs up to this size run on the loop
   int64_t budget = 0;
   int64_t used = 0;
   std::mutex mu;
@@ -157,10 +170,16 @@ void run_job(rd_server* s, Job* j, cudaStream_t st) {
   // the handle is this worker's until the request ends; a handle made for it counts from its creation
   const int64_t launches0 = (h && !j->fresh) ? h->launches : 0;
   if (r == RD_OK) {
-    if (j->r.kind == RD_REQ_APSP)
+    if (j->r.kind == RD_REQ_APSP) {
       r = rd_apsp(h, j->r.D_out, nullptr);
-    else
+    } else if (s->loop && j->r.n <= s->loop_max_n) {
+      for (int c = 0; c < j->r.k && r == RD_OK; ++c)
+        if (j->goals[c] < 0 || j->goals[c] >= j->r.n) r = RD_ERR_ARG;
+      if (r == RD_OK) r = rd_prepare_inverses(h);
+      if (r == RD_OK) r = rd_loop_goals(s->loop, h, j->goals.data(), j->r.k, j->r.Y_out, 60000.0);
+    } else {
       r = rd_goal_solve(h, j->goals.data(), j->r.k, j->r.Y_out);
+    }
   }
   std::lock_guard<std::mutex> lk(s->mu);
   if (h) s->launches += h->launches - launches0;
@@ -262,10 +281,23 @@ rd_status rd_serve_create(int64_t hbm_budget_bytes, int32_t workers, rd_server_h
   }
   uint64_t keep = (uint64_t)hbm_budget_bytes;  // memory kept mapped in the pool between requests
   cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  std::string lerr;
+  {
+    // RD_SERVE_LOOP_MAX_N overrides the largest graph whose goal requests run on the loop (0: none)
+    const char* lm = getenv("RD_SERVE_LOOP_MAX_N");
+    if (lm) s->loop_max_n = std::max(0, std::min(RD_LOOP_MAX_N, atoi(lm)));
+  }
+  if (rd_loop_create(s->device, &s->loop, &lerr) != RD_OK) {
+    cudaMemPoolDestroy(s->pool);
+    delete s;
+    rd_record_error("rd_serve_create: " + lerr);
+    return RD_ERR_CUDA;
+  }
   for (int w = 0; w < workers; ++w) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       for (cudaStream_t q : s->streams) cudaStreamDestroy(q);
+      rd_loop_destroy(s->loop);
       cudaMemPoolDestroy(s->pool);
       delete s;
       rd_record_error("rd_serve_create: cudaStreamCreate failed");
@@ -355,9 +387,16 @@ rd_status rd_serve_stats(rd_server_handle s, rd_serve_report* out) {
   out->evictions = s->evictions;
   out->reused = s->reused;
   out->launches = s->launches;
+  out->loop_requests = s->loop ? rd_loop_requests(s->loop) : 0;
   out->p50_ms = percentile(s->lat_ms, 0.5);
   out->p99_ms = percentile(s->lat_ms, 0.99);
   out->seconds = std::chrono::duration<double>(clock_type::now() - s->t0).count();
+  return RD_OK;
+}
+
+rd_status rd_serve_loop_check(rd_server_handle s, rd_status* result) {
+  if (!s || !result || !s->loop) return RD_ERR_ARG;
+  *result = rd_loop_unready(s->loop, 10000.0);
   return RD_OK;
 }
 
@@ -369,6 +408,7 @@ void rd_serve_destroy(rd_server_handle s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
+  rd_loop_destroy(s->loop);  // every request is done: the loop reads no handle any more
   for (auto& e : s->cache)
     if (e.second.h) rd_destroy(e.second.h);
   for (auto& e : s->jobs) delete e.second;

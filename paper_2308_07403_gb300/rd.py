@@ -73,6 +73,7 @@ _SIGS = {
     "rd_serve_wait_for": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_double)]),
     "rd_serve_stats": (ctypes.c_int, [_P, _P]),
+    "rd_serve_loop_check": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "rd_serve_destroy": (None, [_P]),
 }
 RD_REQ_APSP = 0
@@ -446,7 +447,7 @@ class rd_serve_report(ctypes.Structure):
                 ("resident_graphs", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("bytes_used", ctypes.c_int64), ("evictions", ctypes.c_int64), ("reused", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("loop_requests", ctypes.c_int64)]
 
 
 class Server:
@@ -513,6 +514,13 @@ class Server:
                                             ctypes.byref(lat)))
         self._live.pop(int(rid), None)
         return st.value, lat.value
+
+    def loop_check(self):
+        """The device loop's failure path: the status it reports for a request whose descriptor is
+        never marked ready (RD_ERR_TIMEOUT when its bounded wait ran out and it recovered)."""
+        st = ctypes.c_int()
+        _check(load().rd_serve_loop_check(self.h, ctypes.byref(st)))
+        return st.value
 
     def stats(self):
         r = rd_serve_report()

@@ -104,6 +104,8 @@ def test_serve_alone_equals_mix_and_the_oracle(rd, oracle_results):
     assert s["completed"] == len(reqs) and s["failed"] == 0
     assert s["max_inflight"] > 1          # the work overlapped
     assert s["reused"] >= len(reqs) - 8   # goal solves on resident factors
+    # goal requests on graphs of at most 1024 nodes ran on the device loop, the rest on the host path
+    assert s["loop_requests"] == sum(r[0] == "goals" and r[2].shape[0] <= 1024 for r in reqs)
     for req, out in zip(reqs, alone):     # and the results are the method's
         check_against_oracle(req, out, oracle_results)
 
@@ -178,3 +180,44 @@ def test_serve_rejects_bad_requests(rd):
         with pytest.raises(rd.RDError) as ei:
             srv.submit_apsp(0, big, graphs.gamma_small(big), np.empty((2048, 2048), np.int32))
         assert ei.value.status == rd.RD_ERR_OOM
+
+
+def test_serve_device_loop_bounded_wait_and_recovery(rd):
+    """The device loop's failure path: a request whose descriptor is never marked ready makes the
+    loop's bounded wait run out (RD_ERR_TIMEOUT, reported by the device), and the loop goes on
+    serving: goal requests before and after are the oracle's rows."""
+    A = graphs.ws(600, 10, 0.1, 12)  # (600 <= 1024: the loop serves it)
+    g = graphs.gamma_small(A)
+    goals = np.array([0, 17, 333, 599], np.int32)
+    ref = oracle.goal_rows(A, g, goals)
+    with rd.Server(4 << 30, workers=2) as srv:
+        for precision in (rd.RD_PREC_FP64, rd.RD_PREC_SPLIT_BF16):
+            out = np.empty((goals.size, 600))
+            assert srv.wait(srv.submit_goals(5 + precision, A, g, goals, out, precision=precision))[0] == rd.RD_OK
+            assert np.max(np.abs(out - ref) / ref) < YTOL[precision]
+        assert srv.loop_check() == rd.RD_ERR_TIMEOUT
+        out = np.empty((goals.size, 600))
+        assert srv.wait(srv.submit_goals(5, A, g, goals, out, precision=rd.RD_PREC_FP64))[0] == rd.RD_OK
+        assert np.max(np.abs(out - ref) / ref) < YTOL[0]
+        s = srv.stats()
+    assert s["loop_requests"] == 3 and s["failed"] == 0
+
+
+def test_serve_large_goal_requests_take_the_host_path(rd):
+    """Goal requests on graphs of more than 1024 nodes run through rd_goal_solve on the worker's
+    stream: on the directed path 0 -> 1 -> ... the row of goal g is gamma^(g - j) for j <= g and 0
+    beyond (the closed form of Y)."""
+    n, gam = 4300, 0.9
+    A = graphs.directed_path(n)
+    goals = np.array([0, 5, 2000, n - 1], np.int32)
+    out = np.empty((goals.size, n))
+    with rd.Server(8 << 30, workers=1) as srv:
+        assert srv.wait(srv.submit_goals(1, A, gam, goals, out, precision=rd.RD_PREC_FP64))[0] == rd.RD_OK
+        s = srv.stats()
+    assert s["loop_requests"] == 0
+    j = np.arange(n)
+    for c, g in enumerate(goals):
+        ref = np.where(j <= g, float(gam) ** np.maximum(g - j, 0), 0.0)
+        nz = ref > 0
+        assert np.array_equal(out[c] == 0, ~nz)
+        assert np.max(np.abs(out[c][nz] - ref[nz]) / ref[nz]) < 1e-11
