@@ -334,7 +334,7 @@ rd_status rd_batch_tuning(rd_batch_handle b, int32_t* graphs, int32_t* split, do
  * Sec. 4.2) -- on `workers` threads, each with its own CUDA stream, one request per worker at a
  * time, so requests that arrive while others run start as soon as a worker and device memory are
  * free and their work overlaps on the device.  Goal requests on graphs of at most 1024 nodes run on
- * a device-resident loop: a persistent kernel (16 CTAs, while requests flow; every wait bounded)
+ * a device-resident loop: a persistent kernel (38 CTAs, while requests flow; every wait bounded)
  * takes request descriptors from a ring in mapped host memory and computes the rows of Y from the
  * graph's resident triangular inverses (row g of U^-1 times L^-1, FP64), so no kernel is launched
  * per request; larger goal requests run on the tensor-core path through the worker's stream.  Each graph's handle (its LU factors and inverses)

@@ -11,8 +11,10 @@
 //   row g of Y = (row g of U^-1) L^-1, entry q = sum_{k >= max(g, q)} U^-1[g][k] L^-1[k][q]
 //
 // (Y = M^-1 = U^-1 L^-1; L^-1 is unit lower triangular; both inverses are non-negative for the
-// M-matrices of the method, so every sum adds terms of one sign.)  A work unit is a block of
-// columns for all the request's goals: 64 units cover the padded size N.  A graph in the split
+// M-matrices of the method, so every sum adds terms of one sign.)  A work unit is a group of 16
+// goals times a block of columns: 4 goal groups x 32 column blocks cover 64 goals and the padded
+// size N.  FP64 is slow on this GPU (2 FMA per clock per SM), so a request is spread over many
+// small units: a 256-node request with 32 goals is 16 units, one per SM.  A graph in the split
 // path's locality order keeps its inverses in that order: goal g sits at position pos[g] and
 // position q holds node ord[q], so the rows are written back in the caller's node order.
 //
@@ -36,10 +38,13 @@
 namespace {
 
 constexpr int LOOP_RING = 32;          // request descriptors in flight
-constexpr int LOOP_UNITS = 64;         // work units per request (column blocks covering N)
-constexpr int LOOP_CTAS = 16;          // about a tenth of the SMs (its requests are small graphs)
+constexpr int LOOP_GG = 4;             // goal groups of 16 per request
+constexpr int LOOP_CB = 32;            // column blocks per request
+constexpr int LOOP_UNITS = LOOP_GG * LOOP_CB;  // work units per request
+constexpr int LOOP_CTAS = 38;          // a quarter of the SMs, while requests flow
 constexpr int LOOP_THREADS = 256;
 constexpr int LOOP_KB = 32;            // K step of the staged tiles
+constexpr int LOOP_COLS = 32;          // columns of a unit's sub-block
 constexpr unsigned long long LOOP_IDLE_NS = 2000000ull;     // a CTA leaves after 2 ms without work (default)
 constexpr unsigned long long LOOP_READY_NS = 200000000ull;  // wait for a posted descriptor: 0.2 s
 
@@ -48,7 +53,7 @@ struct LoopSlot {  // mapped pinned host memory; the host writes it before posti
   const int32_t* pos;         // node -> position (locality order) or null
   const int32_t* ord;         // position -> node (locality order) or null
   double* out;                // device address of the slot's staging rows (mapped), k x n
-  int32_t n, N, k, cw;        // cw: columns per unit, a multiple of 64
+  int32_t n, N, k, cw;        // cw: columns per column block, a multiple of 32
   int32_t goals[RD_MAX_GOALS];
   volatile long long seq;     // the request's sequence number, written last
   volatile int32_t state;     // written by the device: 0 pending, 2 done, 3 a bounded wait expired
@@ -66,10 +71,11 @@ __device__ __forceinline__ unsigned long long loop_time() {
   return t;
 }
 
-// One work unit: columns [unit cw, (unit + 1) cw) of the request's k rows.  Thread t owns a 4 x 4
-// register tile (goals 4 (t / 16) + a, columns 4 (t % 16) + b of a 64-column block); K advances
-// LOOP_KB at a time through shared memory.  The descriptor (host memory that the host rewrites for
-// every request of the slot) is read with volatile loads, never from a cached copy.
+// One work unit: goals [16 gg, 16 gg + 16) of the request's k and columns [cb cw, (cb + 1) cw), unit
+// = gg LOOP_CB + cb, in sub-blocks of 32 columns.  Thread t owns goal 16 gg + t / 16 and columns
+// 2 (t % 16) and 2 (t % 16) + 1 of the sub-block; K advances LOOP_KB at a time through shared
+// memory.  The descriptor (host memory that the host rewrites for every request of the slot) is
+// read with volatile loads, never from a cached copy.
 struct UnitDesc {
   const double* T;
   const int32_t* pos;
@@ -77,8 +83,8 @@ struct UnitDesc {
   double* out;
   int n, N, k, cw;
 };
-__device__ void loop_unit(const LoopSlot* S_, int unit, double (*Us)[LOOP_KB + 1], double (*Ls)[64 + 1], int* gpos,
-                          UnitDesc* d) {
+__device__ void loop_unit(const LoopSlot* S_, int unit, double (*Us)[LOOP_KB + 1], double (*Ls)[LOOP_COLS + 1],
+                          int* gpos, UnitDesc* d) {
   const volatile LoopSlot* S = S_;
   const int t = threadIdx.x;
   if (t == 0) {
@@ -93,67 +99,57 @@ __device__ void loop_unit(const LoopSlot* S_, int unit, double (*Us)[LOOP_KB + 1
   }
   __syncthreads();
   const int N = d->N, n = d->n, k = d->k, cw = d->cw;
+  const int gg = unit / LOOP_CB, cb = unit % LOOP_CB;
+  const int c0 = 16 * gg;
+  if (c0 >= k || cb * cw >= n) return;  // (uniform) no goal or no column of this unit
   const double* __restrict__ T = d->T;
   const int32_t* pos = d->pos;
   const int32_t* ord = d->ord;
   double* out = d->out;
-  if (t < RD_MAX_GOALS) gpos[t] = (t < k) ? (pos ? pos[S->goals[t]] : S->goals[t]) : N;  // N: a zero row
+  if (t < 16) gpos[t] = (c0 + t < k) ? (pos ? pos[S->goals[c0 + t]] : S->goals[c0 + t]) : N;  // N: a zero row
   __syncthreads();
-  const int ci = 4 * (t / 16), cj = 4 * (t % 16);
-  const int q1 = min(N, (unit + 1) * cw);
-  for (int q0 = unit * cw; q0 < q1; q0 += 64) {
-    double acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  const int ci = t / 16, cj = 2 * (t % 16);
+  const int q1 = min(n, (cb + 1) * cw);
+  for (int q0 = cb * cw; q0 < q1; q0 += LOOP_COLS) {
+    double acc0 = 0.0, acc1 = 0.0;
     for (int k0 = q0; k0 < N; k0 += LOOP_KB) {  // L^-1[kk][q] = 0 for kk < q
-      for (int e = t; e < RD_MAX_GOALS * LOOP_KB; e += LOOP_THREADS) {
+      for (int e = t; e < 16 * LOOP_KB; e += LOOP_THREADS) {
         const int c = e / LOOP_KB, kk = k0 + e % LOOP_KB;
         const int g = gpos[c];
         Us[c][e % LOOP_KB] = (g < N && kk >= g && kk < N) ? T[(long long)g * N + kk] : 0.0;
       }
-      for (int e = t; e < LOOP_KB * 64; e += LOOP_THREADS) {
-        const int kk = k0 + e / 64, q = q0 + e % 64;
+      for (int e = t; e < LOOP_KB * LOOP_COLS; e += LOOP_THREADS) {
+        const int kk = k0 + e / LOOP_COLS, q = q0 + e % LOOP_COLS;
         double v = 0.0;
         if (kk < N && q < N) v = kk > q ? T[(long long)kk * N + q] : (kk == q ? 1.0 : 0.0);
-        Ls[e / 64][e % 64] = v;
+        Ls[e / LOOP_COLS][e % LOOP_COLS] = v;
       }
       __syncthreads();
-      // (goal rows c >= k are zero: a warp whose two goal groups are both past k skips the FMAs)
-#pragma unroll 4
-      for (int kk = 0; kk < LOOP_KB && ci < k; ++kk) {
-        double x[4], y[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) x[a] = Us[ci + a][kk];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) y[b] = Ls[kk][cj + b];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+      if (c0 + ci < k) {  // (goal rows past k are zero: their warps skip the FMAs)
+#pragma unroll 8
+        for (int kk = 0; kk < LOOP_KB; ++kk) {
+          const double x = Us[ci][kk];
+          acc0 = fma(x, Ls[kk][cj], acc0);
+          acc1 = fma(x, Ls[kk][cj + 1], acc1);
+        }
       }
       __syncthreads();
     }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int c = ci + a, q = q0 + cj + b;
-        if (c < k && q < n) {  // positions n..N-1 are padding
-          const int node = ord ? ord[q] : q;
-          out[(long long)c * n + node] = acc[a][b];
-        }
-      }
+    const int c = c0 + ci;
+    if (c < k) {  // positions n..N-1 are padding
+      const int qa = q0 + cj, qb = qa + 1;
+      if (qa < n) out[(long long)c * n + (ord ? ord[qa] : qa)] = acc0;
+      if (qb < n) out[(long long)c * n + (ord ? ord[qb] : qb)] = acc1;
+    }
   }
 }
 
 __global__ void __launch_bounds__(LOOP_THREADS) serve_loop_kernel(LoopSlot* ring, LoopCtl* ctl,
                                                                   unsigned long long* ctr, int* units_done,
                                                                   int* slot_err, unsigned long long idle_ns) {
-  __shared__ double Us[RD_MAX_GOALS][LOOP_KB + 1];
-  __shared__ double Ls[LOOP_KB][64 + 1];
-  __shared__ int gpos[RD_MAX_GOALS];
+  __shared__ double Us[16][LOOP_KB + 1];
+  __shared__ double Ls[LOOP_KB][LOOP_COLS + 1];
+  __shared__ int gpos[16];
   __shared__ long long s_unit;
   __shared__ int s_ready;
   __shared__ UnitDesc desc;
@@ -407,8 +403,8 @@ rd_status rd_loop_goals(rd_serve_loop* L, rd_ctx* h, const int32_t* goals, int k
     S.n = h->n;
     S.N = h->N;
     S.k = k;
-    const int per_unit = (h->N + LOOP_UNITS - 1) / LOOP_UNITS;
-    S.cw = (per_unit + 63) / 64 * 64;
+    const int per_block = (h->N + LOOP_CB - 1) / LOOP_CB;
+    S.cw = (per_block + LOOP_COLS - 1) / LOOP_COLS * LOOP_COLS;
     for (int c = 0; c < k; ++c) S.goals[c] = goals[c];
     S.state = 0;
     std::atomic_thread_fence(std::memory_order_release);
