@@ -36,6 +36,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "n=8192 R-distance APSP time/TFLOPS, split-prec vs FP64 (D exact); p50/p99"
+# DRAM bytes (read + write) per split GEMM launch of the headline workload: the mean over the 648
+# launches of six steps (all six graphs) in one one-pass ncu capture of this kernel build, and the
+# algorithmic bytes per launch (the digit tiles each product needs at least once plus its outputs,
+# same launches); profiles/launches_apsp_split_n8192.md gives the command and the model.  To be
+# captured again whenever split_gemm_kernel changes.
+SPLIT_TRAFFIC_PER_LAUNCH = 0.3552e9
+# DRAM bytes of the inverse product launch of `--workload product` (ER n = 4096, 9 digits, CTA pairs),
+# one one-pass ncu capture (profiles/split_gemm_pairs_inverse_product_n4096.md); None until taken
+PRODUCT_TRAFFIC = None
+SPLIT_ALGORITHMIC_BYTES_PER_LAUNCH = 0.1389e9
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
@@ -53,7 +63,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--verify", type=int, default=1, help="hash D of every graph against the oracle's")
     p.add_argument("--cpu-sample", type=int, default=1536, help="oracle sample size (leading block)")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "serving", "weighted", "update", "product"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "serving", "weighted", "update", "product",
+                                                            "mma-probe"],
                    help="single: the n=8192 graphs (default); batched: 4096 graphs n~U[32,512] in one launch; "
                         "serving: a Poisson stream of requests over a pool of graphs; "
                         "weighted: n=32768 king grid, split inverse + 1024 goal rows + greedy; "
@@ -999,15 +1010,60 @@ def run_product(args):
                      "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
                      # DRAM bytes of this launch (read + write) from an ncu capture of this
                      # kernel build on this graph; stale once either changes
-                     "traffic": 2.345e9 if (args.product_graph == "er" and n == 4096 and st["slices"] == 9) else None,
+                     "traffic": PRODUCT_TRAFFIC if (args.product_graph == "er" and n == 4096 and st["slices"] == 9) else None,
                      "traffic_unit": "B", "peak_source": f"{pk_kind} bf16 burst (cuBLAS)",
                      "work": "issued BF16 digit products, s(s+1)/2 x 2MNK"},
     }
     print(json.dumps(line), flush=True)
 
 
+def run_mma_probe(args):
+    """The tensor-core rate of the split path's BF16 digit products with nothing else in the loop
+    (rd_probe_mma): one CTA per SM issuing 128 x 128 x 16 MMAs from shared memory back to back,
+    against the measured cuBLAS BF16 peak; the INT8 kind is reported as unavailable on sm_103a."""
+    import torch
+
+    from paper_2308_07403_gb300 import build, rd
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    rd.load()
+    rd.rd_probe_mma(0, 200)  # warm-up (clocks up, module loaded)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    res = {}
+    runs = [rd.rd_probe_mma(0, 8000) for _ in range(max(1, args.steps))]
+    res["bf16"] = {"tera_ops_per_s": max(r for r, _ in runs), "seconds": min(s for _, s in runs)}
+    try:
+        rd.rd_probe_mma(1, 1)
+        int8 = "measured"
+    except rd.RDError as ex:
+        int8 = str(ex)
+    clk = clocks.stop()
+    pk, pk_kind = peaks()
+    line = {
+        "metric": "tcgen05 BF16 MMA rate (128 x 128 x 16, operands in shared memory, every SM)",
+        "value": res["bf16"]["tera_ops_per_s"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": res["bf16"]["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic (zero operands)",
+        "config": {"workload": "152 CTAs x 8000 x 64 MMAs of 128 x 128 x 16, one thread issuing per SM, "
+                               "a commit and a bounded wait per 64"},
+        "int8": int8,
+        "bf16_of_measured_cublas_burst": res["bf16"]["tera_ops_per_s"] / pk["bf16_tflops"], "peak_source": pk_kind,
+        "clocks": clk, "gpu_launches": 1 + max(1, args.steps),
+        "roofline": {"kernel": "probe_mma_kernel", "bound": "tensor", "achieved": res["bf16"]["tera_ops_per_s"],
+                     "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": res["bf16"]["tera_ops_per_s"] / pk["bf16_tflops"], "traffic": None},
+        "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "mma-probe":
+        run_mma_probe(args)
+        return
     if args.workload == "product":
         run_product(args)
         return
@@ -1098,8 +1154,12 @@ def main():
         roof = {"kernel": "split_gemm_kernel", "bound": "tensor",
                 "peak_source": f"{pk_kind} bf16 sustained (cuBLAS, seconds-long loop)",
                 "work": "issued BF16 digit products, s(s+1)/2 x 2MNK per split product"}
+    split_line = args.precision == "split" and n == 8192 and args.slices == 0
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                 "frac": (achieved / peak) if achieved else None, "traffic": None,
+                 "frac": (achieved / peak) if achieved else None,
+                 "traffic": SPLIT_TRAFFIC_PER_LAUNCH if split_line else None,
+                 "traffic_algorithmic": SPLIT_ALGORITHMIC_BYTES_PER_LAUNCH if split_line else None,
+                 "traffic_unit": "B per launch",
                  "launches": prof_n, "kernel_ms": prof_ms,
                  "kernel_share_of_step": prof_ms / total_ms if total_ms else None})
     slices_used = st1["slices"]

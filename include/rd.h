@@ -232,6 +232,15 @@ const char* rd_status_string(rd_status s);
 /* Free the handle and its device memory (synchronises its stream).  NULL is ignored. */
 void rd_destroy(rd_handle h);
 
+/* The tensor-core rate of the split path's digit products on the current device, with nothing else
+ * in the loop (the ceiling the split GEMM is held against; no counterpart in the paper): one CTA
+ * per SM issues 128 x 128 x 16 tcgen05 MMAs (kind 0: BF16 inputs, FP32 accumulation) from shared
+ * memory back to back, `batches` x 64 per SM; *tera_ops receives the rate (10^12 flop/s) and
+ * *seconds the device time.  Kind 1 (signed 8-bit digits, tcgen05.mma.kind::i8) returns
+ * RD_ERR_UNSUPPORTED: the instruction does not exist for sm_103a.  Every wait is bounded
+ * (RD_ERR_TIMEOUT).  Synchronises the device. */
+rd_status rd_probe_mma(int32_t kind, int32_t batches, double* tera_ops, double* seconds);
+
 /* Largest n accepted by rd_apsp_noalloc. */
 #define RD_NOALLOC_MAX_N 512
 

@@ -55,6 +55,8 @@ _SIGS = {
     "rd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rd_destroy": (None, [_P]),
     "rd_apsp_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, _P, _P]),
+    "rd_probe_mma": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]),
     "rd_update_edge": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P, _P]),
     "rd_batch_create": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(_P)]),
     "rd_batch_offsets": (ctypes.c_int, [_P, _P]),
@@ -289,6 +291,13 @@ def rd_apsp_noalloc(A, n: int, gamma: float, D, stream_ptr: int = 0):
     pa, ka = _ptr(A)
     pd, kd = _ptr(D)
     _check(load().rd_apsp_noalloc(pa, int(n), float(gamma), pd, ctypes.c_void_p(int(stream_ptr))))
+
+
+def rd_probe_mma(kind: int, batches: int = 4000):
+    """(tera-ops/s, seconds) of back-to-back tcgen05 MMAs: kind 0 BF16 (K = 16), 1 INT8 (K = 32)."""
+    r, s = ctypes.c_double(), ctypes.c_double()
+    _check(load().rd_probe_mma(int(kind), int(batches), ctypes.byref(r), ctypes.byref(s)))
+    return r.value, s.value
 
 
 # ---- convenience wrapper ---------------------------------------------------------------------
