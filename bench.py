@@ -44,7 +44,7 @@ METRIC = "n=8192 R-distance APSP time/TFLOPS, split-prec vs FP64 (D exact); p50/
 SPLIT_TRAFFIC_PER_LAUNCH = 0.3552e9
 # DRAM bytes of the inverse product launch of `--workload product` (ER n = 4096, 9 digits, CTA pairs),
 # one one-pass ncu capture (profiles/split_gemm_pairs_inverse_product_n4096.md); None until taken
-PRODUCT_TRAFFIC = None
+PRODUCT_TRAFFIC = 1.0349e9
 SPLIT_ALGORITHMIC_BYTES_PER_LAUNCH = 0.1389e9
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
