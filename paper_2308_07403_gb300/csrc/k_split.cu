@@ -246,6 +246,23 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// the same two copies with the destination and the barrier as shared-memory addresses
+__device__ __forceinline__ void tma_load_2d_pair_u32(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
+                                                     int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(dst), "l"((uint64_t)map), "r"(bar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_u32(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -294,6 +311,17 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar, uint16_t mask = 3) {
   else
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void umma_commit_u32(uint32_t bar, uint16_t mask = 3) {
+  if (PAIR)
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // tcgen05.ld of 8 columns without the wait; tmem_wait_ld(r) then waits for every prior load of this
@@ -724,9 +752,20 @@ __global__ void __launch_bounds__(THREADS, 1)
   const unsigned long long deadline = globaltimer() + WAIT_NS;
   const int nloop = *abort_flag ? 0 : nchunks;
 
+  // The producer and the MMA issuer are single threads whose every instruction sits between two
+  // tensor-core instructions: their loops keep the per-item work to a few independent integer
+  // operations (no divisions; smem addresses, descriptors and barrier addresses as a base plus
+  // compile-time offsets; items of a stage unrolled).  A single issuing thread runs its dependent
+  // scalar code at a few cycles per instruction, and an M = 128, N = 128, K = 16 MMA takes 64.
+  const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
+  const uint32_t full0 = smem_u32(full), empty0 = smem_u32(empty);
   if (warp == 0) {
     if (lane == 0) {  // TMA producer (in each CTA of a pair: its own A rows and half of B)
-      int it = 0;
+      const uint32_t full_lead0 = PAIR ? mapa_shared(full, 0) : full0;  // the pair leader's full[0]
+      const int b_col = n0 + (PAIR ? (int)rank * (TN / 2) : 0);
+      const int a_row = PAIR ? m_cta : m0;
+      int st = 0;
+      uint32_t phase = 0;  // of the current pass over the stages
       bool ok = true;
       for (int c = 0; c < nloop && ok; ++c) {
         const int kc0 = max(kbeg, (cbeg + c) * KP);
@@ -734,10 +773,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int g = 0; g < s && ok; ++g) {
           // the group's items (pair pa, K step ks) in order, R::ITEMS to a stage
           const int items = (g + 1) * ksteps;
-          for (int i0 = 0; i0 < items; i0 += R::ITEMS, ++it) {
-            const int st = it % STAGES;
-            const uint32_t round = (uint32_t)(it / STAGES);
-            if (!mbar_wait<false, PAIR>(&empty[st], (round + 1) & 1u, abort_flag, deadline)) {
+          int pa = 0, ks = 0;
+          int ya = (a_plane0 + 0) * p.ma_pad + a_row, yb = (b_plane0 + g) * p.nb_pad + b_col;
+          for (int i0 = 0; i0 < items; i0 += R::ITEMS) {
+            if (!mbar_wait<false, PAIR>(&empty[st], phase ^ 1u, abort_flag, deadline)) {
               ok = false;
               break;
             }
@@ -745,18 +784,30 @@ __global__ void __launch_bounds__(THREADS, 1)
             // the leader's barrier counts the bytes of both CTAs (a peer's copies may land first:
             // the transaction count goes negative until the leader's expect)
             if (leader) mbar_arrive_expect_tx(&full[st], cnt * (PAIR ? 2 : 1) * (R::A_BYTES + R::B_BYTES));
-            for (int u = 0; u < cnt; ++u) {
-              const int pa = (i0 + u) / ksteps, ks = (i0 + u) % ksteps, slot = st * R::ITEMS + u;
-              const int ka = kc0 + ks * TK;
-              if (PAIR) {
-                const uint32_t bar = mapa_shared(&full[st], 0);
-                tma_load_2d_pair(sA + slot * R::A_BYTES, &tmA, bar, ka, (a_plane0 + pa) * p.ma_pad + m_cta);
-                tma_load_2d_pair(sB + slot * R::B_BYTES, &tmB, bar, ka,
-                                 (b_plane0 + g - pa) * p.nb_pad + n0 + (int)rank * (TN / 2));
-              } else {
-                tma_load_2d(sA + slot * R::A_BYTES, &tmA, &full[st], ka, (a_plane0 + pa) * p.ma_pad + m0);
-                tma_load_2d(sB + slot * R::B_BYTES, &tmB, &full[st], ka, (b_plane0 + g - pa) * p.nb_pad + n0);
+            const uint32_t bar = (PAIR ? full_lead0 : full0) + (uint32_t)(st * 8);
+            const uint32_t da = sA0 + (uint32_t)(st * R::ITEMS * R::A_BYTES), db = sB0 + (uint32_t)(st * R::ITEMS * R::B_BYTES);
+#pragma unroll
+            for (int u = 0; u < R::ITEMS; ++u) {
+              if (u < cnt) {
+                const int ka = kc0 + ks * TK;
+                if (PAIR) {
+                  tma_load_2d_pair_u32(da + u * R::A_BYTES, &tmA, bar, ka, ya);
+                  tma_load_2d_pair_u32(db + u * R::B_BYTES, &tmB, bar, ka, yb);
+                } else {
+                  tma_load_2d_u32(da + u * R::A_BYTES, &tmA, bar, ka, ya);
+                  tma_load_2d_u32(db + u * R::B_BYTES, &tmB, bar, ka, yb);
+                }
+                if (++ks == ksteps) {  // next digit pair (pa + 1, g - pa - 1)
+                  ks = 0;
+                  ++pa;
+                  ya += p.ma_pad;
+                  yb -= p.nb_pad;
+                }
               }
+            }
+            if (++st == STAGES) {
+              st = 0;
+              phase ^= 1u;
             }
           }
         }
@@ -764,7 +815,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0 && leader) {  // MMA issuer (a pair's leader issues for both CTAs)
-      int it = 0, gi = 0;
+      // descriptors of slot 0 of A and B; a slot, a K = 16 step, adds its byte offset / 16 (the
+      // start-address field holds shared-memory addresses below 256 KiB: no carry out of it)
+      const uint64_t dA0 = sdesc_sw128(sA0), dB0 = sdesc_sw128(sB0);
+      int st = 0, gi = 0;
+      uint32_t phase = 0;
       bool ok = true;
       for (int c = 0; c < nloop && ok; ++c) {
         const int kc0 = max(kbeg, (cbeg + c) * KP);
@@ -780,25 +835,31 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t dt = tmem + (uint32_t)(buf * TN);
           uint32_t acc = 0;
           const int items = (g + 1) * ksteps;
-          for (int i0 = 0; i0 < items; i0 += R::ITEMS, ++it) {
-            const int st = it % STAGES;
-            const uint32_t round = (uint32_t)(it / STAGES);
-            if (!mbar_wait<true, PAIR>(&full[st], round & 1u, abort_flag, deadline)) {
+          for (int i0 = 0; i0 < items; i0 += R::ITEMS) {
+            if (!mbar_wait<true, PAIR>(&full[st], phase, abort_flag, deadline)) {
               ok = false;
               break;
             }
             tc_fence_after();
             const int cnt = min(R::ITEMS, items - i0);
-            for (int u = 0; u < cnt; ++u) {
-              const uint32_t a_addr = smem_u32(sA + (st * R::ITEMS + u) * R::A_BYTES);
-              const uint32_t b_addr = smem_u32(sB + (st * R::ITEMS + u) * R::B_BYTES);
+            const uint64_t da = dA0 + (uint64_t)((st * R::ITEMS * R::A_BYTES) >> 4);
+            const uint64_t db = dB0 + (uint64_t)((st * R::ITEMS * R::B_BYTES) >> 4);
 #pragma unroll
-              for (int k16 = 0; k16 < TK / 16; ++k16) {
-                umma_bf16<PAIR>(dt, sdesc_sw128(a_addr + k16 * 32), sdesc_sw128(b_addr + k16 * 32), acc);
-                acc = 1;
+            for (int u = 0; u < R::ITEMS; ++u) {
+              if (u < cnt) {
+#pragma unroll
+                for (int k16 = 0; k16 < TK / 16; ++k16) {
+                  umma_bf16<PAIR>(dt, da + (uint64_t)((u * R::A_BYTES + k16 * 32) >> 4),
+                                  db + (uint64_t)((u * R::B_BYTES + k16 * 32) >> 4), acc);
+                  acc = 1;
+                }
               }
             }
-            umma_commit<PAIR>(&empty[st]);  // (a pair: both CTAs' stage barriers)
+            umma_commit_u32<PAIR>(empty0 + (uint32_t)(st * 8));  // (a pair: both CTAs' stage barriers)
+            if (++st == STAGES) {
+              st = 0;
+              phase ^= 1u;
+            }
           }
           if (ok) umma_commit<PAIR>(&acc_full[buf]);
         }
