@@ -25,12 +25,12 @@
 //
 // Kernel structure (one CTA per 128 x 128 output tile, 320 threads, 512 tensor-memory columns; with
 // 256-wide chunks a cluster of two CTAs per 256 x 128 tile, tcgen05 cta_group::2, see Ring):
-//   warp 0      TMA producer: digit tiles A_p[128 x 64] and B_q[128 x 64] (a pair: each CTA its
-//               half of B, 64 x 64) into a 3-stage ring of two (pair, K step) items per stage (a
-//               pair: 2 stages of four)
-//   warp 1      TMEM allocator and MMA issuer (one thread): tcgen05.mma.kind::f16, M=N=128,
-//               K=16, 8 MMAs per wait; group accumulators double-buffered in tensor memory
-//               (columns 0..255)
+//   warp 0      TMA producer (one elected lane issues): digit tiles A_p[128 x 64] and B_q[128 x 64]
+//               (a pair: each CTA its half of B, 64 x 64) into a 3-stage ring of two (pair, K step)
+//               items per stage (a pair: 2 stages of four)
+//   warp 1      TMEM allocator and MMA issuer (one elected lane issues): tcgen05.mma.kind::f16,
+//               M=N=128 (a pair: M=256), K=16, 8 MMAs per wait (a pair: 16); group accumulators
+//               double-buffered in tensor memory (columns 0..255)
 //   warps 2..9  epilogue: tcgen05.ld of each group sum, float-float accumulation with the low
 //               words and each chunk's per-entry scale in tensor memory (columns 256..511),
 //               final FP64 scale, the C update, a split-K partial, or the fused decode
@@ -141,11 +141,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -204,6 +199,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return true;
 }
 
+// The same wait by every lane of a warp (each lane observes the phase itself, so whichever lane is
+// elected to issue next has seen it); the outcome is the same in every lane.
+template <bool NOSLEEP = false, bool CLUSTER = false>
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                               unsigned long long deadline) {
+  const bool ok = mbar_wait<NOSLEEP, CLUSTER>(bar, parity, abort_flag, deadline);
+  return __all_sync(0xffffffffu, ok);
+}
+
 // ---- CTA pairs (a cluster of two CTAs sharing each MMA: tcgen05 cta_group::2) ------------------
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -229,37 +233,22 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
 
-// TMA tile load into this CTA's shared memory whose completion (bytes) is signalled on the pair
-// leader's barrier (bar_cluster: a shared::cluster address, possibly in the peer CTA)
-__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int x, int y) {
+// TMA tile loads (whole warp, the elected lane issues).  The pair form writes this CTA's shared memory
+// and signals the pair leader's barrier (bar_cluster: a shared::cluster address, possibly in the
+// peer CTA).
+__device__ __forceinline__ void tma_load_2d_pair_w(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster, int x, int y) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(bar_cluster), "r"(x), "r"(y)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// the same two copies with the destination and the barrier as shared-memory addresses
-__device__ __forceinline__ void tma_load_2d_pair_u32(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
-                                                     int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n}\n"
       ::"r"(dst), "l"((uint64_t)map), "r"(bar_cluster), "r"(x), "r"(y)
       : "memory");
 }
 
-__device__ __forceinline__ void tma_load_2d_u32(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+__device__ __forceinline__ void tma_load_2d_w(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n}\n"
+      ::"r"(dst), "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
 
@@ -278,50 +267,54 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
   return d;
 }
 
-// D (tensor memory) (+)= A B^T for one K = 16 step.  PAIR: M = 256 issued by the leader CTA of a
+// The issuing instructions are executed by every lane of a converged warp, and the lane that
+// elect.sync picks issues the one instruction: the addresses and descriptors are then values of a
+// converged warp rather than of one divergent lane.
+//
+// umma_bf16_w: D (tensor memory) (+)= A B^T for one K = 16 step.  PAIR: M = 256 issued by the leader CTA of a
 // pair; A's rows 0..127 come from the leader's shared memory and 128..255 from the peer's, B's rows
 // (the N = 128 columns) 0..63 from the leader's and 64..127 from the peer's (same offsets in both),
 // and each CTA's tensor memory receives its 128 rows.
 template <bool PAIR>
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void umma_bf16_w(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
   if (PAIR)
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d_tmem),
+        "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+        " @e tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(Ring<true>::IDESC), "r"(accumulate)
         : "memory");
   else
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d_tmem),
+        "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(Ring<false>::IDESC), "r"(accumulate)
         : "memory");
 }
 
-// Arrive (once) on `bar` when every MMA issued so far has completed.  PAIR: on the barrier at the
-// same offset in each CTA of the pair named by `mask` (bit r = CTA rank r).
+// Arrive (once) on the barrier at shared address `bar` when every MMA issued so far has completed.
+// PAIR: on the barrier at the same offset in each CTA of the pair named by `mask` (bit r = CTA rank r).
 template <bool PAIR>
-__device__ __forceinline__ void umma_commit(uint64_t* bar, uint16_t mask = 3) {
+__device__ __forceinline__ void umma_commit_w(uint32_t bar, uint16_t mask = 3) {
   if (PAIR)
     asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n}\n" ::"r"(
+            bar),
         "h"(mask)
         : "memory");
   else
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(bar)
+        : "memory");
 }
 
-template <bool PAIR>
-__device__ __forceinline__ void umma_commit_u32(uint32_t bar, uint16_t mask = 3) {
-  if (PAIR)
-    asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-        "h"(mask)
-        : "memory");
-  else
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+__device__ __forceinline__ void mbar_arrive_expect_tx_w(uint32_t bar, uint32_t bytes) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n @e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n}\n" ::"r"(
+          bar),
+      "r"(bytes)
+      : "memory");
 }
 
 // tcgen05.ld of 8 columns without the wait; tmem_wait_ld(r) then waits for every prior load of this
@@ -752,15 +745,16 @@ __global__ void __launch_bounds__(THREADS, 1)
   const unsigned long long deadline = globaltimer() + WAIT_NS;
   const int nloop = *abort_flag ? 0 : nchunks;
 
-  // The producer and the MMA issuer are single threads whose every instruction sits between two
-  // tensor-core instructions: their loops keep the per-item work to a few independent integer
-  // operations (no divisions; smem addresses, descriptors and barrier addresses as a base plus
-  // compile-time offsets; items of a stage unrolled).  A single issuing thread runs its dependent
-  // scalar code at a few cycles per instruction, and an M = 128, N = 128, K = 16 MMA takes 64.
+  // The producer and the MMA issuer are whole warps whose every instruction sits between two
+  // tensor-core instructions: one elected lane issues each copy, MMA and commit, and the loops keep
+  // the per-item work to a few independent integer operations (no divisions; smem addresses,
+  // descriptors and barrier addresses as a base plus compile-time offsets; items of a stage
+  // unrolled).  The issuing warp runs its dependent scalar code at a few cycles per instruction,
+  // sharing its SM sub-partition with two epilogue warps, and an M = 128, N = 128, K = 16 MMA takes 64.
   const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
   const uint32_t full0 = smem_u32(full), empty0 = smem_u32(empty);
   if (warp == 0) {
-    if (lane == 0) {  // TMA producer (in each CTA of a pair: its own A rows and half of B)
+    {  // TMA producer, the whole warp (in each CTA of a pair: its own A rows and half of B)
       const uint32_t full_lead0 = PAIR ? mapa_shared(full, 0) : full0;  // the pair leader's full[0]
       const int b_col = n0 + (PAIR ? (int)rank * (TN / 2) : 0);
       const int a_row = PAIR ? m_cta : m0;
@@ -776,14 +770,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           int pa = 0, ks = 0;
           int ya = (a_plane0 + 0) * p.ma_pad + a_row, yb = (b_plane0 + g) * p.nb_pad + b_col;
           for (int i0 = 0; i0 < items; i0 += R::ITEMS) {
-            if (!mbar_wait<false, PAIR>(&empty[st], phase ^ 1u, abort_flag, deadline)) {
+            if (!mbar_wait_warp<false, PAIR>(&empty[st], phase ^ 1u, abort_flag, deadline)) {
               ok = false;
               break;
             }
             const int cnt = min(R::ITEMS, items - i0);
             // the leader's barrier counts the bytes of both CTAs (a peer's copies may land first:
             // the transaction count goes negative until the leader's expect)
-            if (leader) mbar_arrive_expect_tx(&full[st], cnt * (PAIR ? 2 : 1) * (R::A_BYTES + R::B_BYTES));
+            if (leader) mbar_arrive_expect_tx_w(full0 + (uint32_t)(st * 8), cnt * (PAIR ? 2 : 1) * (R::A_BYTES + R::B_BYTES));
             const uint32_t bar = (PAIR ? full_lead0 : full0) + (uint32_t)(st * 8);
             const uint32_t da = sA0 + (uint32_t)(st * R::ITEMS * R::A_BYTES), db = sB0 + (uint32_t)(st * R::ITEMS * R::B_BYTES);
 #pragma unroll
@@ -791,11 +785,11 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (u < cnt) {
                 const int ka = kc0 + ks * TK;
                 if (PAIR) {
-                  tma_load_2d_pair_u32(da + u * R::A_BYTES, &tmA, bar, ka, ya);
-                  tma_load_2d_pair_u32(db + u * R::B_BYTES, &tmB, bar, ka, yb);
+                  tma_load_2d_pair_w(da + u * R::A_BYTES, &tmA, bar, ka, ya);
+                  tma_load_2d_pair_w(db + u * R::B_BYTES, &tmB, bar, ka, yb);
                 } else {
-                  tma_load_2d_u32(da + u * R::A_BYTES, &tmA, bar, ka, ya);
-                  tma_load_2d_u32(db + u * R::B_BYTES, &tmB, bar, ka, yb);
+                  tma_load_2d_w(da + u * R::A_BYTES, &tmA, bar, ka, ya);
+                  tma_load_2d_w(db + u * R::B_BYTES, &tmB, bar, ka, yb);
                 }
                 if (++ks == ksteps) {  // next digit pair (pa + 1, g - pa - 1)
                   ks = 0;
@@ -814,7 +808,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && leader) {  // MMA issuer (a pair's leader issues for both CTAs)
+    if (leader) {  // MMA issuer, the whole warp (a pair's leader issues for both CTAs)
       // descriptors of slot 0 of A and B; a slot, a K = 16 step, adds its byte offset / 16 (the
       // start-address field holds shared-memory addresses below 256 KiB: no carry out of it)
       const uint64_t dA0 = sdesc_sw128(sA0), dB0 = sdesc_sw128(sB0);
@@ -827,7 +821,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int g = 0; g < s && ok; ++g, ++gi) {
           const int buf = gi & 1;
           const uint32_t use = (uint32_t)(gi >> 1);
-          if (!mbar_wait<true, PAIR>(&acc_empty[buf], (use + 1) & 1u, abort_flag, deadline)) {
+          if (!mbar_wait_warp<true, PAIR>(&acc_empty[buf], (use + 1) & 1u, abort_flag, deadline)) {
             ok = false;
             break;
           }
@@ -836,7 +830,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint32_t acc = 0;
           const int items = (g + 1) * ksteps;
           for (int i0 = 0; i0 < items; i0 += R::ITEMS) {
-            if (!mbar_wait<true, PAIR>(&full[st], phase, abort_flag, deadline)) {
+            if (!mbar_wait_warp<true, PAIR>(&full[st], phase, abort_flag, deadline)) {
               ok = false;
               break;
             }
@@ -849,25 +843,25 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (u < cnt) {
 #pragma unroll
                 for (int k16 = 0; k16 < TK / 16; ++k16) {
-                  umma_bf16<PAIR>(dt, da + (uint64_t)((u * R::A_BYTES + k16 * 32) >> 4),
-                                  db + (uint64_t)((u * R::B_BYTES + k16 * 32) >> 4), acc);
+                  umma_bf16_w<PAIR>(dt, da + (uint64_t)((u * R::A_BYTES + k16 * 32) >> 4),
+                                    db + (uint64_t)((u * R::B_BYTES + k16 * 32) >> 4), acc);
                   acc = 1;
                 }
               }
             }
-            umma_commit_u32<PAIR>(empty0 + (uint32_t)(st * 8));  // (a pair: both CTAs' stage barriers)
+            umma_commit_w<PAIR>(empty0 + (uint32_t)(st * 8));  // (a pair: both CTAs' stage barriers)
             if (++st == STAGES) {
               st = 0;
               phase ^= 1u;
             }
           }
-          if (ok) umma_commit<PAIR>(&acc_full[buf]);
+          if (ok) umma_commit_w<PAIR>(smem_u32(&acc_full[buf]));
         }
       }
       // every MMA issued has completed before the tensor memory can be freed (bounded: a second)
-      umma_commit<PAIR>(drain, 1);
+      umma_commit_w<PAIR>(smem_u32(drain), 1);
       volatile int no_abort = 0;
-      mbar_wait<false, false>(drain, 0, &no_abort, globaltimer() + 1000000000ull);
+      mbar_wait_warp<false, false>(drain, 0, &no_abort, globaltimer() + 1000000000ull);
     }
   } else {  // epilogue warps 2..9
     const int ew = warp - 2;
