@@ -75,6 +75,9 @@ def parse():
     p.add_argument("--product-graph", default="er", choices=["er", "grid"],
                    help="product: ER p=0.01 (natural order, 256-wide chunks) or a 4-neighbour grid "
                         "(locality order, 64-wide chunks)")
+    p.add_argument("--split-stats", action="store_true",
+                   help="product: run the diagnostic build with the split GEMM's cycle counters and report "
+                        "where the kernel's time goes (the counters slow the kernel by a few percent)")
     p.add_argument("--weighted-rows", type=int, default=128)
     p.add_argument("--weighted-cols", type=int, default=256)
     p.add_argument("--weighted-frac", type=float, default=0.9, help="weighted: gain as a fraction of the weighted bound")
@@ -944,8 +947,11 @@ def run_product(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    build.build()
-    rd.load()
+    if args.split_stats:
+        rd.load(build.build(stats=True))
+    else:
+        build.build()
+        rd.load()
     n = args.product_n
     if args.product_graph == "grid":
         cols = int(round(n ** 0.5))
@@ -964,6 +970,8 @@ def run_product(args):
         rd.rd_apsp(h, D, None)
     torch.cuda.synchronize()
     rd.rd_set_profiling(h, True)
+    if args.split_stats:
+        rd.rd_split_stats(reset=True)
     st0 = rd.rd_get_stats(h)
     clocks = ClockSampler(local)
     clocks.start()
@@ -976,6 +984,21 @@ def run_product(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    split_stats = None
+    if args.split_stats:
+        c = rd.rd_split_stats()
+        nm, ne = max(c["mma_warps"], 1), max(c["epilogue_warps"], 1)
+        kc = lambda v, w: round(v / w / 1e3, 1)  # thousands of cycles per warp (a tile's CTA or pair)
+        split_stats = {
+            "unit": "thousand SM cycles per tile (per MMA warp; epilogue per CTA)",
+            "mma": {"total": kc(c["mma_cycles"], nm), "wait_accumulator": kc(c["mma_wait_accumulator"], nm),
+                    "wait_operands": kc(c["mma_wait_operands"], nm), "issue": kc(c["mma_issue"], nm),
+                    "tensor_busy_at_64_cycles_per_mma": kc(64 * c["mmas"], nm)},
+            "producer": {"total": kc(c["producer_cycles"], nm), "wait_stage": kc(c["producer_wait_stage"], nm)},
+            "epilogue": {"total": kc(c["epilogue_cycles"], ne), "wait_group": kc(c["epilogue_wait_group"], ne),
+                         "renormalise": kc(c["epilogue_renormalise"], ne)},
+            "groups_per_tile": round(c["groups"] / nm, 1), "mmas_per_tile": round(c["mmas"] / nm, 1),
+            "tiles": c["mma_warps"] // args.steps}
     st = rd.rd_get_stats(h)
     rd.rd_destroy(h)
     import oracle
@@ -1010,10 +1033,14 @@ def run_product(args):
                      "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
                      # DRAM bytes of this launch (read + write) from an ncu capture of this
                      # kernel build on this graph; stale once either changes
-                     "traffic": PRODUCT_TRAFFIC if (args.product_graph == "er" and n == 4096 and st["slices"] == 9) else None,
+                     "traffic": (PRODUCT_TRAFFIC if (args.product_graph == "er" and n == 4096 and st["slices"] == 9
+                                                     and not args.split_stats) else None),
                      "traffic_unit": "B", "peak_source": f"{pk_kind} bf16 burst (cuBLAS)",
                      "work": "issued BF16 digit products, s(s+1)/2 x 2MNK"},
     }
+    if split_stats is not None:
+        line["split_stats"] = split_stats
+        line["config"]["build"] = "diagnostic build with the split GEMM's cycle counters (RD_SPLIT_STATS)"
     print(json.dumps(line), flush=True)
 
 

@@ -241,6 +241,24 @@ void rd_destroy(rd_handle h);
  * (RD_ERR_TIMEOUT).  Synchronises the device. */
 rd_status rd_probe_mma(int32_t kind, int32_t batches, double* tera_ops, double* seconds);
 
+/* Number of counters rd_split_stats can return. */
+#define RD_SPLIT_STATS_N 13
+
+/* Where the split GEMM's time goes (a diagnostic; no counterpart in the paper).  A library built with
+ * the RD_SPLIT_STATS option (build(stats=True)) sums clock cycles of the kernel's roles over every
+ * launch that carries the fused decode (the inverse product Y = U^-1 L^-1); the first n (1..13)
+ * counters are copied to out (host memory) and, if reset is non-zero, set to zero:
+ *   0 MMA-warp cycles, of which 1 waiting for a free accumulator buffer, 2 waiting for a full
+ *   operand stage, 3 issuing (from a stage's arrival to its commit);
+ *   4 producer-warp cycles, of which 5 waiting for a free stage;
+ *   6 epilogue cycles (one warp per CTA), of which 7 waiting for a group sum, 8 in the per-chunk
+ *   renormalisation;
+ *   9 MMA warps counted, 10 epilogue warps counted, 11 digit groups, 12 MMA instructions issued
+ *   (for a CTA pair, its leader's MMA and producer warps only).
+ * The counters cost the kernel registers and a few percent of its speed, so the default build has
+ * none: there the call returns RD_ERR_UNSUPPORTED.  Synchronises the device. */
+rd_status rd_split_stats(uint64_t* out, int32_t n, int32_t reset);
+
 /* Largest n accepted by rd_apsp_noalloc. */
 #define RD_NOALLOC_MAX_N 512
 

@@ -27,9 +27,9 @@
 // 256-wide chunks a cluster of two CTAs per 256 x 128 tile, tcgen05 cta_group::2, see Ring):
 //   warp 0      TMA producer (one elected lane issues): digit tiles A_p[128 x 64] and B_q[128 x 64]
 //               (a pair: each CTA its half of B, 64 x 64) into a 3-stage ring of two (pair, K step)
-//               items per stage (a pair: 2 stages of four)
+//               items per stage (a pair: 4 stages of two)
 //   warp 1      TMEM allocator and MMA issuer (one elected lane issues): tcgen05.mma.kind::f16,
-//               M=N=128 (a pair: M=256), K=16, 8 MMAs per wait (a pair: 16); group accumulators
+//               M=N=128 (a pair: M=256), K=16, 8 MMAs per wait; group accumulators
 //               double-buffered in tensor memory (columns 0..255)
 //   warps 2..9  epilogue: tcgen05.ld of each group sum, float-float accumulation with the low
 //               words and each chunk's per-entry scale in tensor memory (columns 256..511),
@@ -93,18 +93,19 @@ constexpr uint32_t idesc(int m) {
 // (PAIR = true, tcgen05 cta_group::2): each CTA holds its own 128 rows of A (16 KiB) and half of
 // the B tile (64 rows, 8 KiB) per item, so an item costs each CTA 24 KiB of L2 reads instead of
 // 32 KiB and one MMA instruction does twice the work; the same 192 KiB then hold 2 stages of 4
-// items.  Measured on the inverse product (256-wide chunks): 4 items x 2 stages 5 % faster than the
-// one-CTA kernel (n = 4096 and 8192), 2 items x 4 stages and 3 x 2 slower; with 64-wide chunks,
-// whose groups fill few items, the pair kernel is 2 % slower, so it runs for 256-wide chunks only.
+// items.  Measured on the inverse product (256-wide chunks) with the issue loops run by whole warps:
+// 2 items x 4 stages 7 % faster than 4 x 2 at n = 8192 (a stage's copies have three stages of MMAs
+// to land in), 1 x 8 slower (a wait per 4 MMAs); for the one-CTA kernel with 64-wide chunks 2 x 3
+// beats 3 x 2 and 1 x 6.  With 64-wide chunks, whose groups fill few items, the pair kernel is 2 %
+// slower, so it runs for 256-wide chunks only.
 // After the ring: the barriers (256 B), the chunk exponents of the tile's columns (2 x TN ints)
 // and the per-entry reference exponents (TM x TN int16).
 template <bool PAIR>
 struct Ring {
-  // (digit pair, K step) items per stage: each item is TK / 16 = 4 MMAs, and the MMA thread waits
-  // once per stage (a wait costs the tensor pipe about as much whatever the MMA size, so the pair
-  // kernel's 4 items of M = 256 MMAs give 1024 tensor cycles per wait against 512)
-  static constexpr int ITEMS = PAIR ? 4 : 2;
-  static constexpr int STAGES = PAIR ? 2 : 3;
+  // (digit pair, K step) items per stage: each item is TK / 16 = 4 MMAs, and the MMA warp waits
+  // once per stage
+  static constexpr int ITEMS = 2;
+  static constexpr int STAGES = PAIR ? 4 : 3;
   static constexpr int SLOTS = STAGES * ITEMS;
   static constexpr int A_BYTES = TILE_BYTES;
   static constexpr int B_BYTES = PAIR ? TILE_BYTES / 2 : TILE_BYTES;
@@ -114,7 +115,8 @@ struct Ring {
   static constexpr size_t SMEM = 1024 + REF_OFFSET + TM * TN * 2;
   static constexpr uint32_t IDESC = idesc(PAIR ? 2 * TM : TM);
 };
-static_assert((2 * 4 + 2 * 2 + 1) * 8 + 8 <= 256, "barriers, tensor-memory slot and abort flag");
+static_assert((2 * Ring<true>::STAGES + 2 * 2 + 1) * 8 + 8 <= 256 && (2 * Ring<false>::STAGES + 2 * 2 + 1) * 8 + 8 <= 256,
+              "barriers, tensor-memory slot and abort flag");
 static_assert(Ring<false>::SMEM <= 232448 && Ring<true>::SMEM <= 232448, "shared memory of one CTA");
 static_assert(Ring<true>::A_BYTES % 1024 == 0 && Ring<true>::B_BYTES % 1024 == 0, "128-byte swizzle atoms");
 
@@ -124,6 +126,17 @@ constexpr int16_t REF_NONE = -32768;                                    // no ch
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t TMEM_LO = 2 * TN;
 constexpr uint32_t TMEM_SCALE = 3 * TN;
+
+#ifdef RD_SPLIT_STATS
+// Cycle counters of the split GEMM's roles (a build with RD_SPLIT_STATS only), summed over the
+// launches that carry the fused decode (the inverse product Y = U^-1 L^-1), read by rd_split_stats:
+//  0 MMA-warp cycles, 1 of them waiting for a free accumulator buffer, 2 waiting for a full operand
+//  stage, 3 issuing (from a stage's arrival to its commit); 4 producer-warp cycles, 5 of them
+//  waiting for a free stage; 6 epilogue cycles (warp 2 of each CTA), 7 of them waiting for a group
+//  sum, 8 in the per-chunk renormalisation; 9 MMA warps counted, 10 epilogue warps counted,
+//  11 digit groups, 12 MMA instructions.  (Pair leaders only for the MMA and producer warps.)
+__device__ unsigned long long g_split_stats[16];
+#endif
 
 // ---- PTX wrappers -----------------------------------------------------------------------
 
@@ -761,6 +774,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       int st = 0;
       uint32_t phase = 0;  // of the current pass over the stages
       bool ok = true;
+#ifdef RD_SPLIT_STATS
+      const unsigned long long pt0 = clock64();
+      unsigned long long pwait = 0;
+#endif
       for (int c = 0; c < nloop && ok; ++c) {
         const int kc0 = max(kbeg, (cbeg + c) * KP);
         const int ksteps = (min(kend, (cbeg + c + 1) * KP) - kc0) / TK;
@@ -770,10 +787,16 @@ __global__ void __launch_bounds__(THREADS, 1)
           int pa = 0, ks = 0;
           int ya = (a_plane0 + 0) * p.ma_pad + a_row, yb = (b_plane0 + g) * p.nb_pad + b_col;
           for (int i0 = 0; i0 < items; i0 += R::ITEMS) {
+#ifdef RD_SPLIT_STATS
+            const unsigned long long pw0 = clock64();
+#endif
             if (!mbar_wait_warp<false, PAIR>(&empty[st], phase ^ 1u, abort_flag, deadline)) {
               ok = false;
               break;
             }
+#ifdef RD_SPLIT_STATS
+            pwait += clock64() - pw0;
+#endif
             const int cnt = min(R::ITEMS, items - i0);
             // the leader's barrier counts the bytes of both CTAs (a peer's copies may land first:
             // the transaction count goes negative until the leader's expect)
@@ -806,6 +829,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
+#ifdef RD_SPLIT_STATS
+      if (p.D && leader && lane == 0) {
+        atomicAdd(&g_split_stats[4], clock64() - pt0);
+        atomicAdd(&g_split_stats[5], pwait);
+      }
+#endif
     }
   } else if (warp == 1) {
     if (leader) {  // MMA issuer, the whole warp (a pair's leader issues for both CTAs)
@@ -815,25 +844,42 @@ __global__ void __launch_bounds__(THREADS, 1)
       int st = 0, gi = 0;
       uint32_t phase = 0;
       bool ok = true;
+#ifdef RD_SPLIT_STATS
+      const unsigned long long mt0 = clock64();
+      unsigned long long macc = 0, mfull = 0, missue = 0, mmas = 0;
+#endif
       for (int c = 0; c < nloop && ok; ++c) {
         const int kc0 = max(kbeg, (cbeg + c) * KP);
         const int ksteps = (min(kend, (cbeg + c + 1) * KP) - kc0) / TK;
         for (int g = 0; g < s && ok; ++g, ++gi) {
           const int buf = gi & 1;
           const uint32_t use = (uint32_t)(gi >> 1);
+#ifdef RD_SPLIT_STATS
+          const unsigned long long ma0 = clock64();
+#endif
           if (!mbar_wait_warp<true, PAIR>(&acc_empty[buf], (use + 1) & 1u, abort_flag, deadline)) {
             ok = false;
             break;
           }
+#ifdef RD_SPLIT_STATS
+          macc += clock64() - ma0;
+#endif
           tc_fence_after();
           const uint32_t dt = tmem + (uint32_t)(buf * TN);
           uint32_t acc = 0;
           const int items = (g + 1) * ksteps;
           for (int i0 = 0; i0 < items; i0 += R::ITEMS) {
+#ifdef RD_SPLIT_STATS
+            const unsigned long long mf0 = clock64();
+#endif
             if (!mbar_wait_warp<true, PAIR>(&full[st], phase, abort_flag, deadline)) {
               ok = false;
               break;
             }
+#ifdef RD_SPLIT_STATS
+            const unsigned long long mi0 = clock64();
+            mfull += mi0 - mf0;
+#endif
             tc_fence_after();
             const int cnt = min(R::ITEMS, items - i0);
             const uint64_t da = dA0 + (uint64_t)((st * R::ITEMS * R::A_BYTES) >> 4);
@@ -850,6 +896,10 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
             }
             umma_commit_w<PAIR>(empty0 + (uint32_t)(st * 8));  // (a pair: both CTAs' stage barriers)
+#ifdef RD_SPLIT_STATS
+            missue += clock64() - mi0;
+            mmas += (unsigned long long)cnt * (TK / 16);
+#endif
             if (++st == STAGES) {
               st = 0;
               phase ^= 1u;
@@ -858,6 +908,17 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (ok) umma_commit_w<PAIR>(smem_u32(&acc_full[buf]));
         }
       }
+#ifdef RD_SPLIT_STATS
+      if (p.D && lane == 0) {
+        atomicAdd(&g_split_stats[0], clock64() - mt0);
+        atomicAdd(&g_split_stats[1], macc);
+        atomicAdd(&g_split_stats[2], mfull);
+        atomicAdd(&g_split_stats[3], missue);
+        atomicAdd(&g_split_stats[9], 1ull);
+        atomicAdd(&g_split_stats[11], (unsigned long long)gi);
+        atomicAdd(&g_split_stats[12], mmas);
+      }
+#endif
       // every MMA issued has completed before the tensor memory can be freed (bounded: a second)
       umma_commit_w<PAIR>(smem_u32(drain), 1);
       volatile int no_abort = 0;
@@ -898,6 +959,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     int gi = 0;
     bool ok = true;
+#ifdef RD_SPLIT_STATS
+    const unsigned long long et0 = clock64();
+    unsigned long long ewait = 0, eren = 0;
+#endif
     for (int c = 0; c < nloop; ++c) {  // every warp passes the barrier once per chunk
       const int kc = cbeg + c;
       const int cb = c & 1;
@@ -908,6 +973,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
       if (!ok) continue;
       const int erow = eA[(long long)kc * p.ma_pad + row];
+#ifdef RD_SPLIT_STATS
+      const unsigned long long er0 = clock64();
+#endif
       // renormalise the previous chunk's sums, rebase where this chunk's scale exceeds the
       // reference, and set this chunk's per-entry scale
 #pragma unroll
@@ -942,14 +1010,23 @@ __global__ void __launch_bounds__(THREADS, 1)
         tmem_st8(tl + TMEM_SCALE + t * 8, sr);
       }
       tmem_wait_st();
+#ifdef RD_SPLIT_STATS
+      eren += clock64() - er0;
+#endif
       for (int g = 0; g < s; ++g, ++gi) {
         const int buf = gi & 1;
         const uint32_t use = (uint32_t)(gi >> 1);
+#ifdef RD_SPLIT_STATS
+        const unsigned long long ew0 = clock64();
+#endif
         // warp-uniform outcome: the tensor-memory loads below are warp-wide
         if (!__all_sync(0xffffffffu, mbar_wait<false, PAIR>(&acc_full[buf], use & 1u, abort_flag, deadline))) {
           ok = false;
           break;
         }
+#ifdef RD_SPLIT_STATS
+        ewait += clock64() - ew0;
+#endif
         tc_fence_after();
         const float cg = __int_as_float((127 + ACC_OFF - SIGMA * (g + 2)) << 23);  // 2^(ACC_OFF - 7 (g + 2))
 #pragma unroll
@@ -986,6 +1063,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         tmem_wait_st();
       }
     }
+#ifdef RD_SPLIT_STATS
+    if (p.D && warp == 2 && lane == 0) {
+      atomicAdd(&g_split_stats[6], clock64() - et0);
+      atomicAdd(&g_split_stats[7], ewait);
+      atomicAdd(&g_split_stats[8], eren);
+      atomicAdd(&g_split_stats[10], 1ull);
+    }
+#endif
     // final values, 16 columns at a time (the tensor-memory loads are warp-wide: outside any
     // per-lane condition)
     const bool store = ok && !*abort_flag && s > 0;
@@ -1673,4 +1758,29 @@ cudaError_t rd_goal_split(rd_ctx* h, const int32_t* dgoals, int k, double* out, 
   return split_gemm(h, full(h->dR, N, RD_MAX_GOALS, (int)N), tri(h->dT, N, (int)N, RD_TRI_LOWER_UNIT), RD_MAX_GOALS,
                     (int)N, (int)N, 1.0, 0.0, out, h->n, k, h->n, nullptr, nullptr, RD_MAX_GOALS * Nd * (Nd + 1),
                     s, nullptr, h->ordered ? h->dOrd : nullptr, true);
+}
+
+// Cycle counters of the split GEMM's roles (the decode products since the last reset); a library built
+// without RD_SPLIT_STATS has none.
+extern "C" rd_status rd_split_stats(uint64_t* out, int32_t n, int32_t reset) {
+  if (!out || n < 1 || n > 16) {
+    rd_record_error("rd_split_stats: out not NULL, 1 <= n <= 16");
+    return RD_ERR_ARG;
+  }
+#ifdef RD_SPLIT_STATS
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, g_split_stats, sizeof(uint64_t) * (size_t)n);
+  if (e == cudaSuccess && reset) {
+    const unsigned long long z[16] = {0};
+    e = cudaMemcpyToSymbol(g_split_stats, z, sizeof(z));
+  }
+  if (e != cudaSuccess) {
+    rd_record_error(std::string("rd_split_stats: ") + cudaGetErrorString(e));
+    return RD_ERR_CUDA;
+  }
+  return RD_OK;
+#else
+  rd_record_error("rd_split_stats: this library was built without RD_SPLIT_STATS (build(stats=True))");
+  return RD_ERR_UNSUPPORTED;
+#endif
 }

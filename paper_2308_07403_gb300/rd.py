@@ -57,6 +57,7 @@ _SIGS = {
     "rd_apsp_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, _P, _P]),
     "rd_probe_mma": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]),
+    "rd_split_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32, ctypes.c_int32]),
     "rd_update_edge": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P, _P]),
     "rd_batch_create": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(_P)]),
     "rd_batch_offsets": (ctypes.c_int, [_P, _P]),
@@ -298,6 +299,19 @@ def rd_probe_mma(kind: int, batches: int = 4000):
     r, s = ctypes.c_double(), ctypes.c_double()
     _check(load().rd_probe_mma(int(kind), int(batches), ctypes.byref(r), ctypes.byref(s)))
     return r.value, s.value
+
+
+SPLIT_STATS_N = 13
+SPLIT_STATS_FIELDS = ("mma_cycles", "mma_wait_accumulator", "mma_wait_operands", "mma_issue",
+                      "producer_cycles", "producer_wait_stage", "epilogue_cycles", "epilogue_wait_group",
+                      "epilogue_renormalise", "mma_warps", "epilogue_warps", "groups", "mmas")
+
+
+def rd_split_stats(reset: bool = False):
+    """The split GEMM's role cycle counters as a dict (a library built with stats=True only)."""
+    buf = (ctypes.c_uint64 * SPLIT_STATS_N)()
+    _check(load().rd_split_stats(buf, SPLIT_STATS_N, 1 if reset else 0))
+    return dict(zip(SPLIT_STATS_FIELDS, (int(v) for v in buf)))
 
 
 # ---- convenience wrapper ---------------------------------------------------------------------
