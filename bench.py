@@ -41,10 +41,10 @@ METRIC = "n=8192 R-distance APSP time/TFLOPS, split-prec vs FP64 (D exact); p50/
 # algorithmic bytes per launch (the digit tiles each product needs at least once plus its outputs,
 # same launches); profiles/launches_apsp_split_n8192.md gives the command and the model.  To be
 # captured again whenever split_gemm_kernel changes.
-SPLIT_TRAFFIC_PER_LAUNCH = 0.3562e9
+SPLIT_TRAFFIC_PER_LAUNCH = 0.3612e9
 # DRAM bytes of the inverse product launch of `--workload product` (ER n = 4096, 9 digits, CTA pairs),
 # one one-pass ncu capture (profiles/split_gemm_pairs_inverse_product_n4096.md); None until taken
-PRODUCT_TRAFFIC = 1.0335e9
+PRODUCT_TRAFFIC = 1.0339e9
 SPLIT_ALGORITHMIC_BYTES_PER_LAUNCH = 0.1389e9
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
