@@ -60,7 +60,8 @@ def parse():
     p.add_argument("--slices", type=int, default=0)
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--goals", type=int, default=64)
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=6,
+                   help="end-to-end steps (host buffers); 6 = each of the six graphs once, the mix of the timed steps")
     p.add_argument("--verify", type=int, default=1, help="hash D of every graph against the oracle's")
     p.add_argument("--cpu-sample", type=int, default=1536, help="oracle sample size (leading block)")
     p.add_argument("--workload", default="single", choices=["single", "batched", "serving", "weighted", "update", "product",
