@@ -234,7 +234,9 @@ def time_path(rd, h, step, first, steps, warmup, stream, local, world, dist, pro
     torch.cuda.synchronize()
     st0 = rd.rd_get_stats(h)
     if profile:
-        rd.rd_set_profiling(h, True)
+        # (2: events around the split GEMM alone, whose roofline the line reports; True: every
+        # dense-contraction kernel)
+        rd.rd_set_profiling(h, profile)
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
@@ -1152,7 +1154,8 @@ def main():
 
     # ---- the headline path
     rd.rd_set_precision(h, modes[args.precision], args.slices)
-    per_step, total_ms, st0, st1, clk = time_path(rd, h, step, 0, args.steps, args.warmup, stream, local, world, dist)
+    per_step, total_ms, st0, st1, clk = time_path(rd, h, step, 0, args.steps, args.warmup, stream, local, world, dist,
+                                                  profile=2 if args.precision == "split" else True)
     ms_step = total_ms / args.steps
     flop_step = 2.0 * n ** 3
     # device ms of each graph's steps (step i runs graph i mod 6), median per graph

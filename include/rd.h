@@ -209,10 +209,12 @@ rd_status rd_greedy_walk(rd_handle h, const int32_t* next, int32_t k, const int3
  * resident Y.  Synchronises. */
 rd_status rd_update_edge(rd_handle h, int32_t i, int32_t j, int32_t present, float w, int32_t* D, double* Y);
 
-/* Turn the per-kernel profile on (1) or off (0); either way its counters restart at zero.
- * With the profile on, every launch of the dense-contraction (GEMM) kernels is bracketed by a
- * pair of CUDA events on the handle's stream and its algorithmic flop count is accumulated;
- * rd_get_stats reports the totals (prof_launches, prof_ms, prof_flops). */
+/* Turn the per-kernel profile on (1: every dense-contraction kernel; 2: the split GEMM alone) or
+ * off (0); either way its counters restart at zero (another value: RD_ERR_ARG).  With the profile
+ * on, every launch of the profiled kernels is bracketed by a pair of CUDA events on the handle's
+ * stream and its algorithmic flop count is accumulated; rd_get_stats reports the totals
+ * (prof_launches, prof_ms, prof_flops, and the split GEMM's prof_split_*).  Mode 2 leaves the
+ * small FP64 products of the split path's recursion without events. */
 rd_status rd_set_profiling(rd_handle h, int32_t on);
 
 /* Wait for the handle's stream and return the device status (RD_OK or RD_ERR_NUMERIC). */

@@ -479,9 +479,14 @@ double event_ms(rd_ctx* h, int slot) {
 
 void rd_record_error(const std::string& msg) { g_create_err = msg; }
 
+// profile mode 1: every dense-contraction kernel; 2: the split GEMM alone
+static bool prof_wanted(const rd_ctx* h, int kind) {
+  return h->prof_on != 0 && kind != RD_PROF_NONE && (h->prof_on == 1 || kind == RD_PROF_SPLIT);
+}
+
 cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, int kind) {
   h->launches++;
-  if (!h->prof_on || kind == RD_PROF_NONE) return cudaSuccess;
+  if (!prof_wanted(h, kind)) return cudaSuccess;
   if (h->prof_used == rd_ctx::kProfPairs) {
     cudaError_t e = rd_prof_collect(h);
     if (e != cudaSuccess) return e;
@@ -490,7 +495,7 @@ cudaError_t rd_prof_begin(rd_ctx* h, cudaStream_t s, int kind) {
 }
 
 cudaError_t rd_prof_end(rd_ctx* h, cudaStream_t s, int kind, double flops) {
-  if (!h->prof_on || kind == RD_PROF_NONE) return cudaSuccess;
+  if (!prof_wanted(h, kind)) return cudaSuccess;
   cudaError_t e = cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
   if (e != cudaSuccess) return e;
   h->prof_kind[h->prof_used] = (int8_t)kind;
@@ -544,13 +549,14 @@ extern "C" {
 
 rd_status rd_set_profiling(rd_handle h, int32_t on) {
   if (!h) return fail(nullptr, RD_ERR_ARG, "handle is NULL");
+  if (on < 0 || on > 2) return fail(h, RD_ERR_ARG, "rd_set_profiling: on is 0, 1 or 2");
   RD_CK(h, cudaSetDevice(h->device));
   if (on && !h->prof_ev) {
     h->prof_ev = new cudaEvent_t[2 * rd_ctx::kProfPairs]();
     for (int i = 0; i < 2 * rd_ctx::kProfPairs; ++i) RD_CK(h, cudaEventCreate(&h->prof_ev[i]));
   }
   RD_CK(h, cudaStreamSynchronize(h->stream));
-  h->prof_on = on ? 1 : 0;
+  h->prof_on = on;
   h->prof_used = 0;
   h->prof_ms = h->prof_flops = 0.0;
   h->prof_launches = 0;

@@ -255,8 +255,9 @@ def rd_greedy_next(h, goals, k: int, Yrows, nxt):
     _check(load().rd_greedy_next(h, pg, int(k), py, pn), h)
 
 
-def rd_set_profiling(h, on: bool):
-    _check(load().rd_set_profiling(h, int(bool(on))), h)
+def rd_set_profiling(h, on):
+    """0 / False: off; 1 / True: every dense-contraction kernel; 2: the split GEMM alone."""
+    _check(load().rd_set_profiling(h, int(on)), h)
 
 
 def rd_sync(h):
