@@ -1259,8 +1259,7 @@ SliceBatch slice_batch(const rd_ctx* h, const void* x, int rows_pad, int k_pad) 
 }
 
 // Slice the A operand (rows x k) into digA/eA (chunks of h->kappa along k).
-cudaError_t slice_a(rd_ctx* h, const View& v, int rows_pad, int k_pad, cudaStream_t st) {
-  rd_split_plan* P = h->split;
+cudaError_t slice_a(rd_ctx* h, const View& v, int rows_pad, int k_pad, cudaStream_t st, rd_split_plan* P) {
   cudaError_t e = rd_prof_begin(h, st, RD_PROF_NONE);
   if (e != cudaSuccess) return e;
   const long long warps = (long long)rows_pad * (k_pad / h->kappa);
@@ -1297,8 +1296,8 @@ __global__ void ksplit_reduce_kernel(const double* __restrict__ part, int ksplit
 // Slice the B operand (k x cols, row-major) into digB/eB (K-major per column).  With cacheable
 // (B is the final L^-1 of the current factors), digits already sliced from the same view, digit
 // count and chunk width for the same factorisation are reused.
-cudaError_t slice_b(rd_ctx* h, const View& v, int cols_pad, int k_pad, cudaStream_t st, bool cacheable) {
-  rd_split_plan* P = h->split;
+cudaError_t slice_b(rd_ctx* h, const View& v, int cols_pad, int k_pad, cudaStream_t st, bool cacheable,
+                    rd_split_plan* P) {
   if (cacheable && P->b_cached && P->b_p == v.p && P->b_ld == v.ld && P->b_rows == v.rows && P->b_cols == v.cols &&
       P->b_tri == v.tri && P->b_cols_pad == cols_pad && P->b_k_pad == k_pad && P->b_s == P->s &&
       P->b_kappa == h->kappa && P->b_gen == h->factor_gen)
@@ -1364,14 +1363,14 @@ cudaError_t launch_split(const CUtensorMap& ta, const CUtensorMap& tb, const Spl
 cudaError_t split_gemm(rd_ctx* h, const View& A, const View& B, int M, int N, int K, double alpha, double beta,
                        double* C, long long ldc, int c_rows, int c_cols, int32_t* D, double* Ystore, double flops,
                        cudaStream_t st, const int32_t* row_map = nullptr, const int32_t* col_map = nullptr,
-                       bool b_is_final_linv = false) {
-  rd_split_plan* P = h->split;
+                       bool b_is_final_linv = false, rd_split_plan* plan = nullptr) {
+  rd_split_plan* P = plan ? plan : h->split;  // (the side stream's products have a workspace of their own)
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   if (M % 64 || N % 64 || K % 64) return cudaErrorInvalidValue;
   const int ma_pad = round_up(M, TM), nb_pad = round_up(N, TN), k_pad = round_up(K, h->kappa);  // k_pad <= N + 128
   cudaError_t e;
-  if ((e = slice_a(h, A, ma_pad, k_pad, st)) != cudaSuccess) return e;
-  if ((e = slice_b(h, B, nb_pad, k_pad, st, b_is_final_linv)) != cudaSuccess) return e;
+  if ((e = slice_a(h, A, ma_pad, k_pad, st, P)) != cudaSuccess) return e;
+  if ((e = slice_b(h, B, nb_pad, k_pad, st, b_is_final_linv, P)) != cudaSuccess) return e;
   // CTA pairs (256 x 128 per cluster of two, half of each B tile per CTA) with 256-wide chunks when
   // the rows fill whole pairs, unless the handle asks for single CTAs
   const bool pair = h->split_pairs && h->kappa == KAPPA_WIDE && ma_pad % (2 * TM) == 0;
@@ -1520,8 +1519,17 @@ cudaError_t product(rd_ctx* h, bool fp64, const View& A, const View& B, int M, i
   return rd_gemm_f64(h, &g, 1, st, flops);
 }
 
-// Recursive factorisation of the diagonal range [lo, hi) (see the header comment).
-cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
+// the least node whose S_L runs on the side stream: smaller products are short, and so are the
+// right halves they would overlap
+constexpr int SIDE_MIN_NODE = 2048;
+
+// elements of dSL: the S_L of every depth at once (m1 m2 <= (m/2 + 63) m/2 down the right spine)
+long long side_sl_elems(long long N) { return N * N / 3 + 128 * N; }
+
+// Recursive factorisation of the diagonal range [lo, hi) (see the header comment).  With the
+// overlap on, a node's S_L = L21 L11^-1 (rows m2, columns m1) is computed on the side stream into
+// dSL + sl_off while the right half is factored; the right half's own S_L go beyond it.
+cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st, long long sl_off = 0, int depth = 0) {
   const int m = hi - lo;
   if (m <= LEAF) return rd_lu_diag(h, lo, st);
   const bool f64 = m <= h->fp64_node;
@@ -1531,7 +1539,7 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
   double* LU = h->dLU;
   double* T = h->dT;
   cudaError_t e;
-  if ((e = factor(h, lo, mid, st)) != cudaSuccess) return e;
+  if ((e = factor(h, lo, mid, st, sl_off, depth + 1)) != cudaSuccess) return e;
   double* A12 = LU + (long long)lo * N + mid;
   double* A21 = LU + (long long)mid * N + lo;
   double* A22 = LU + (long long)mid * N + mid;
@@ -1559,11 +1567,26 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
                      2.0 * t1 * m2, st)) != cudaSuccess)
       return e;
   }
+  // S_L = L21 L11^-1 needs only the left half: on the side stream, while the right half is factored
+  // (the right half writes neither A21 nor T11; the side product has its own digit workspace)
+  const bool side = !f64 && m >= SIDE_MIN_NODE && h->side && h->split_side && depth < RD_SIDE_DEPTH &&
+                    sl_off + (long long)m1 * m2 <= side_sl_elems(N);
+  double* SLs = side ? h->dSL + sl_off : nullptr;
+  if (side) {
+    const cudaEvent_t fork = h->side_ev[2 * depth], join = h->side_ev[2 * depth + 1];
+    if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->side, fork, 0)) != cudaSuccess) return e;
+    if ((e = split_gemm(h, full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_LOWER_UNIT), m2, m1, m1, 1.0, 0.0, SLs, m1, m2,
+                        m1, nullptr, nullptr, 2.0 * t1 * m2, h->side, nullptr, nullptr, false, h->split_side)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(join, h->side)) != cudaSuccess) return e;
+  }
   // A22 -= L21 U12
   if ((e = product(h, f64, full(A21, N, m2, m1), full(A12, N, m1, m2), m2, m2, m1, -1.0, 1.0, A22, N,
                    2.0 * m2 * (double)m2 * m1, st)) != cudaSuccess)
     return e;
-  if ((e = factor(h, mid, hi, st)) != cudaSuccess) return e;
+  if ((e = factor(h, mid, hi, st, side ? sl_off + (long long)m1 * m2 : sl_off, depth + 1)) != cudaSuccess) return e;
   // L^-1_21 = -L22^-1 (L21 L11^-1) ; U^-1_12 = -U11^-1 (U12 U22^-1)
   double* SL = h->dS;                         // m2 x m1
   double* SU = h->dS + (long long)m1 * m2;    // m1 x m2
@@ -1580,9 +1603,13 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st) {
                  N)};
     return rd_gemm_f64(h, x, 2, st, fl);
   }
-  if ((e = product(h, f64, full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_LOWER_UNIT), m2, m1, m1, 1.0, 0.0, SL, m1,
-                   2.0 * t1 * m2, st)) != cudaSuccess)
+  if (side) {  // S_L from the side stream
+    if ((e = cudaStreamWaitEvent(st, h->side_ev[2 * depth + 1], 0)) != cudaSuccess) return e;
+    SL = SLs;
+  } else if ((e = product(h, f64, full(A21, N, m2, m1), tri(T11, N, m1, RD_TRI_LOWER_UNIT), m2, m1, m1, 1.0, 0.0, SL,
+                          m1, 2.0 * t1 * m2, st)) != cudaSuccess) {
     return e;
+  }
   if ((e = product(h, f64, tri(T22, N, m2, RD_TRI_LOWER_UNIT), full(SL, m1, m2, m1), m2, m1, m2, -1.0, 0.0,
                    T + (long long)mid * N + lo, N, 2.0 * t2 * m1, st)) != cudaSuccess)
     return e;
@@ -1616,6 +1643,8 @@ __global__ void gather_uinv_rows_kernel(const double* __restrict__ T, long long 
 }
 
 }  // namespace
+
+static void side_prepare(rd_ctx* h, int s);
 
 rd_status rd_split_prepare(rd_ctx* h, int s) {
   const int smax = h->ordered ? MAX_SLICES_NARROW : MAX_SLICES_WIDE;
@@ -1656,6 +1685,7 @@ rd_status rd_split_prepare(rd_ctx* h, int s) {
   }
   h->split->s = s;
   h->slices = s;
+  side_prepare(h, s);
   return RD_OK;
 }
 
@@ -1685,7 +1715,85 @@ rd_status rd_split_prepare_borrowed(rd_ctx* h, int s, void* digA, void* digB, in
   return RD_OK;
 }
 
+// The overlap's streams, events, S_L buffer and side workspace (work in flight on either stream
+// finishes first).
+static void side_release(rd_ctx* h) {
+  if (h->prio) cudaStreamSynchronize(h->prio);
+  if (h->side) cudaStreamSynchronize(h->side);
+  if (rd_split_plan* Q = h->split_side) {
+    void* ptrs[] = {Q->digA, Q->digB, Q->eA, Q->eB, Q->part};
+    for (void* q : ptrs)
+      if (q) rd_dev_free(h, q);
+    h->bytes -= (h->bytes >= Q->bytes) ? Q->bytes : 0;
+    delete Q;
+    h->split_side = nullptr;
+  }
+  if (h->dSL) {
+    rd_dev_free(h, h->dSL);
+    const int64_t b = (int64_t)side_sl_elems(h->N) * (int64_t)sizeof(double);
+    h->bytes -= (h->bytes >= b) ? b : 0;
+    h->dSL = nullptr;
+  }
+  for (cudaEvent_t& ev : h->side_ev)
+    if (ev) cudaEventDestroy(ev), ev = nullptr;
+  for (cudaEvent_t& ev : h->prio_ev)
+    if (ev) cudaEventDestroy(ev), ev = nullptr;
+  if (h->side) cudaStreamDestroy(h->side), h->side = nullptr;
+  if (h->prio) cudaStreamDestroy(h->prio), h->prio = nullptr;
+}
+
+// The overlap's resources for s digits (one graph, N >= RD_SIDE_MIN_N); without them (any failure)
+// the recursion runs on one stream, as for every other handle.
+static void side_prepare(rd_ctx* h, int s) {
+  if (!h->split_overlap || h->nbatch > 1 || h->N < RD_SIDE_MIN_N) return;
+  if (h->split_side && h->split_side->cap_s >= s) {
+    h->split_side->s = s;
+    return;
+  }
+  side_release(h);
+  cudaError_t e = cudaSuccess;
+  int least = 0, greatest = 0;
+  e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->prio, cudaStreamNonBlocking, greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, least);
+  for (cudaEvent_t& ev : h->side_ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  for (cudaEvent_t& ev : h->prio_ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  // the side products' operands: at most N/2 + 63 rows and columns (the recursion's first split)
+  rd_split_plan* Q = nullptr;
+  if (e == cudaSuccess) {
+    Q = new rd_split_plan();
+    h->split_side = Q;
+    Q->N = h->N;
+    Q->s = Q->cap_s = s;
+    const size_t half = (size_t)h->N / 2 + 2 * TM;
+    const size_t NK = half * (half + KAPPA_WIDE);
+    const size_t dig = (size_t)s * NK * sizeof(__nv_bfloat16);
+    const size_t ex = (NK / KAPPA_NARROW + 64) * sizeof(int);
+    auto get = [&](void** ptr, size_t bytes) {
+      if (e == cudaSuccess) e = rd_dev_alloc(h, ptr, bytes);
+      if (e == cudaSuccess) Q->bytes += (int64_t)bytes;
+    };
+    get((void**)&Q->digA, dig);
+    get((void**)&Q->digB, dig);
+    get((void**)&Q->eA, ex);
+    get((void**)&Q->eB, ex);
+    if (e == cudaSuccess) h->bytes += Q->bytes;
+  }
+  if (e == cudaSuccess) {
+    const size_t b = (size_t)side_sl_elems(h->N) * sizeof(double);
+    e = rd_dev_alloc(h, (void**)&h->dSL, b);
+    if (e == cudaSuccess) h->bytes += (int64_t)b;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // (not sticky: the handle goes on without the overlap)
+    side_release(h);
+  }
+}
+
 void rd_split_release(rd_ctx* h) {
+  side_release(h);
   rd_split_plan* P = h->split;
   if (!P) return;
   if (P->borrowed) P->digA = P->digB = nullptr, P->eA = P->eB = nullptr;
@@ -1697,8 +1805,18 @@ void rd_split_release(rd_ctx* h) {
   h->split = nullptr;
 }
 
-// LU and both triangular inverses are produced together by the recursion.
-cudaError_t rd_lu_split(rd_ctx* h, cudaStream_t s) { return factor(h, 0, h->N, s); }
+// LU and both triangular inverses are produced together by the recursion.  With the overlap on,
+// the recursion runs on the handle's high-priority stream (forked from s and joined back to it),
+// so that its kernels take SMs before the side stream's S_L products.
+cudaError_t rd_lu_split(rd_ctx* h, cudaStream_t s) {
+  if (!h->prio) return factor(h, 0, h->N, s);
+  cudaError_t e;
+  if ((e = cudaEventRecord(h->prio_ev[0], s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(h->prio, h->prio_ev[0], 0)) != cudaSuccess) return e;
+  if ((e = factor(h, 0, h->N, h->prio)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(h->prio_ev[1], h->prio)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s, h->prio_ev[1], 0);
+}
 
 
 cudaError_t rd_trmm_decode_split(rd_ctx* h, int32_t* D, double* Y, cudaStream_t s) {

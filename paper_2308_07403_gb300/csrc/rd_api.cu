@@ -215,6 +215,8 @@ rd_status create_impl(const uint8_t* A, const float* W, int32_t n, double gamma,
   {
     const char* pairs = getenv("RD_SPLIT_CTA_PAIRS");
     h->split_pairs = (pairs && pairs[0] == '0') ? 0 : 1;
+    const char* overlap = getenv("RD_SPLIT_OVERLAP");
+    h->split_overlap = (overlap && overlap[0] == '0') ? 0 : 1;
   }
   h->pool = pool;
   h->stream = stream;

@@ -52,6 +52,10 @@
 // digit count.
 #define RD_SCREEN_WEIGHTED 1.1
 
+// the split recursion's overlap (rd_ctx::split_overlap): the least N, and the deepest node it serves
+#define RD_SIDE_MIN_N 8192
+#define RD_SIDE_DEPTH 16
+
 struct rd_split_plan;       // defined by the split path
 
 // One graph of a stacked batch (device array, see rd_ctx::nbatch): the batched split path's
@@ -137,6 +141,18 @@ struct rd_ctx {
   double last_residual = 0.0;  // largest sampled-row residual of the last split result
 
   rd_split_plan* split = nullptr;
+  // Overlap in the split recursion (one graph, N >= RD_SIDE_MIN_N): the first product of a node's
+  // L-side inverse block, S_L = L21 L11^-1, needs only the left half, so it runs on a side stream of
+  // the lowest priority, with its own digit workspace, while the node's right half is factored (whose
+  // leaf chain and small FP64 products leave most SMs idle); dSL holds S_L of every depth of the
+  // recursion at once.  Environment RD_SPLIT_OVERLAP=0 at rd_create turns it off.
+  int split_overlap = 1;
+  rd_split_plan* split_side = nullptr;
+  cudaStream_t prio = nullptr;  // the recursion's own stream (highest priority), forked from and joined to the caller's
+  cudaStream_t side = nullptr;  // the S_L products (lowest priority)
+  cudaEvent_t prio_ev[2] = {};
+  cudaEvent_t side_ev[2 * RD_SIDE_DEPTH] = {};
+  double* dSL = nullptr;
 
   cudaEvent_t ev[8] = {};
   int ev_used[4] = {0, 0, 0, 0};

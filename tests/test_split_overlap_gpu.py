@@ -1,0 +1,65 @@
+"""The split recursion's overlap (n >= 8192, one graph): each node's S_L = L21 L11^-1 runs on a
+low-priority side stream with its own digit workspace while the node's right half is factored on
+the handle's high-priority stream.  The product is the same split GEMM on the same operands, so Y
+must be bit-identical with the overlap turned off (RD_SPLIT_OVERLAP=0 at rd_create), and D must be
+the oracle's (the golden hash)."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2308_07403_gb300 import graphs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def rd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_07403_gb300 import build
+    from paper_2308_07403_gb300 import rd as _rd
+
+    build.build()
+    _rd.load()
+    return _rd
+
+
+def run(rd, A, g, overlap):
+    n = A.shape[0]
+    old = os.environ.get("RD_SPLIT_OVERLAP")
+    os.environ["RD_SPLIT_OVERLAP"] = "1" if overlap else "0"
+    try:
+        D = torch.empty((n, n), dtype=torch.int32, device="cuda")
+        Y = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        with rd.Handle(torch.from_numpy(A).cuda(), g, stream=torch.cuda.current_stream().cuda_stream) as h:
+            h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
+            h.apsp(D, Y)
+            h.sync()
+            st = h.stats()
+        torch.cuda.synchronize()
+        return D, Y, st
+    finally:
+        if old is None:
+            del os.environ["RD_SPLIT_OVERLAP"]
+        else:
+            os.environ["RD_SPLIT_OVERLAP"] = old
+
+
+@pytest.mark.parametrize("kind", ["er", "grid"])
+def test_overlap_is_bit_identical(rd, kind):
+    A, g = graphs.workload_large(kind, 0.5)
+    D1, Y1, st1 = run(rd, A, g, True)
+    D0, Y0, st0 = run(rd, A, g, False)
+    assert st1["precision_used"] == rd.RD_PREC_SPLIT_BF16 and st1["slices"] == st0["slices"]
+    assert torch.equal(Y1, Y0)
+    assert torch.equal(D1, D0)
+    with open(os.path.join(HERE, "golden", f"large_{kind}_0.5.json")) as f:
+        rec = json.load(f)
+    digest = hashlib.sha256(np.ascontiguousarray(D1.cpu().numpy(), dtype="<i4").tobytes()).hexdigest()
+    assert digest == rec["sha256_D"]
