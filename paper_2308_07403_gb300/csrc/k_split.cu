@@ -1521,7 +1521,7 @@ cudaError_t product(rd_ctx* h, bool fp64, const View& A, const View& B, int M, i
 
 // the least node whose S_L runs on the side stream: smaller products are short, and so are the
 // right halves they would overlap
-constexpr int SIDE_MIN_NODE = 2048;
+constexpr int SIDE_MIN_NODE = 1024;
 
 // elements of dSL: the S_L of every depth at once (m1 m2 <= (m/2 + 63) m/2 down the right spine)
 long long side_sl_elems(long long N) { return N * N / 3 + 128 * N; }
