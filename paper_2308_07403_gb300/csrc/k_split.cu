@@ -1523,12 +1523,15 @@ cudaError_t product(rd_ctx* h, bool fp64, const View& A, const View& B, int M, i
 // right halves they would overlap
 constexpr int SIDE_MIN_NODE = 1024;
 
-// elements of dSL: the S_L of every depth at once (m1 m2 <= (m/2 + 63) m/2 down the right spine)
-long long side_sl_elems(long long N) { return N * N / 3 + 128 * N; }
+// elements of dSL: S_L and V of every depth at once (m1 m2 <= (m/2 + 63) m/2 each, down the right spine)
+long long side_sl_elems(long long N) { return 2 * (N * N / 3 + 128 * N); }
 
 // Recursive factorisation of the diagonal range [lo, hi) (see the header comment).  With the
-// overlap on, a node's S_L = L21 L11^-1 (rows m2, columns m1) is computed on the side stream into
-// dSL + sl_off while the right half is factored; the right half's own S_L go beyond it.
+// overlap on, a node's S_L = L21 L11^-1 (m2 x m1) and V = U11^-1 U12 (m1 x m2) are computed on the
+// side stream into dSL + sl_off while the right half is factored (the right half's own go beyond
+// them), and the U side's block becomes U^-1_12 = -V U22^-1: the same product reassociated, one
+// product fewer after the right half.  Every product there is sign-definite (U11^-1 >= 0, U12 <= 0,
+// U22^-1 >= 0), so the reassociation keeps each entry accurate relative to itself.
 cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st, long long sl_off = 0, int depth = 0) {
   const int m = hi - lo;
   if (m <= LEAF) return rd_lu_diag(h, lo, st);
@@ -1570,7 +1573,7 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st, long long sl_off 
   // S_L = L21 L11^-1 needs only the left half: on the side stream, while the right half is factored
   // (the right half writes neither A21 nor T11; the side product has its own digit workspace)
   const bool side = !f64 && m >= SIDE_MIN_NODE && h->side && h->split_side && depth < RD_SIDE_DEPTH &&
-                    sl_off + (long long)m1 * m2 <= side_sl_elems(N);
+                    sl_off + 2LL * m1 * m2 <= side_sl_elems(N);
   double* SLs = side ? h->dSL + sl_off : nullptr;
   if (side) {
     const cudaEvent_t fork = h->side_ev[2 * depth], join = h->side_ev[2 * depth + 1];
@@ -1580,13 +1583,18 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st, long long sl_off 
                         m1, nullptr, nullptr, 2.0 * t1 * m2, h->side, nullptr, nullptr, false, h->split_side)) !=
         cudaSuccess)
       return e;
+    // V = U11^-1 U12 (the U side reassociated: U^-1_12 = -V U22^-1)
+    if ((e = split_gemm(h, tri(T11, N, m1, RD_TRI_UPPER), full(A12, N, m1, m2), m1, m2, m1, 1.0, 0.0,
+                        SLs + (long long)m1 * m2, m2, m1, m2, nullptr, nullptr, 2.0 * t1 * m2, h->side, nullptr,
+                        nullptr, false, h->split_side)) != cudaSuccess)
+      return e;
     if ((e = cudaEventRecord(join, h->side)) != cudaSuccess) return e;
   }
   // A22 -= L21 U12
   if ((e = product(h, f64, full(A21, N, m2, m1), full(A12, N, m1, m2), m2, m2, m1, -1.0, 1.0, A22, N,
                    2.0 * m2 * (double)m2 * m1, st)) != cudaSuccess)
     return e;
-  if ((e = factor(h, mid, hi, st, side ? sl_off + (long long)m1 * m2 : sl_off, depth + 1)) != cudaSuccess) return e;
+  if ((e = factor(h, mid, hi, st, side ? sl_off + 2LL * m1 * m2 : sl_off, depth + 1)) != cudaSuccess) return e;
   // L^-1_21 = -L22^-1 (L21 L11^-1) ; U^-1_12 = -U11^-1 (U12 U22^-1)
   double* SL = h->dS;                         // m2 x m1
   double* SU = h->dS + (long long)m1 * m2;    // m1 x m2
@@ -1613,6 +1621,9 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st, long long sl_off 
   if ((e = product(h, f64, tri(T22, N, m2, RD_TRI_LOWER_UNIT), full(SL, m1, m2, m1), m2, m1, m2, -1.0, 0.0,
                    T + (long long)mid * N + lo, N, 2.0 * t2 * m1, st)) != cudaSuccess)
     return e;
+  if (side)  // U^-1_12 = -V U22^-1
+    return product(h, f64, full(SLs + (long long)m1 * m2, m2, m1, m2), tri(T22, N, m2, RD_TRI_UPPER), m1, m2, m2, -1.0,
+                   0.0, T + (long long)lo * N + mid, N, 2.0 * t2 * m1, st);
   if ((e = product(h, f64, full(A12, N, m1, m2), tri(T22, N, m2, RD_TRI_UPPER), m1, m2, m2, 1.0, 0.0, SU, m2,
                    2.0 * t2 * m1, st)) != cudaSuccess)
     return e;

@@ -1,8 +1,10 @@
-"""The split recursion's overlap (n >= 8192, one graph): each node's S_L = L21 L11^-1 runs on a
-low-priority side stream with its own digit workspace while the node's right half is factored on
-the handle's high-priority stream.  The product is the same split GEMM on the same operands, so Y
-must be bit-identical with the overlap turned off (RD_SPLIT_OVERLAP=0 at rd_create), and D must be
-the oracle's (the golden hash)."""
+"""The split recursion's overlap (n >= 8192, one graph): each node's S_L = L21 L11^-1 and
+V = U11^-1 U12 run on a low-priority side stream with their own digit workspace while the node's
+right half is factored on the handle's high-priority stream, and the U side's inverse block is
+then -V U22^-1 instead of -U11^-1 (U12 U22^-1).  The L side is the same product on the same
+operands; the U side is reassociated, so Y may differ from the one-stream path
+(RD_SPLIT_OVERLAP=0 at rd_create) in its last bits only: D must be identical and the oracle's (the
+golden hash), Y within 1e-12 relative with the same zero pattern."""
 import hashlib
 import json
 import os
@@ -52,13 +54,16 @@ def run(rd, A, g, overlap):
 
 
 @pytest.mark.parametrize("kind", ["er", "grid"])
-def test_overlap_is_bit_identical(rd, kind):
+def test_overlap_matches_one_stream(rd, kind):
     A, g = graphs.workload_large(kind, 0.5)
     D1, Y1, st1 = run(rd, A, g, True)
     D0, Y0, st0 = run(rd, A, g, False)
     assert st1["precision_used"] == rd.RD_PREC_SPLIT_BF16 and st1["slices"] == st0["slices"]
-    assert torch.equal(Y1, Y0)
     assert torch.equal(D1, D0)
+    assert torch.equal(Y1 == 0, Y0 == 0)
+    nz = Y0 != 0
+    rel = ((Y1[nz] - Y0[nz]).abs() / Y0[nz].abs()).max().item()
+    assert rel < 1e-12, rel
     with open(os.path.join(HERE, "golden", f"large_{kind}_0.5.json")) as f:
         rec = json.load(f)
     digest = hashlib.sha256(np.ascontiguousarray(D1.cpu().numpy(), dtype="<i4").tobytes()).hexdigest()
