@@ -351,3 +351,32 @@ def test_goal_rows_follow_reloaded_graphs(rd):
             h.goal_solve(goals, rows)
             assert rel_err(rows, Yo[goals]) < YTOL, step
         assert h.stats()["precision_used"] == rd.RD_PREC_SPLIT_BF16
+
+
+def test_profiling_modes(rd):
+    """rd_set_profiling: mode 1 brackets every dense-contraction launch (the split GEMM and the FP64
+    products of the recursion's small nodes), mode 2 the split GEMM alone; another value is refused."""
+    A, g = graphs.workload_small()
+    n = A.shape[0]
+    D = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    At = torch.from_numpy(A).cuda()
+    with rd.Handle(At, g, stream=torch.cuda.current_stream().cuda_stream) as h:
+        h.set_precision(rd.RD_PREC_SPLIT_BF16, 0)
+        h.apsp(D)
+        counts = {}
+        for mode in (1, 2):
+            rd.rd_set_profiling(h.h, mode)
+            h.load(At, g)  # factored again: the recursion's products run, not just the inverse product
+            h.apsp(D)
+            h.sync()
+            st = h.stats()
+            counts[mode] = (st["prof_launches"], st["prof_split_launches"])
+        with pytest.raises(rd.RDError) as ei:
+            rd.rd_set_profiling(h.h, 3)
+        assert ei.value.status == rd.RD_ERR_ARG
+        rd.rd_set_profiling(h.h, 0)
+    all1, split1 = counts[1]
+    all2, split2 = counts[2]
+    assert split1 > 0 and split1 == split2
+    assert all1 > split1          # the FP64 products of the small nodes are counted too
+    assert all2 == split2         # mode 2: the split GEMM alone
