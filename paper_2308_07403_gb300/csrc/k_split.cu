@@ -1570,8 +1570,9 @@ cudaError_t factor(rd_ctx* h, int lo, int hi, cudaStream_t st, long long sl_off 
                      2.0 * t1 * m2, st)) != cudaSuccess)
       return e;
   }
-  // S_L = L21 L11^-1 needs only the left half: on the side stream, while the right half is factored
-  // (the right half writes neither A21 nor T11; the side product has its own digit workspace)
+  // S_L = L21 L11^-1 and V = U11^-1 U12 need only the left half: on the side stream, while the right
+  // half is factored (the right half writes none of A12, A21, T11; the side products have their own
+  // digit workspace)
   const bool side = !f64 && m >= SIDE_MIN_NODE && h->side && h->split_side && depth < RD_SIDE_DEPTH &&
                     sl_off + 2LL * m1 * m2 <= side_sl_elems(N);
   double* SLs = side ? h->dSL + sl_off : nullptr;
