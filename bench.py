@@ -64,8 +64,8 @@ def parse():
                    help="end-to-end steps (host buffers); 6 = each of the six graphs once, the mix of the timed steps")
     p.add_argument("--verify", type=int, default=1, help="hash D of every graph against the oracle's")
     p.add_argument("--cpu-sample", type=int, default=1536, help="oracle sample size (leading block)")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "serving", "weighted", "update", "product",
-                                                            "mma-probe"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "batched-stack", "serving", "weighted",
+                                                            "update", "product", "mma-probe"],
                    help="single: the n=8192 graphs (default); batched: 4096 graphs n~U[32,512] in one launch; "
                         "serving: a Poisson stream of requests over a pool of graphs; "
                         "weighted: n=32768 king grid, split inverse + 1024 goal rows + greedy; "
@@ -388,6 +388,67 @@ def time_batch(b, A_dev, D_dev, steps, warmup, dev, local, world, dist):
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
     tot = reduce_max(ev[0].elapsed_time(ev[-1]), dist, world, f"cuda:{local}")
     return per, tot, clk
+
+
+def run_batched_stack(args):
+    """One stack of 152 seeded directed ER graphs (p = 4/n, n uniform in [480, 512], gain 0.5/(Delta+1))
+    with every size class on the split path (autotune off), against the FP64 Gauss-Jordan kernel on the
+    same batch: the batched split variant where it is meant to win.  Each variant is one CUDA-graph
+    replay per step; D of both is compared graph by graph."""
+    import torch
+
+    from paper_2308_07403_gb300 import build, graphs, rd
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    rd.load()
+    rng = np.random.default_rng(2308_07403 + 3000)
+    ns = rng.integers(480, 513, size=152).astype(np.int32)
+    As = [graphs.er(int(n), 4.0 / n, int(rng.integers(1 << 30))) for n in ns]
+    gs = np.array([graphs.gamma_small(A) for A in As])
+    flop = float((2.0 * ns.astype(np.float64) ** 3).sum())
+    b = rd.Batch(ns, gs)
+    off = b.offsets()
+    A_host = torch.empty(int(off[-1]), dtype=torch.uint8).pin_memory()
+    A_np = A_host.numpy()
+    for g, A in enumerate(As):
+        A_np[off[g]:off[g + 1]] = A.ravel()
+    A_dev = A_host.to(dev)
+    D_dev = torch.empty(int(off[-1]), dtype=torch.int32, device=dev)
+    steps, warmup = max(1, args.steps), max(3, args.warmup)
+    _, tot64, clk64 = time_batch(b, A_dev, D_dev, steps, warmup, dev, local, 1, None)
+    D64 = D_dev.cpu()
+    b.set_precision(rd.RD_PREC_SPLIT_BF16, False)
+    per, tot, clk = time_batch(b, A_dev, D_dev, steps, warmup, dev, local, 1, None)
+    routes = b.routes()
+    info = b.split_info()
+    launches = b.tuning()["launches_last_run"]
+    same = bool(torch.equal(D_dev.cpu(), D64))
+    b.close()
+    ms, ms64 = tot / steps, tot64 / steps
+    on_split = routes == 1
+    digits = {int(d): int((info["digits"][on_split] == d).sum()) for d in sorted(set(info["digits"][on_split].tolist()))}
+    line = {
+        "metric": "batched split stack: 152 ER graphs n~U[480,512], ms per batch (split variant vs FP64 kernel)",
+        "value": ms, "unit": "ms", "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16-digits+f64",
+        "data": "synthetic",
+        "config": {"workload": "152 directed ER graphs, p = 4/n, n uniform in [480, 512], gain 0.5/(Delta+1); "
+                               "every size class on the split path (autotune off); one CUDA-graph replay per step"},
+        "fp64_ms_per_step": ms64, "speedup_over_fp64": ms64 / ms, "effective_tflops": flop / (ms * 1e-3) / 1e12,
+        "routes": {"split": int((routes == 1).sum()), "split_redone_fp64": int((routes == 2).sum()),
+                   "screened_to_fp64": int((routes == 3).sum()), "gain_failed": int((routes == 4).sum())},
+        "second_pass": int(((info["passes"] > 1) & on_split).sum()), "digits_histogram": digits,
+        "screen_bits": [float(np.min(info["screen_bits"])), float(np.max(info["screen_bits"]))],
+        "largest_residual_kept": float(np.max(info["residual"][on_split])) if on_split.any() else None,
+        "D_identical_to_fp64_variant": same, "gpu_launches": int(launches), "clocks": clk,
+        "e2e": None, "cpu_baseline": None,
+        "roofline": {"bound": "latency", "note": "a stack of small products; the kernels' rooflines are the "
+                                                 "single-graph and product lines'", "traffic": None},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_batched(args):
@@ -1105,6 +1166,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "batched-stack":
+        run_batched_stack(args)
         return
     if args.workload == "serving":
         run_serving(args)
