@@ -110,6 +110,9 @@ typedef struct {
   int64_t prof_update_launches; /* profiled rank-1 update passes of rd_update_edge, their      */
   double prof_update_ms;  /* summed device time and algorithmic bytes (read and write Y,      */
   double prof_update_bytes; /* write D: 20 n^2 per pass)                                      */
+  double prof_split_busy_ms; /* the split GEMM's busy time: the union of its profiled launches' */
+                          /* intervals (prof_split_ms sums their durations, which counts twice */
+                          /* the time two launches of the recursion's two streams overlap)    */
 } rd_stats;
 
 /* Create a handle for the unweighted graph A (n x n bytes) and gain gamma: validates gamma

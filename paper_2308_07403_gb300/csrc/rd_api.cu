@@ -9,6 +9,9 @@
 //   inverse:  blocked triangular inverses L^-1, U^-1
 //   product:  Y = U^-1 L^-1 with D = ceil(log_gamma Y - tau) fused into the epilogue
 #include <algorithm>
+#include <utility>
+#include <vector>
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -508,8 +511,29 @@ cudaError_t rd_prof_end(rd_ctx* h, cudaStream_t s, int kind, double flops) {
 
 cudaError_t rd_prof_collect(rd_ctx* h) {
   if (!h->prof_ev || h->prof_used == 0) return cudaSuccess;
-  cudaError_t e = cudaEventSynchronize(h->prof_ev[2 * h->prof_used - 1]);
+  cudaError_t e = cudaSuccess;
+  // every pair's end (the pairs of the split recursion's side stream may end after the last one
+  // recorded on the handle's stream)
+  for (int i = 0; i < h->prof_used && e == cudaSuccess; ++i) e = cudaEventSynchronize(h->prof_ev[2 * i + 1]);
   if (e != cudaSuccess) return e;
+  // the split GEMM's busy time: the union of its launches' intervals (launches on the two streams of
+  // the recursion overlap; their summed durations count the shared time twice)
+  std::vector<std::pair<float, float>> iv;
+  for (int i = 0; i < h->prof_used; ++i) {
+    if (h->prof_kind[i] != RD_PROF_SPLIT) continue;
+    float t0 = 0.f, t1 = 0.f;
+    if ((e = cudaEventElapsedTime(&t0, h->prof_ev[0], h->prof_ev[2 * i])) != cudaSuccess) return e;
+    if ((e = cudaEventElapsedTime(&t1, h->prof_ev[0], h->prof_ev[2 * i + 1])) != cudaSuccess) return e;
+    iv.emplace_back(t0, t1);
+  }
+  std::sort(iv.begin(), iv.end());
+  double busy = 0.0;
+  for (size_t i = 0; i < iv.size();) {
+    float a = iv[i].first, b = iv[i].second;
+    for (++i; i < iv.size() && iv[i].first <= b; ++i) b = std::max(b, iv[i].second);
+    busy += (double)(b - a);
+  }
+  h->prof_split_busy_ms += busy;
   for (int i = 0; i < h->prof_used; ++i) {
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]);
@@ -563,6 +587,7 @@ rd_status rd_set_profiling(rd_handle h, int32_t on) {
   h->prof_ms = h->prof_flops = 0.0;
   h->prof_launches = 0;
   h->prof_split_ms = h->prof_split_flops = 0.0;
+  h->prof_split_busy_ms = 0.0;
   h->prof_split_launches = 0;
   h->prof_update_ms = h->prof_update_bytes = 0.0;
   h->prof_update_launches = 0;
@@ -903,6 +928,7 @@ rd_status rd_get_stats(rd_handle h, rd_stats* s) {
   s->prof_update_launches = h->prof_update_launches;
   s->prof_update_ms = h->prof_update_ms;
   s->prof_update_bytes = h->prof_update_bytes;
+  s->prof_split_busy_ms = h->prof_split_busy_ms;
   return st;
 }
 

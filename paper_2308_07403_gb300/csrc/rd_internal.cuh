@@ -165,6 +165,7 @@ struct rd_ctx {
   // algorithmic flop count is accumulated.
   int64_t launches = 0;
   int prof_on = 0;
+  double prof_split_busy_ms = 0.0;  // union of the split GEMM's profiled launch intervals
   static constexpr int kProfPairs = 4096;
   cudaEvent_t* prof_ev = nullptr;  // 2 * kProfPairs
   int prof_used = 0;

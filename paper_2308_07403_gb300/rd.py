@@ -99,6 +99,7 @@ class rd_stats(ctypes.Structure):
         ("edge_updates", ctypes.c_int64), ("update_refactors", ctypes.c_int64),
         ("prof_update_launches", ctypes.c_int64), ("prof_update_ms", ctypes.c_double),
         ("prof_update_bytes", ctypes.c_double),
+        ("prof_split_busy_ms", ctypes.c_double),
     ]
 
 
