@@ -149,7 +149,15 @@ rd_status rd_set_stream(rd_handle h, void* stream);
  * min(1e-9, tau |ln gamma| / 16) per entry, at least 1e-12 (rd_stats.split_residual; D is exact
  * while Y's relative error stays below tau |ln gamma|).  When the check fails it recomputes the graph's inverse with
  * the digits the residual r asks for (about log2(r / 2^-40) / 7 more), or in FP64 beyond the
- * order's limit.  Drops cached factors when the mode changes. */
+ * order's limit.  Drops cached factors when the mode changes.
+ * For a handle with N >= 8192 (N: n rounded up to 128) the split factorisation overlaps two of
+ * each recursion node's products (S_L = L21 L11^-1 and V = U11^-1 U12, the U side's inverse block
+ * then formed as -V U22^-1) with the factorisation of the node's right half, on two streams the
+ * handle creates (the highest and the lowest priority), forked from and joined back to the
+ * handle's stream with events: the caller still sees one ordered stream.  It takes about
+ * 2 s (N/2)^2 BF16 digits and 2 N^2 / 3 doubles more device memory (s digits); the environment
+ * variable RD_SPLIT_OVERLAP=0 at rd_create turns it off (one stream, the products as in the
+ * paper's order). */
 rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices);
 
 /* Change the decode snap tau (>= 0, < 0.5).  The split path's self-check limit follows tau at
