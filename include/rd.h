@@ -156,8 +156,8 @@ rd_status rd_set_stream(rd_handle h, void* stream);
  * handle creates (the highest and the lowest priority), forked from and joined back to the
  * handle's stream with events: the caller still sees one ordered stream.  It takes about
  * 2 s (N/2)^2 BF16 digits and 2 N^2 / 3 doubles more device memory (s digits); the environment
- * variable RD_SPLIT_OVERLAP=0 at rd_create turns it off (one stream, the products as in the
- * paper's order). */
+ * variable RD_SPLIT_OVERLAP=0 at rd_create turns it off (one stream; the U side's block then
+ * -U11^-1 (U12 U22^-1)). */
 rd_status rd_set_precision(rd_handle h, int32_t mode, int32_t slices);
 
 /* Change the decode snap tau (>= 0, < 0.5).  The split path's self-check limit follows tau at
