@@ -61,3 +61,18 @@ def test_reference_arm_other_ranks_exit_quietly():
                         "--warmup", "0", "--cpu-sample", "64"], capture_output=True, text=True, timeout=300,
                        cwd=ROOT, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_defaults_cover_the_six_graphs(monkeypatch):
+    """The default run: at least 3 warm-up steps, and the end-to-end line over six steps, one per
+    graph of the n = 8192 workload (step i runs graph i mod 6), the mix of the timed steps."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    args = bench.parse()
+    assert args.warmup >= 3 and args.steps >= 6
+    assert args.e2e_steps == len(bench.workloads(64)) == 6
+    for w in ("single", "batched", "batched-stack", "serving", "weighted", "update", "product", "mma-probe"):
+        monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", w])
+        assert bench.parse().workload == w
